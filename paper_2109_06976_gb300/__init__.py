@@ -1,0 +1,149 @@
+"""GB300-native batched rigid-body dynamics with analytical gradients.
+
+Thin PyTorch-facing layer over the C-ABI of ``include/grid.h``: it only checks
+shapes, allocates outputs with torch and passes device pointers and the current
+CUDA stream. Every step of the computation runs in the CUDA kernels of
+``csrc/``; there is no CPU fallback.
+
+The operations follow Sec. IV-B of the GRiD paper (arXiv 2109.06976):
+RNEA inverse dynamics, the direct inverse of the mass matrix, forward dynamics
+qdd = M^-1 (tau - RNEA(q, qd, 0)) and the analytical gradient of forward
+dynamics [dqdd/dq | dqdd/dqd] = -M^-1 [dID/dq | dID/dqd].
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+from ._native import GRID_FP32, GRID_FP64, GRID_MIXED, GridError  # noqa: F401
+
+__all__ = ["Model", "GridError", "GRID_FP32", "GRID_MIXED", "GRID_FP64", "build"]
+
+_PREC = {"fp32": GRID_FP32, "mixed": GRID_MIXED}
+
+
+def build(verbose: bool = False) -> str:
+    from . import build_ext as _b
+    return _b.build(verbose=verbose)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+class Model:
+    """A robot model resident on the current CUDA device.
+
+    parent [n] (int, -1 = fixed base, parent[i] < i), axis [n, 3] unit joint
+    axes, xtree [n, 12] (E row-major then r), inertia [n, 10] (m, COM, Ic about
+    the COM: xx yy zz xy xz yz), gravity [3]. See include/grid.h.
+    """
+
+    def __init__(self, parent, axis, xtree, inertia, gravity=(0.0, 0.0, -9.81), precision="fp32"):
+        lib = _native.load()
+        self._keep = (_np(parent, np.int32), _np(axis, np.float64), _np(xtree, np.float64),
+                      _np(inertia, np.float64), _np(gravity, np.float64))
+        self.n = int(self._keep[0].shape[0])
+        h = ctypes.c_void_p()
+        _native.check("grid_create", lib.grid_create(
+            self.n, *[a.ctypes.data_as(ctypes.c_void_p) for a in self._keep],
+            _PREC[precision], ctypes.byref(h)))
+        self._h = h
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def from_robot(cls, robot, precision="fp32"):
+        return cls(robot.parent, robot.axis, robot.xtree, robot.inertia, robot.gravity, precision)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_option(self, key: str, value: int):
+        _native.call("grid_set_option", self._h, key.encode(), int(value))
+
+    def set_precision(self, precision: str):
+        self.set_option("precision", _PREC[precision])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.load().grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    def _state(self, *ts):
+        out = []
+        N = None
+        dtype = None
+        for t in ts:
+            if t is None:
+                out.append(None)
+                continue
+            if not (isinstance(t, torch.Tensor) and t.is_cuda):
+                raise TypeError("states must be CUDA tensors")
+            if t.shape[-1] != self.n:
+                raise ValueError(f"last dimension must be n = {self.n}")
+            t2 = t.reshape(-1, self.n).contiguous()
+            if N is None:
+                N, dtype = t2.shape[0], t2.dtype
+            elif t2.shape[0] != N or t2.dtype != dtype:
+                raise ValueError("state tensors must share batch size and dtype")
+            out.append(t2)
+        if dtype not in (torch.float32, torch.float64):
+            raise TypeError("states must be float32 or float64")
+        return N, dtype, out
+
+    @staticmethod
+    def _fn(name, dtype):
+        return name + ("_f64" if dtype == torch.float64 else "")
+
+    @staticmethod
+    def _stream():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    # ------------------------------------------------------------ operations
+    def rnea(self, q, qd, qdd=None, out=None):
+        """tau = ID(q, qd, qdd), [N, n]."""
+        N, dt, (q, qd, qdd) = self._state(q, qd, qdd)
+        tau = out if out is not None else torch.empty((N, self.n), dtype=dt, device=q.device)
+        _native.call(self._fn("grid_rnea", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(tau),
+                     self._stream())
+        return tau
+
+    def minv(self, q, out=None):
+        """M(q)^-1, [N, n, n] (full symmetric)."""
+        N, dt, (q,) = self._state(q)
+        Mi = out if out is not None else torch.empty((N, self.n, self.n), dtype=dt, device=q.device)
+        _native.call(self._fn("grid_minv", dt), self._h, N, _ptr(q), _ptr(Mi), self._stream())
+        return Mi
+
+    def fd(self, q, qd, tau, out=None):
+        """qdd = M^-1 (tau - RNEA(q, qd, 0)), [N, n]."""
+        N, dt, (q, qd, tau) = self._state(q, qd, tau)
+        qdd = out if out is not None else torch.empty((N, self.n), dtype=dt, device=q.device)
+        _native.call(self._fn("grid_fd", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(qdd),
+                     self._stream())
+        return qdd
+
+    def grad_fd(self, q, qd, tau, out=None, qdd_out=None, return_qdd=False):
+        """J = [dqdd/dq | dqdd/dqd], [N, n, 2n]; optionally also qdd [N, n]."""
+        N, dt, (q, qd, tau) = self._state(q, qd, tau)
+        J = out if out is not None else torch.empty((N, self.n, 2 * self.n), dtype=dt, device=q.device)
+        if return_qdd and qdd_out is None:
+            qdd_out = torch.empty((N, self.n), dtype=dt, device=q.device)
+        _native.call(self._fn("grid_grad_fd", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(J),
+                     _ptr(qdd_out), self._stream())
+        return (J, qdd_out) if return_qdd else J

@@ -1,0 +1,238 @@
+// Host-side model construction: validation, depth-first renumbering, device
+// constants and the per-lane schedules of the derivative-column phase.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "grid_internal.h"
+
+static thread_local char g_err[512] = "";
+
+void grid_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* grid_last_error(void) { return g_err; }
+
+namespace {
+
+int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+// Per-knot shared-memory layout, in scalars of `ssize` bytes.
+KnotLayout make_layout(int n, int maxd, int nsk, int ssize) {
+  KnotLayout L;
+  int off = 0;
+  auto take = [&](int count) { int o = off; off += round_up(count, 4); return o; };
+  L.Q = take(n); L.QD = take(n); L.TAU = take(n); L.QDD = take(n); L.CB = take(n);
+  L.X = take(12 * n);
+  L.V = take(6 * n); L.GAM = take(6 * n); L.BET = take(6 * n); L.PHI = take(6 * n);
+  L.UB = take(6 * n);
+  L.DINV = take(ssize == 4 ? 2 * n : n);     // doubles (mixed mode stores them in pairs of floats)
+  L.MINV = take(n * n);
+  L.SK = take(8 * nsk);
+  L.UNION = off;
+  int b = 0;
+  auto tb = [&](int count) { int o = b; b += round_up(count, 4); return o; };
+  L.A = tb(6 * n); L.FO = tb(6 * n); L.FA = tb(6 * n); L.DA = tb(6 * n);
+  L.IAS = tb(36 * maxd); L.IAT = tb(36); L.CT = tb(36); L.FB = tb(6 * n);
+  L.PST = tb(6 * n * maxd);
+  int c = 0;
+  auto tc = [&](int count) { int o = c; c += round_up(count, 4); return o; };
+  L.DC = tc(2 * n * n); L.JS = tc(2 * n * n);
+  off += std::max(b, c);
+  // Knot stride: a multiple of 4 scalars, offset from a multiple of the bank
+  // count so that groups of a warp touching the same field hit other banks.
+  if (ssize == 4) L.stride = round_up(off, 32) + 4;
+  else L.stride = round_up(off, 16) + 4;
+  return L;
+}
+
+struct Unit {            // one root-to-leaf path of one derivative column
+  std::vector<uint32_t> steps;
+};
+
+}  // namespace
+
+grid_status grid_build_model(int n, const int* parent, const double* axis, const double* X_tree,
+                             const double* inertia, const double* gravity,
+                             ModelDev<float>* mf, ModelDev<double>* md) {
+  if (n < 1 || n > GRID_MAX_DOF) {
+    grid_set_error("grid_create: n = %d outside [1, %d]", n, GRID_MAX_DOF);
+    return GRID_E_TOPOLOGY;
+  }
+  if (!parent || !axis || !X_tree || !inertia || !gravity) {
+    grid_set_error("grid_create: null model array");
+    return GRID_E_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (parent[i] < -1 || parent[i] >= i) {
+      grid_set_error("grid_create: parent[%d] = %d violates -1 <= parent[i] < i", i, parent[i]);
+      return GRID_E_TOPOLOGY;
+    }
+    double an = std::sqrt(axis[3 * i] * axis[3 * i] + axis[3 * i + 1] * axis[3 * i + 1] +
+                          axis[3 * i + 2] * axis[3 * i + 2]);
+    if (!(std::fabs(an - 1.0) < 1e-6)) {
+      grid_set_error("grid_create: axis %d has norm %g (must be unit)", i, an);
+      return GRID_E_NUMERIC;
+    }
+    if (!(inertia[10 * i] > 0.0)) {
+      grid_set_error("grid_create: body %d has mass %g (must be > 0)", i, inertia[10 * i]);
+      return GRID_E_NUMERIC;
+    }
+  }
+  // Depth-first preorder: children in caller order, roots in caller order.
+  std::vector<std::vector<int>> kids(n);
+  std::vector<int> roots;
+  for (int i = 0; i < n; ++i) (parent[i] < 0 ? roots : kids[parent[i]]).push_back(i);
+  std::vector<int> perm;          // internal -> caller
+  std::vector<int> stack(roots.rbegin(), roots.rend());
+  while (!stack.empty()) {
+    int b = stack.back();
+    stack.pop_back();
+    perm.push_back(b);
+    for (auto it = kids[b].rbegin(); it != kids[b].rend(); ++it) stack.push_back(*it);
+  }
+  std::vector<int> inv(n);
+  for (int k = 0; k < n; ++k) inv[perm[k]] = k;
+
+  ModelDev<double>& D = *md;
+  std::memset(&D, 0, sizeof(D));
+  D.n = n;
+  std::vector<int> par(n), dep(n), send(n), clo(n), chi(n);
+  for (int k = 0; k < n; ++k) {
+    int p = parent[perm[k]];
+    par[k] = p < 0 ? -1 : inv[p];
+    dep[k] = par[k] < 0 ? 0 : dep[par[k]] + 1;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    send[k] = k + 1;
+    for (int m = k + 1; m < n && dep[m] > dep[k]; ++m) send[k] = m + 1;
+  }
+  int ncomp = 0;
+  for (int k = 0; k < n; ++k) {
+    if (par[k] < 0) { ++ncomp; clo[k] = k; chi[k] = send[k]; }
+    else { clo[k] = clo[par[k]]; chi[k] = chi[par[k]]; }
+  }
+  int maxd = 0, nsk = 0;
+  for (int k = 0; k < n; ++k) {
+    maxd = std::max(maxd, dep[k] + 1);
+    D.skoff[k] = nsk;
+    nsk += dep[k] + 1;
+  }
+  D.maxd = maxd; D.nsk = nsk; D.ncomp = ncomp;
+  for (int k = 0; k < n; ++k) {
+    int c = perm[k];
+    D.parent[k] = par[k]; D.depth[k] = dep[k]; D.sub_end[k] = send[k];
+    D.comp_lo[k] = clo[k]; D.comp_hi[k] = chi[k]; D.perm[k] = c;
+    for (int a = 0; a < 3; ++a) D.axis[k][a] = axis[3 * c + a];
+    bool ident = true;
+    for (int a = 0; a < 9; ++a) {
+      D.ET[k][a] = X_tree[12 * c + a];
+      double e = (a % 4 == 0) ? 1.0 : 0.0;
+      if (X_tree[12 * c + a] != e) ident = false;
+    }
+    D.et_ident[k] = ident ? 1 : 0;
+    for (int a = 0; a < 3; ++a) D.rT[k][a] = X_tree[12 * c + 9 + a];
+    // Spatial inertia about the body origin in compact form: mass m,
+    // first moment h = m c, rotational inertia Ibar = Ic + m (c.c 1 - c c^T).
+    const double* p = inertia + 10 * c;
+    double m = p[0], cx = p[1], cy = p[2], cz = p[3];
+    double cc = cx * cx + cy * cy + cz * cz;
+    D.inert[k][0] = m;
+    D.inert[k][1] = m * cx; D.inert[k][2] = m * cy; D.inert[k][3] = m * cz;
+    D.inert[k][4] = p[4] + m * (cc - cx * cx);
+    D.inert[k][5] = p[5] + m * (cc - cy * cy);
+    D.inert[k][6] = p[6] + m * (cc - cz * cz);
+    D.inert[k][7] = p[7] - m * cx * cy;
+    D.inert[k][8] = p[8] - m * cx * cz;
+    D.inert[k][9] = p[9] - m * cy * cz;
+  }
+  D.a0[0] = D.a0[1] = D.a0[2] = 0.0;
+  D.a0[3] = -gravity[0]; D.a0[4] = -gravity[1]; D.a0[5] = -gravity[2];
+
+  // Derivative-column work units: every root-to-leaf path of subtree(j), for
+  // u in {q, qd} and every joint j. The first path through a body owns it.
+  std::vector<Unit> units;
+  for (int u = 0; u < 2; ++u)
+    for (int j = 0; j < n; ++j) {
+      std::vector<char> owned(n, 0);
+      for (int leaf = j; leaf < send[j]; ++leaf) {
+        bool is_leaf = (leaf + 1 >= send[j]) || dep[leaf + 1] <= dep[leaf];
+        if (!is_leaf) continue;
+        std::vector<int> path;
+        for (int b = leaf; b != par[j]; b = par[b]) path.push_back(b);
+        std::reverse(path.begin(), path.end());
+        Unit un;
+        for (size_t s = 0; s < path.size(); ++s) {
+          int b = path[s];
+          uint32_t d = (uint32_t)b | ((uint32_t)(u * n + j) << 5) | STEP_VALID;
+          if (s == 0) d |= STEP_RESET | STEP_ROOT;
+          if (!owned[b]) { d |= STEP_OWNED; owned[b] = 1; }
+          if (s + 1 == path.size()) d |= STEP_FLUSH;
+          if (u == 0) d |= STEP_UQ;
+          un.steps.push_back(d);
+        }
+        units.push_back(un);
+      }
+    }
+  // Longest-processing-time assignment of paths to lanes, per lane count.
+  std::vector<int> order(units.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return units[a].steps.size() > units[b].steps.size(); });
+  int soff = 0;
+  const int lanes_cfg[GRID_NUM_LANE_CFG] = {8, 16, 32};
+  for (int c = 0; c < GRID_NUM_LANE_CFG; ++c) {
+    int T = lanes_cfg[c];
+    std::vector<std::vector<uint32_t>> lane(T);
+    for (int ui : order) {
+      int best = 0;
+      for (int l = 1; l < T; ++l)
+        if (lane[l].size() < lane[best].size()) best = l;
+      lane[best].insert(lane[best].end(), units[ui].steps.begin(), units[ui].steps.end());
+    }
+    int S = 0;
+    for (auto& v : lane) S = std::max(S, (int)v.size());
+    if (soff + S * T > GRID_SCHED_MAX) {
+      grid_set_error("grid_create: derivative schedule too large (%d steps)", soff + S * T);
+      return GRID_E_TOPOLOGY;
+    }
+    D.steps[c] = S;
+    D.sched_off[c] = soff;
+    for (int s = 0; s < S; ++s)
+      for (int l = 0; l < T; ++l)
+        D.sched[soff + s * T + l] = s < (int)lane[l].size() ? lane[l][s] : 0u;
+    soff += S * T;
+  }
+  D.L = make_layout(n, maxd, nsk, 8);
+
+  // Float copy of everything; its own layout.
+  ModelDev<float>& F = *mf;
+  std::memset(&F, 0, sizeof(F));
+  F.n = D.n; F.maxd = D.maxd; F.nsk = D.nsk; F.ncomp = D.ncomp;
+  std::memcpy(F.steps, D.steps, sizeof(D.steps));
+  std::memcpy(F.sched_off, D.sched_off, sizeof(D.sched_off));
+  std::memcpy(F.parent, D.parent, sizeof(D.parent));
+  std::memcpy(F.depth, D.depth, sizeof(D.depth));
+  std::memcpy(F.sub_end, D.sub_end, sizeof(D.sub_end));
+  std::memcpy(F.comp_lo, D.comp_lo, sizeof(D.comp_lo));
+  std::memcpy(F.comp_hi, D.comp_hi, sizeof(D.comp_hi));
+  std::memcpy(F.perm, D.perm, sizeof(D.perm));
+  std::memcpy(F.skoff, D.skoff, sizeof(D.skoff));
+  std::memcpy(F.et_ident, D.et_ident, sizeof(D.et_ident));
+  std::memcpy(F.sched, D.sched, sizeof(D.sched));
+  for (int k = 0; k < GRID_MAX_DOF; ++k) {
+    for (int a = 0; a < 3; ++a) { F.axis[k][a] = (float)D.axis[k][a]; F.rT[k][a] = (float)D.rT[k][a]; }
+    for (int a = 0; a < 9; ++a) F.ET[k][a] = (float)D.ET[k][a];
+    for (int a = 0; a < 10; ++a) F.inert[k][a] = (float)D.inert[k][a];
+  }
+  for (int a = 0; a < 6; ++a) F.a0[a] = (float)D.a0[a];
+  F.L = make_layout(n, maxd, nsk, 4);
+  return GRID_OK;
+}

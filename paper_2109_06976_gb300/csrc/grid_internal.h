@@ -1,0 +1,95 @@
+// Internal model representation shared by the host builder and the kernels.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/grid.h"
+
+#ifdef __CUDACC__
+#define GRID_HD __host__ __device__
+#else
+#define GRID_HD
+#endif
+
+#define GRID_SCHED_MAX 4096    // step descriptors for all lane counts together
+#define GRID_NUM_LANE_CFG 3    // lanes per knot point: 8, 16, 32
+
+// Column-phase step descriptor (one uint32 per lane per step).
+//   bits 0-4   body k (internal numbering)
+//   bits 5-10  output column (u * n + j)
+//   bit 11     RESET: first step of a path, parent derivatives are zero
+//   bit 12     ROOT: body k is the column's joint j (case terms of Alg. 1)
+//   bit 13     OWNED: first path through k; its force derivative is counted
+//   bit 14     FLUSH: last step of a path; accumulators are written out
+//   bit 15     UQ: column is d/dq_j (else d/dqd_j)
+//   bit 16     VALID: real work (padding steps have it clear)
+#define STEP_BODY(s) ((int)((s) & 31u))
+#define STEP_COL(s) ((int)(((s) >> 5) & 63u))
+#define STEP_RESET (1u << 11)
+#define STEP_ROOT (1u << 12)
+#define STEP_OWNED (1u << 13)
+#define STEP_FLUSH (1u << 14)
+#define STEP_UQ (1u << 15)
+#define STEP_VALID (1u << 16)
+
+// Offsets (in scalars) of the per-knot shared-memory workspace.
+struct KnotLayout {
+  int Q, QD, TAU, QDD, CB;      // staged q, qd, tau (or qdd input), qdd, bias / tau out
+  int X;                        // per body E(9) r(3)
+  int V, GAM, BET, PHI;         // per body 6: v, gamma = I v, beta = (X a_parent) x S, phi = S x* F
+  int UB, DINV;                 // per body U_i (6) and D_i^-1 (stored as 2 scalars when mixed)
+  int MINV;                     // n x n
+  int SK;                       // ancestor subspaces s_i^(k), 8 scalars per row
+  int UNION;                    // start of the phase-dependent area
+  // phase B (dynamics, M^-1) temporaries, relative to UNION
+  int A, FO, FA, DA;            // per body 6: accelerations, own forces, accumulated forces, qdd-accel
+  int IAS, IAT, CT, FB, PST;    // IA depth stack (36 per slot), IA of current body, congruence temp, F buffer (6 x n), P stack (6 x n per depth)
+  // phase C/D temporaries, relative to UNION
+  int DC, JS;                   // dc [n][2n], J staging [n][2n] (caller order)
+  int stride;                   // scalars per knot
+};
+
+template <class S>
+struct ModelDev {
+  int n, maxd, nsk, ncomp;
+  int steps[GRID_NUM_LANE_CFG];      // steps per lane for 8, 16, 32 lanes
+  int sched_off[GRID_NUM_LANE_CFG];  // offsets into sched
+  KnotLayout L;
+  int parent[GRID_MAX_DOF];
+  int depth[GRID_MAX_DOF];
+  int sub_end[GRID_MAX_DOF];
+  int comp_lo[GRID_MAX_DOF];
+  int comp_hi[GRID_MAX_DOF];
+  int perm[GRID_MAX_DOF];        // internal body -> caller index
+  int skoff[GRID_MAX_DOF];       // first sK row of body k
+  int et_ident[GRID_MAX_DOF];
+  S axis[GRID_MAX_DOF][3];
+  S ET[GRID_MAX_DOF][9];
+  S rT[GRID_MAX_DOF][3];
+  S inert[GRID_MAX_DOF][10];     // m, h = m c (3), Ibar about the origin: xx yy zz xy xz yz
+  S a0[6];                       // base acceleration -g
+  uint32_t sched[GRID_SCHED_MAX];
+};
+
+// Bytes of ModelDev that every CTA copies into shared memory (everything but
+// the schedules, whose lane-count slice is copied separately).
+template <class S>
+GRID_HD constexpr int model_head_bytes() { return (int)(sizeof(ModelDev<S>) - sizeof(uint32_t) * GRID_SCHED_MAX); }
+
+struct grid_model {
+  int n;
+  int device;
+  grid_precision prec;
+  int lanes_opt;
+  int ctas_opt;
+  ModelDev<float>* dev_f;        // device copies
+  ModelDev<double>* dev_d;
+  ModelDev<float>* host_f;       // host mirrors (for launch decisions)
+  ModelDev<double>* host_d;
+};
+
+// Host helpers (grid_host.cpp)
+void grid_set_error(const char* fmt, ...);
+grid_status grid_build_model(int n, const int* parent, const double* axis, const double* X_tree,
+                             const double* inertia, const double* gravity,
+                             ModelDev<float>* mf, ModelDev<double>* md);

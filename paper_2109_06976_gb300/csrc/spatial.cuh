@@ -1,0 +1,131 @@
+// Compact spatial algebra for the kernels. Spatial vectors are [angular; linear]
+// (the ordering of Eq. (2)). A transform iX_lambda is held as (E, r):
+// X = [E 0; -E r~ E], so X m = [E w; E (v - r x w)] and
+// X^T f = [E^T n + r x (E^T f); E^T f]. A spatial inertia is held as
+// (m, h = m c, Ibar): I m = [Ibar w + h x v; m v - h x w].
+#pragma once
+
+template <class S>
+__device__ __forceinline__ void cross3(const S* a, const S* b, S* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// o = X m
+template <class S>
+__device__ __forceinline__ void x_mul(const S* E, const S* r, const S* m, S* o) {
+  S t0 = m[3] - (r[1] * m[2] - r[2] * m[1]);
+  S t1 = m[4] - (r[2] * m[0] - r[0] * m[2]);
+  S t2 = m[5] - (r[0] * m[1] - r[1] * m[0]);
+  o[0] = E[0] * m[0] + E[1] * m[1] + E[2] * m[2];
+  o[1] = E[3] * m[0] + E[4] * m[1] + E[5] * m[2];
+  o[2] = E[6] * m[0] + E[7] * m[1] + E[8] * m[2];
+  o[3] = E[0] * t0 + E[1] * t1 + E[2] * t2;
+  o[4] = E[3] * t0 + E[4] * t1 + E[5] * t2;
+  o[5] = E[6] * t0 + E[7] * t1 + E[8] * t2;
+}
+
+// o = X^T f
+template <class S>
+__device__ __forceinline__ void xt_mul(const S* E, const S* r, const S* f, S* o) {
+  S g0 = E[0] * f[3] + E[3] * f[4] + E[6] * f[5];
+  S g1 = E[1] * f[3] + E[4] * f[4] + E[7] * f[5];
+  S g2 = E[2] * f[3] + E[5] * f[4] + E[8] * f[5];
+  S n0 = E[0] * f[0] + E[3] * f[1] + E[6] * f[2];
+  S n1 = E[1] * f[0] + E[4] * f[1] + E[7] * f[2];
+  S n2 = E[2] * f[0] + E[5] * f[1] + E[8] * f[2];
+  o[0] = n0 + (r[1] * g2 - r[2] * g1);
+  o[1] = n1 + (r[2] * g0 - r[0] * g2);
+  o[2] = n2 + (r[0] * g1 - r[1] * g0);
+  o[3] = g0; o[4] = g1; o[5] = g2;
+}
+
+// o = I m with I = (m, h, Ibar); inert = {m, h0, h1, h2, Ixx, Iyy, Izz, Ixy, Ixz, Iyz}
+template <class S>
+__device__ __forceinline__ void i_mul(const S* in, const S* m, S* o) {
+  const S mass = in[0], h0 = in[1], h1 = in[2], h2 = in[3];
+  o[0] = in[4] * m[0] + in[7] * m[1] + in[8] * m[2] + (h1 * m[5] - h2 * m[4]);
+  o[1] = in[7] * m[0] + in[5] * m[1] + in[9] * m[2] + (h2 * m[3] - h0 * m[5]);
+  o[2] = in[8] * m[0] + in[9] * m[1] + in[6] * m[2] + (h0 * m[4] - h1 * m[3]);
+  o[3] = mass * m[3] - (h1 * m[2] - h2 * m[1]);
+  o[4] = mass * m[4] - (h2 * m[0] - h0 * m[2]);
+  o[5] = mass * m[5] - (h0 * m[1] - h1 * m[0]);
+}
+
+// o = a x b (motion cross product, Eq. (2))
+template <class S>
+__device__ __forceinline__ void crm_mul(const S* a, const S* b, S* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+  o[3] = a[1] * b[5] - a[2] * b[4] + a[4] * b[2] - a[5] * b[1];
+  o[4] = a[2] * b[3] - a[0] * b[5] + a[5] * b[0] - a[3] * b[2];
+  o[5] = a[0] * b[4] - a[1] * b[3] + a[3] * b[1] - a[4] * b[0];
+}
+
+// o = a x* f = -(a x)^T f (force cross product, Eq. (2))
+template <class S>
+__device__ __forceinline__ void crf_mul(const S* a, const S* f, S* o) {
+  o[0] = a[1] * f[2] - a[2] * f[1] + a[4] * f[5] - a[5] * f[4];
+  o[1] = a[2] * f[0] - a[0] * f[2] + a[5] * f[3] - a[3] * f[5];
+  o[2] = a[0] * f[1] - a[1] * f[0] + a[3] * f[4] - a[4] * f[3];
+  o[3] = a[1] * f[5] - a[2] * f[4];
+  o[4] = a[2] * f[3] - a[0] * f[5];
+  o[5] = a[0] * f[4] - a[1] * f[3];
+}
+
+// Component c (0..5) of X m, reading operands from memory.
+template <class S>
+__device__ __forceinline__ S x_mul_c(const S* E, const S* r, const S* m, int c) {
+  if (c < 3) return E[3 * c] * m[0] + E[3 * c + 1] * m[1] + E[3 * c + 2] * m[2];
+  const int k = c - 3;
+  S t0 = m[3] - (r[1] * m[2] - r[2] * m[1]);
+  S t1 = m[4] - (r[2] * m[0] - r[0] * m[2]);
+  S t2 = m[5] - (r[0] * m[1] - r[1] * m[0]);
+  return E[3 * k] * t0 + E[3 * k + 1] * t1 + E[3 * k + 2] * t2;
+}
+
+// Component c of X^T f.
+template <class S>
+__device__ __forceinline__ S xt_mul_c(const S* E, const S* r, const S* f, int c) {
+  S g0 = E[0] * f[3] + E[3] * f[4] + E[6] * f[5];
+  S g1 = E[1] * f[3] + E[4] * f[4] + E[7] * f[5];
+  S g2 = E[2] * f[3] + E[5] * f[4] + E[8] * f[5];
+  if (c >= 3) return c == 3 ? g0 : (c == 4 ? g1 : g2);
+  S n = E[c] * f[0] + E[3 + c] * f[1] + E[6 + c] * f[2];
+  const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+  const S g[3] = {g0, g1, g2};
+  return n + (r[c1] * g[c2] - r[c2] * g[c1]);
+}
+
+// Component c of I m.
+template <class S>
+__device__ __forceinline__ S i_mul_c(const S* in, const S* m, int c) {
+  S o[6];
+  i_mul(in, m, o);
+  S x = o[0];
+#pragma unroll
+  for (int k = 1; k < 6; ++k) x = (c == k) ? o[k] : x;
+  return x;
+}
+
+// Entry (r, c) of the 6x6 spatial inertia matrix.
+template <class S>
+__device__ __forceinline__ S i_entry(const S* in, int r, int c) {
+  const S h[3] = {in[1], in[2], in[3]};
+  if (r < 3 && c < 3) {
+    if (r == c) return in[4 + r];
+    int a = r < c ? r : c, b = r < c ? c : r;          // (0,1)->7, (0,2)->8, (1,2)->9
+    return in[a == 0 ? (b == 1 ? 7 : 8) : 9];
+  }
+  if (r >= 3 && c >= 3) return r == c ? in[0] : S(0);
+  // upper-right block h~, lower-left block h~^T
+  int i = r < 3 ? r : c, j = r < 3 ? c - 3 : r - 3;     // entry (i, j) of h~
+  S v;
+  if (i == j) v = S(0);
+  else if (i == 0) v = (j == 1) ? -h[2] : h[1];
+  else if (i == 1) v = (j == 0) ? h[2] : -h[0];
+  else v = (j == 0) ? -h[1] : h[0];
+  return v;
+}

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on the
+same seeded inputs. FP32 bar: 1e-4 per-column relative error (tests/metrics.py)
+on the workload robots; FP64: 1e-10 on every robot."""
+import numpy as np
+import pytest
+
+import grid_inputs as gi
+import oracle
+from tests.metrics import col_rel_err, col_rel_err_stats, vec_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WORKLOAD = ["chain7", "tree12", "tree30"]
+RANDOM = [(3, 2), (6, 4), (9, 8), (13, 21), (1, 5)]
+TOL32 = 1e-4
+TOL64 = 1e-10
+
+
+def _robot(key):
+    if isinstance(key, str):
+        return gi.robot(key)
+    return gi.random_tree(*key)
+
+
+@pytest.fixture(scope="module")
+def grid():
+    import paper_2109_06976_gb300 as g
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return g
+
+
+_models = {}
+
+
+def _model(grid, key, precision="fp32"):
+    k = (str(key), precision)
+    if k not in _models:
+        _models[k] = grid.Model.from_robot(_robot(key), precision=precision)
+    return _models[k]
+
+
+def _inputs(n, N, seed, dtype):
+    q, qd, tau = gi.states(n, N, seed)
+    npdt = np.float32 if dtype == torch.float32 else np.float64
+    q, qd, tau = (x.astype(npdt) for x in (q, qd, tau))
+    dev = [torch.from_numpy(x).cuda() for x in (q, qd, tau)]
+    host64 = [x.astype(np.float64) for x in (q, qd, tau)]
+    return dev, host64
+
+
+def _floor(key, dtype):
+    return 1e-6 if (isinstance(key, str) or dtype == torch.float64) else 1e-4
+
+
+CASES = [(k, dt) for k in WORKLOAD for dt in (torch.float32, torch.float64)] + \
+        [(k, torch.float64) for k in RANDOM] + [(k, torch.float32) for k in RANDOM]
+
+
+@pytest.mark.parametrize("key,dtype", CASES, ids=lambda x: str(x))
+@pytest.mark.parametrize("N", [1, 37])
+def test_all_outputs_match_oracle(grid, key, dtype, N):
+    r = _robot(key)
+    m = _model(grid, key)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, N, 1000 + N, dtype)
+    tol = TOL32 if dtype == torch.float32 else TOL64
+    fl = _floor(key, dtype)
+    # RNEA with qdd = tau values as accelerations, and with qdd = 0 (NULL)
+    e = vec_rel_err(m.rnea(q, qd, tau).cpu().numpy(), oracle.rnea(r, q64, qd64, tau64), fl)
+    assert e <= tol, f"rnea {e}"
+    e = vec_rel_err(m.rnea(q, qd).cpu().numpy(), oracle.rnea(r, q64, qd64, 0 * qd64), fl)
+    assert e <= tol, f"rnea(qdd=0) {e}"
+    Mi = m.minv(q).cpu().numpy()
+    e = col_rel_err(Mi, oracle.minv(r, q64), fl)
+    assert e <= tol, f"minv {e}"
+    np.testing.assert_array_equal(Mi, np.swapaxes(Mi, 1, 2))      # exactly symmetric output
+    qdd_ref = oracle.fd(r, q64, qd64, tau64)
+    e = vec_rel_err(m.fd(q, qd, tau).cpu().numpy(), qdd_ref, fl)
+    assert e <= tol, f"fd {e}"
+    J, qdd = m.grad_fd(q, qd, tau, return_qdd=True)
+    e = col_rel_err(J.cpu().numpy(), oracle.grad_fd(r, q64, qd64, tau64), fl)
+    assert e <= tol, f"grad_fd {e}"
+    e = vec_rel_err(qdd.cpu().numpy(), qdd_ref, fl)
+    assert e <= tol, f"grad_fd qdd {e}"
+
+
+@pytest.mark.parametrize("key", WORKLOAD)
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+def test_lane_counts_agree(grid, key, lanes):
+    """Every cooperative mapping gives the oracle's result (ragged N spanning
+    several tiles)."""
+    r = _robot(key)
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", lanes)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, 29, 7, torch.float64)
+    J = m.grad_fd(q, qd, tau).cpu().numpy()
+    assert col_rel_err(J, oracle.grad_fd(r, q64, qd64, tau64)) <= TOL64
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, 29, 7, torch.float32)
+    J = m.grad_fd(q, qd, tau).cpu().numpy()
+    assert col_rel_err(J, oracle.grad_fd(r, q64, qd64, tau64)) <= TOL32
+
+
+@pytest.mark.parametrize("key", WORKLOAD)
+def test_grad_fd_workload_sizes(grid, key):
+    """The workload batch sizes (N = 16 .. 1024) in one call each."""
+    r = _robot(key)
+    m = _model(grid, key)
+    for N in (16, 128, 512) if key != "tree30" else (128, 1024):
+        (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, N, gi.workload_seed(2, N), torch.float32)
+        J = m.grad_fd(q, qd, tau).cpu().numpy()
+        mx, p50 = col_rel_err_stats(J, oracle.grad_fd(r, q64, qd64, tau64, nthreads=8))
+        assert mx <= TOL32, (N, mx, p50)
+
+
+def test_grad_fd_bench_size_sampled(grid):
+    """The benchmark's launch (7-DoF chain, 4096 trajectories x 128 knot points
+    in one call) checked on 256 sampled knot points."""
+    r = gi.chain7()
+    m = _model(grid, "chain7")
+    N = 4096 * 128
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(7, N, gi.workload_seed(2, 128), torch.float32)
+    J = m.grad_fd(q, qd, tau)
+    torch.cuda.synchronize()
+    idx = np.sort(gi.Stream(5).u64(256) % np.uint64(N)).astype(np.int64)
+    Js = J[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = oracle.grad_fd(r, q64[idx], qd64[idx], tau64[idx], nthreads=8)
+    assert col_rel_err(Js, ref) <= TOL32
+    assert torch.isfinite(J).all()
+
+
+def test_mixed_precision_tree30(grid):
+    """FP64 pivots in the M^-1 recursion: parity holds and the error is
+    reported next to the all-FP32 form."""
+    r = gi.tree30()
+    m32 = _model(grid, "tree30")
+    mm = _model(grid, "tree30", "mixed")
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(30, 128, gi.workload_seed(3, 128), torch.float32)
+    ref = oracle.grad_fd(r, q64, qd64, tau64, nthreads=8)
+    e32 = col_rel_err(m32.grad_fd(q, qd, tau).cpu().numpy(), ref)
+    emx = col_rel_err(mm.grad_fd(q, qd, tau).cpu().numpy(), ref)
+    assert e32 <= TOL32 and emx <= TOL32, (e32, emx)
+
+
+def test_empty_batch_and_errors(grid):
+    r = gi.chain7()
+    m = _model(grid, "chain7")
+    z = torch.empty((0, 7), device="cuda")
+    assert m.grad_fd(z, z, z).shape == (0, 7, 14)
+    q = torch.zeros((4, 7), device="cuda")
+    with pytest.raises(grid.GridError):
+        grid._native.call("grid_fd", m.handle, 4, None, None, None, None, None)
+    buf = torch.zeros(64, device="cuda")
+    import ctypes
+    mis = ctypes.c_void_p(buf.data_ptr() + 2)
+    with pytest.raises(grid.GridError) as ei:
+        grid._native.call("grid_fd", m.handle, 1, mis, mis, mis, mis, None)
+    assert ei.value.status == 3
+    with pytest.raises(grid.GridError):
+        grid.Model([-1, 1], np.eye(3)[:2], r.xtree[:2], r.inertia[:2])
+    bad_axis = r.axis.copy()
+    bad_axis[0] *= 2
+    with pytest.raises(grid.GridError):
+        grid.Model(r.parent, bad_axis, r.xtree, r.inertia)
+    del q
+
+
+def test_permuted_numbering(grid):
+    """A robot given in non-depth-first order (legs interleaved) is renumbered
+    internally; results come back in the caller's order."""
+    r = gi.tree12()
+    perm = np.array([0, 3, 6, 9, 1, 4, 7, 10, 2, 5, 8, 11])   # breadth-first order
+    rp = r.permuted(perm)
+    m = grid.Model.from_robot(rp)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(12, 9, 11, torch.float64)
+    J = m.grad_fd(q, qd, tau).cpu().numpy()
+    assert col_rel_err(J, oracle.grad_fd(rp, q64, qd64, tau64)) <= TOL64
+    Mi = m.minv(q).cpu().numpy()
+    assert col_rel_err(Mi, oracle.minv(rp, q64)) <= TOL64
+
+
+def test_repeatable(grid):
+    r = gi.tree12()
+    m = _model(grid, "tree12")
+    (q, qd, tau), _ = _inputs(12, 300, 3, torch.float32)
+    a = m.grad_fd(q, qd, tau)
+    b = m.grad_fd(q, qd, tau)
+    assert torch.equal(a, b)
