@@ -1,0 +1,337 @@
+"""Throughput benchmark of the batched gradient of forward dynamics.
+
+One step = one pass of the whole path (joint transforms, RNEA(q, qd, 0), direct
+M^-1, FD, RNEA at qdd, analytical RNEA derivatives, -M^-1 dID) over one batch:
+B trajectories x 128 knot points of the 7-DoF chain in FP32, inputs already
+resident in HBM. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on the host cores on a bounded sample of the same workload.
+Under torchrun every rank processes its own B trajectories (weak scaling, no
+collective on the data path); value = all knot points / max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import grid_inputs as gi  # noqa: E402
+
+METRIC = "∇FD knot-points/sec at N=128 (FP32/mixed vs FP64 plain); serve p50/p99 ms"
+UNIT = "knot-points/s"
+KNOTS = 128                      # knot points per trajectory (the metric's N)
+TRAJ = 16384                     # trajectories per step (2,097,152 knot points)
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+L2_BYTES = 129 * 1024 * 1024
+# FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
+# lanes x 2 flops (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM bytes per knot point of the gradient kernel from an ncu capture, keyed
+# by a hash of the kernel sources; absent when the kernel changed since.
+NCU_DRAM_BYTES_PER_KNOT = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2109_06976_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return dist.get_rank(), dist.get_world_size(), local, dist
+
+
+def time_steps(fn, steps, warmup, stream, dist=None):
+    """W untimed steps, then K steps bracketed by barrier + synchronize; CUDA
+    events on the launching stream. Returns (seconds, max over ranks)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    if dist:
+        t = torch.tensor([sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    return sec
+
+
+def cpu_oracle_rate(robot, seconds_min=10.0, seconds_max=30.0, threads=None):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the
+    workload: repeated batches of 128-knot trajectories until >= seconds_min."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    n = robot.n
+    q, qd, tau = gi.states(n, 64 * KNOTS, gi.workload_seed(2, KNOTS))
+    oracle.grad_fd(robot, q[:KNOTS], qd[:KNOTS], tau[:KNOTS], nthreads=threads)   # warm
+    done, t0 = 0, time.perf_counter()
+    batch = 4 * KNOTS
+    while True:
+        s = (done // batch) % 16
+        sl = slice(s * batch, (s + 1) * batch)
+        oracle.grad_fd(robot, q[sl], qd[sl], tau[sl], nthreads=threads)
+        done += batch
+        el = time.perf_counter() - t0
+        if el >= seconds_min or el >= seconds_max:
+            break
+    return done / el, threads, done, el
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    robot = gi.chain7()
+    threads = os.cpu_count() or 1
+    per_step = 128 * KNOTS          # bounded sample: 128 trajectories x 128 knot points
+    q, qd, tau = gi.states(7, per_step, gi.workload_seed(2, KNOTS))
+    for _ in range(args.warmup):
+        oracle.grad_fd(robot, q, qd, tau, nthreads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.grad_fd(robot, q, qd, tau, nthreads=threads)
+    el = time.perf_counter() - t0
+    v = per_step * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded 7-DoF chain, uniform states)",
+        "config": {"workload": "7-DoF chain, trajectories of 128 knot points, FP64 CPU oracle; "
+                               "each step a 16,384-knot-point sample of the GPU step's batch",
+                   "robot": "chain7", "knot_points_per_step": per_step},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} knot points per step x {args.steps} steps"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2109_06976_gb300 as grid
+    from paper_2109_06976_gb300.flops import grad_fd_flops_per_knot
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    robot = gi.chain7()
+    model = grid.Model.from_robot(robot)
+    n = robot.n
+    Nk = TRAJ * KNOTS
+    seed = gi.workload_seed(2, KNOTS) + 7919 * rank
+    q, qd, tau = (torch.from_numpy(x.astype(np.float32)).cuda()
+                  for x in gi.states(n, Nk, seed))
+    J = torch.empty((Nk, n, 2 * n), device="cuda")
+    in_bytes = 3 * Nk * n * 4
+    out_bytes = Nk * 2 * n * n * 4
+
+    def step():
+        model.grad_fd(q, qd, tau, out=J)
+
+    with ClockSampler(local) as clk:
+        sec = time_steps(step, args.steps, args.warmup, stream, dist)
+    clocks = clk.summary()
+    ms = sec / args.steps * 1e3
+    value = world * Nk * args.steps / sec
+    flops_knot = grad_fd_flops_per_knot(robot.parent)
+    achieved_tflops = flops_knot * Nk / (ms / 1e3) / 1e12
+    dram = NCU_DRAM_BYTES_PER_KNOT.get(kernel_source_hash())
+
+    # End to end through the public API with pinned host buffers: H2D of the
+    # step's states, the kernel, D2H of the Jacobians, every step.
+    hq, hqd, htau = (t.cpu().pin_memory() for t in (q, qd, tau))
+    hJ = torch.empty(J.shape, dtype=J.dtype).pin_memory()
+    dq, dqd, dtau = torch.empty_like(q), torch.empty_like(qd), torch.empty_like(tau)
+
+    def e2e_step():
+        dq.copy_(hq, non_blocking=True)
+        dqd.copy_(hqd, non_blocking=True)
+        dtau.copy_(htau, non_blocking=True)
+        model.grad_fd(dq, dqd, dtau, out=J)
+        hJ.copy_(J, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 4)
+    sec_e2e = time_steps(e2e_step, e2e_steps, 2, stream, dist)
+    e2e_value = world * Nk * e2e_steps / sec_e2e
+
+    # FP64 plain form on the same GPU (smaller batch, same per-knot work)
+    Nd = 256 * KNOTS
+    q64, qd64, tau64 = (x[:Nd].double() for x in (q, qd, tau))
+    J64 = torch.empty((Nd, n, 2 * n), device="cuda", dtype=torch.float64)
+    sec64 = time_steps(lambda: model.grad_fd(q64, qd64, tau64, out=J64), 5, 2, stream, dist)
+    fp64_value = world * Nd * 5 / sec64
+
+    # 12-DoF tree at the same N and batch
+    t12 = gi.tree12()
+    m12 = grid.Model.from_robot(t12)
+    q12, qd12, tau12 = (torch.from_numpy(x.astype(np.float32)).cuda()
+                        for x in gi.states(12, Nk // 2, seed + 1))
+    J12 = torch.empty((Nk // 2, 12, 24), device="cuda")
+    sec12 = time_steps(lambda: m12.grad_fd(q12, qd12, tau12, out=J12), max(3, args.steps // 4), 2,
+                       stream, dist)
+    t12_value = world * (Nk // 2) * max(3, args.steps // 4) / sec12
+
+    # single-trajectory latency at N = 128 (compute only)
+    q1, qd1, tau1 = q[:KNOTS], qd[:KNOTS], tau[:KNOTS]
+    J1 = J[:KNOTS]
+    sec1 = time_steps(lambda: model.grad_fd(q1, qd1, tau1, out=J1), 200, 20, stream, None)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, threads, done, el = cpu_oracle_rate(robot)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{done} knot points of 128-knot trajectories in {el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded 7-DoF chain, q~U[-pi,pi], qd~U[-1,1], tau~U[-5,5])",
+            "config": {
+                "workload": f"7-DoF chain, {TRAJ} trajectories x {KNOTS} knot points per step "
+                            f"({Nk} knot points), FP32, grad FD",
+                "robot": "chain7", "trajectories_per_gpu": TRAJ, "knot_points_per_trajectory": KNOTS,
+                "l2": f"inputs {in_bytes / 1e6:.0f} MB and outputs {out_bytes / 1e6:.0f} MB per "
+                      f"step, both larger than the 129 MB L2",
+                "parallelism": f"dp{world}"},
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
+                         "traffic": None if dram is None else dram * Nk,
+                         "flops_per_knot": flops_knot,
+                         "peak_note": "FP32 from 152 SMs x 128 lanes x 2 x 2070 MHz",
+                         "hbm_gbs": (in_bytes + out_bytes) / (ms / 1e3) / 1e9},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
+                    "d2h_bytes_per_step": out_bytes},
+            "fp64_plain": {"value": fp64_value, "unit": UNIT, "knot_points_per_launch": Nd},
+            "tree12": {"value": t12_value, "unit": UNIT, "knot_points_per_launch": Nk // 2},
+            "latency_n128_us": sec1 / 200 * 1e6,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": args.steps,
+            "kernel_source": kernel_source_hash(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    model.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
