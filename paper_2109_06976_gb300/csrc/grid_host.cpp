@@ -25,27 +25,30 @@ namespace {
 int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 // Per-knot shared-memory layout, in scalars of `ssize` bytes.
-KnotLayout make_layout(int n, int maxd, int nsk, int ssize) {
+KnotLayout make_layout(int n, int nsk, int nbranch, int ssize) {
   KnotLayout L;
   int off = 0;
   auto take = [&](int count) { int o = off; off += round_up(count, 4); return o; };
   L.Q = take(n); L.QD = take(n); L.TAU = take(n); L.QDD = take(n); L.CB = take(n);
   L.X = take(12 * n);
   L.V = take(6 * n); L.GAM = take(6 * n); L.BET = take(6 * n); L.PHI = take(6 * n);
-  L.UB = take(6 * n);
-  L.DINV = take(ssize == 4 ? 2 * n : n);     // doubles (mixed mode stores them in pairs of floats)
   L.MINV = take(n * n);
   L.SK = take(8 * nsk);
   L.UNION = off;
   int b = 0;
   auto tb = [&](int count) { int o = b; b += round_up(count, 4); return o; };
-  L.A = tb(6 * n); L.FO = tb(6 * n); L.FA = tb(6 * n); L.DA = tb(6 * n);
-  L.IAS = tb(36 * maxd); L.IAT = tb(36); L.CT = tb(36); L.FB = tb(6 * n);
-  L.PST = tb(6 * n * maxd);
+  L.UB = tb(6 * n);
+  L.DINV = tb(ssize == 4 ? 2 * n : n);     // doubles (mixed mode stores them in pairs of floats)
+  L.CT = tb(36);
+  L.BIA = tb(36 * nbranch);
+  L.BP = tb(6 * n * nbranch);
+  int r = 0;
+  auto tr = [&](int count) { int o = r; r += round_up(count, 4); return o; };
+  L.A = tr(6 * n); L.FO = tr(6 * n); L.FA = tr(6 * n);
   int c = 0;
   auto tc = [&](int count) { int o = c; c += round_up(count, 4); return o; };
   L.DC = tc(2 * n * n); L.JS = tc(2 * n * n);
-  off += std::max(b, c);
+  off += std::max(b, std::max(r, c));
   // Knot stride: a multiple of 4 scalars, offset from a multiple of the bank
   // count so that groups of a warp touching the same field hit other banks.
   if (ssize == 4) L.stride = round_up(off, 32) + 4;
@@ -119,13 +122,16 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
     if (par[k] < 0) { ++ncomp; clo[k] = k; chi[k] = send[k]; }
     else { clo[k] = clo[par[k]]; chi[k] = chi[par[k]]; }
   }
-  int maxd = 0, nsk = 0;
+  int maxd = 0, nsk = 0, nbranch = 0;
   for (int k = 0; k < n; ++k) {
     maxd = std::max(maxd, dep[k] + 1);
     D.skoff[k] = nsk;
-    nsk += dep[k] + 1;
+    nsk += dep[k] + 2;                      // ancestor subspaces and the gravity row
+    int nk = 0;
+    for (int m = k + 1; m < n; ++m) nk += par[m] == k;
+    D.branch[k] = nk >= 2 ? nbranch++ : -1;
   }
-  D.maxd = maxd; D.nsk = nsk; D.ncomp = ncomp;
+  D.maxd = maxd; D.nsk = nsk; D.ncomp = ncomp; D.nbranch = nbranch;
   for (int k = 0; k < n; ++k) {
     int c = perm[k];
     D.parent[k] = par[k]; D.depth[k] = dep[k]; D.sub_end[k] = send[k];
@@ -210,12 +216,12 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
         D.sched[soff + s * T + l] = s < (int)lane[l].size() ? lane[l][s] : 0u;
     soff += S * T;
   }
-  D.L = make_layout(n, maxd, nsk, 8);
+  D.L = make_layout(n, nsk, nbranch, 8);
 
   // Float copy of everything; its own layout.
   ModelDev<float>& F = *mf;
   std::memset(&F, 0, sizeof(F));
-  F.n = D.n; F.maxd = D.maxd; F.nsk = D.nsk; F.ncomp = D.ncomp;
+  F.n = D.n; F.maxd = D.maxd; F.nsk = D.nsk; F.ncomp = D.ncomp; F.nbranch = D.nbranch;
   std::memcpy(F.steps, D.steps, sizeof(D.steps));
   std::memcpy(F.sched_off, D.sched_off, sizeof(D.sched_off));
   std::memcpy(F.parent, D.parent, sizeof(D.parent));
@@ -225,6 +231,7 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
   std::memcpy(F.comp_hi, D.comp_hi, sizeof(D.comp_hi));
   std::memcpy(F.perm, D.perm, sizeof(D.perm));
   std::memcpy(F.skoff, D.skoff, sizeof(D.skoff));
+  std::memcpy(F.branch, D.branch, sizeof(D.branch));
   std::memcpy(F.et_ident, D.et_ident, sizeof(D.et_ident));
   std::memcpy(F.sched, D.sched, sizeof(D.sched));
   for (int k = 0; k < GRID_MAX_DOF; ++k) {
@@ -233,6 +240,6 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
     for (int a = 0; a < 10; ++a) F.inert[k][a] = (float)D.inert[k][a];
   }
   for (int a = 0; a < 6; ++a) F.a0[a] = (float)D.a0[a];
-  F.L = make_layout(n, maxd, nsk, 4);
+  F.L = make_layout(n, nsk, nbranch, 4);
   return GRID_OK;
 }

@@ -11,6 +11,9 @@
 #define GRID_HD
 #endif
 
+// Kernel modes (one kernel template serves every entry point).
+enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3 };
+
 #define GRID_SCHED_MAX 4096    // step descriptors for all lane counts together
 #define GRID_NUM_LANE_CFG 3    // lanes per knot point: 8, 16, 32
 
@@ -34,24 +37,25 @@
 
 // Offsets (in scalars) of the per-knot shared-memory workspace.
 struct KnotLayout {
-  int Q, QD, TAU, QDD, CB;      // staged q, qd, tau (or qdd input), qdd, bias / tau out
+  int Q, QD, TAU, QDD, CB;      // staged q, qd, tau (or qdd input), qdd, bias force / tau out
   int X;                        // per body E(9) r(3)
   int V, GAM, BET, PHI;         // per body 6: v, gamma = I v, beta = (X a_parent) x S, phi = S x* F
-  int UB, DINV;                 // per body U_i (6) and D_i^-1 (stored as 2 scalars when mixed)
   int MINV;                     // n x n
-  int SK;                       // ancestor subspaces s_i^(k), 8 scalars per row
+  int SK;                       // per body (depth + 2) rows of 8: ancestor subspaces, then g^(k)
   int UNION;                    // start of the phase-dependent area
-  // phase B (dynamics, M^-1) temporaries, relative to UNION
-  int A, FO, FA, DA;            // per body 6: accelerations, own forces, accumulated forces, qdd-accel
-  int IAS, IAT, CT, FB, PST;    // IA depth stack (36 per slot), IA of current body, congruence temp, F buffer (6 x n), P stack (6 x n per depth)
-  // phase C/D temporaries, relative to UNION
+  // M^-1 temporaries, relative to UNION
+  int UB, DINV, CT, BIA, BP;    // U_i (6n), D_i^-1 (n, doubles in mixed mode), congruence exchange (36),
+                                // branch-body I^A contributions (36 each), branch-body P columns (6n each)
+  // RNEA temporaries, relative to UNION
+  int A, FO, FA;                // per body 6: acceleration, own force, accumulated force
+  // derivative-column / product temporaries, relative to UNION
   int DC, JS;                   // dc [n][2n], J staging [n][2n] (caller order)
   int stride;                   // scalars per knot
 };
 
 template <class S>
 struct ModelDev {
-  int n, maxd, nsk, ncomp;
+  int n, maxd, nsk, ncomp, nbranch;
   int steps[GRID_NUM_LANE_CFG];      // steps per lane for 8, 16, 32 lanes
   int sched_off[GRID_NUM_LANE_CFG];  // offsets into sched
   KnotLayout L;
@@ -61,7 +65,8 @@ struct ModelDev {
   int comp_lo[GRID_MAX_DOF];
   int comp_hi[GRID_MAX_DOF];
   int perm[GRID_MAX_DOF];        // internal body -> caller index
-  int skoff[GRID_MAX_DOF];       // first sK row of body k
+  int skoff[GRID_MAX_DOF];       // first subspace row of body k
+  int branch[GRID_MAX_DOF];      // slot of a body with >= 2 children, else -1
   int et_ident[GRID_MAX_DOF];
   S axis[GRID_MAX_DOF][3];
   S ET[GRID_MAX_DOF][9];

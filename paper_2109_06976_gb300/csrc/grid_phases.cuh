@@ -1,13 +1,24 @@
 // Device phases of the dynamics kernels (included by grid_kernels.cu).
-// Mapping and phase list: see grid_kernels.cu.
+//
+// T lanes of a warp cooperate on one knot point (all groups of a warp run the
+// same robot in lockstep; synchronisation is __syncwarp). Bodies use the
+// internal depth-first numbering, so subtree(i) = [i, sub_end[i]) and the first
+// child of i, if any, is i + 1. Phases, in order:
+//  B1 joint transforms X_i(q_i)                                  lanes over bodies
+//  B2 ancestor subspaces s_m^(k) = kX_m S_m and gravity rows      lanes over depths
+//  B3 direct M^-1 (articulated-inertia recursion)                lanes own 6x6 columns / M^-1 columns
+//  B4 RNEA(q, qd, 0) from the subspace table                     lanes over bodies
+//  B5 bias c_i = sum_{k in subtree(i)} s_i^(k) . f_k             lanes over bodies
+//  B6 qdd = M^-1 (tau - c)                                       lanes over rows
+//  B7 RNEA at qdd, beta_i; accumulated forces F_i, phi_i         lanes over bodies / components
+//  C  derivative columns (Alg. 1 / Alg. 2)                       host-balanced path schedules
+//  D  J = -M^-1 dc                                               lanes over outputs
 #pragma once
 
 #include <type_traits>
 
 #include "grid_internal.h"
 #include "spatial.cuh"
-
-enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3 };
 
 template <class S>
 struct Ctx {
@@ -58,102 +69,61 @@ __device__ void ph_transforms(const Ctx<S>& c) {
   SYNC();
 }
 
-// ---------------------------------------------------------------- B2 / B5
-// Forward sweep: v_i = X v_p + S qd_i, a_i = X a_p + S qdd_i + v_i x S qd_i,
-// gamma_i = I v_i, f_i = I a_i + v_i x* gamma_i (a_base = -g).
-// qdd_off < 0 means qdd = 0.
+// ---------------------------------------------------------------- B2
+// Subspace rows of body k (8 scalars each, from SK + 8 * skoff[k]):
+//   row d = 0..depth_k : s_m^(k) = kX_m S_m for the ancestor m of k at depth d
+//                        (m = k at d = depth_k); slot 6 = qd_m, slot 7 = m
+//   row depth_k + 1    : g^(k) = kX_0 a_0 (the base acceleration -g in frame k)
+// s_m^(k) = X_k s_m^(parent k). Row id rho (d, or maxd for gravity) belongs to
+// lane rho mod T, which therefore only reads rows it wrote itself.
 template <class S, int T>
-__device__ void ph_rnea_fwd(const Ctx<S>& c, int qdd_off, bool qdd_caller_order) {
+__device__ void ph_subspaces(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
   const KnotLayout& L = M.L;
-  const int l = c.l;
-  const int U = L.UNION;
+  S* SK = W + L.SK;
   for (int k = 0; k < M.n; ++k) {
+    const int dk = M.depth[k];
     const int p = M.parent[k];
     const S* E = W + L.X + 12 * k;
-    const S* r = E + 9;
-    const S qdk = W[L.QD + M.perm[k]];
-    S qddk = S(0);
-    if (qdd_off >= 0) qddk = W[qdd_off + (qdd_caller_order ? M.perm[k] : k)];
-    if (l < 6) {
-      S vp[6], ap[6];
-#pragma unroll
-      for (int e = 0; e < 6; ++e) {
-        vp[e] = p < 0 ? S(0) : W[L.V + 6 * p + e];
-        ap[e] = p < 0 ? M.a0[e] : W[U + L.A + 6 * p + e];
+    for (int rho = c.l; rho <= M.maxd; rho += T) {
+      if (rho < dk) {
+        const S* src = SK + 8 * (M.skoff[p] + rho);
+        S* dst = SK + 8 * (M.skoff[k] + rho);
+        x_mul(E, E + 9, src, dst);
+        dst[6] = src[6];
+        dst[7] = src[7];
+      } else if (rho == dk) {
+        S* dst = SK + 8 * (M.skoff[k] + dk);
+        dst[0] = M.axis[k][0]; dst[1] = M.axis[k][1]; dst[2] = M.axis[k][2];
+        dst[3] = dst[4] = dst[5] = S(0);
+        dst[6] = W[L.QD + M.perm[k]];
+        dst[7] = S(k);
+      } else if (rho == M.maxd) {
+        const S* src = p < 0 ? M.a0 : SK + 8 * (M.skoff[p] + M.depth[p] + 1);
+        x_mul(E, E + 9, src, SK + 8 * (M.skoff[k] + dk + 1));
       }
-      S sc = l < 3 ? M.axis[k][l] : S(0);
-      W[L.V + 6 * k + l] = x_mul_c(E, r, vp, l) + sc * qdk;
-      W[U + L.A + 6 * k + l] = x_mul_c(E, r, ap, l) + sc * qddk;
-    }
-    SYNC();
-    if (l < 6) {
-      const S* v = W + L.V + 6 * k;
-      const S* a = M.axis[k];
-      // (v x S qd)_l: S qd = [a qd; 0]
-      S sq[6] = {a[0] * qdk, a[1] * qdk, a[2] * qdk, S(0), S(0), S(0)};
-      S vx[6];
-      crm_mul(v, sq, vx);
-      S add = vx[0];
-#pragma unroll
-      for (int e = 1; e < 6; ++e) add = (l == e) ? vx[e] : add;
-      W[U + L.A + 6 * k + l] += add;
-      W[L.GAM + 6 * k + l] = i_mul_c(M.inert[k], v, l);
-    }
-    SYNC();
-    if (l < 6) {
-      const S* v = W + L.V + 6 * k;
-      S ia[6], vg[6];
-      i_mul(M.inert[k], W + U + L.A + 6 * k, ia);
-      crf_mul(v, W + L.GAM + 6 * k, vg);
-      S x = ia[0] + vg[0];
-#pragma unroll
-      for (int e = 1; e < 6; ++e) x = (l == e) ? ia[e] + vg[e] : x;
-      W[U + L.FO + 6 * k + l] = x;
-      W[U + L.FA + 6 * k + l] = x;
     }
   }
   SYNC();
 }
 
-// Backward sweep: tau_i = S_i^T F_i, F_p += X_i^T F_i (F = accumulated forces).
-template <class S, int T>
-__device__ void ph_rnea_bwd(const Ctx<S>& c) {
-  const ModelDev<S>& M = c.M;
-  S* W = c.W;
-  const KnotLayout& L = M.L;
-  const int l = c.l;
-  const int U = L.UNION;
-  for (int k = M.n - 1; k >= 0; --k) {
-    const int p = M.parent[k];
-    const S* F = W + U + L.FA + 6 * k;
-    if (l < 6 && p >= 0) {
-      const S* E = W + L.X + 12 * k;
-      W[U + L.FA + 6 * p + l] += xt_mul_c(E, E + 9, F, l);
-    }
-    if (l == 6) {
-      const S* a = M.axis[k];
-      W[L.CB + k] = a[0] * F[0] + a[1] * F[1] + a[2] * F[2];
-    }
-    SYNC();
-  }
-}
-
 // ---------------------------------------------------------------- B3
-// Direct M^-1 by the articulated-inertia recursion (Sec. IV-B, Carpentier 2018).
-// Backward (leaves to root):
+// Direct M^-1 by the articulated-inertia recursion (Sec. IV-B; Carpentier 2018).
+// Backward, bodies i = n-1 .. 0:
 //   I^A_i = I_i + sum_children X_c^T (I^A_c - U_c D_c^-1 U_c^T) X_c
 //   U_i = I^A_i S_i,  D_i = S_i^T U_i,  Minv[i][i] = D_i^-1
-//   Minv[i][k] = -D_i^-1 S_i^T F[:, k]          for k in subtree(i), k != i
-//   F[:, k] <- X_i^T (F[:, k] + U_i Minv[i][k])  for k in subtree(i)
-// Forward (root to leaves), for k >= i in i's base-branch:
-//   t = X_i P_p[:, k],  Minv[i][k] -= D_i^-1 U_i^T t,  P_i[:, k] = S_i Minv[i][k] + t
-// F is one 6 x n buffer (columns are owned by one subtree at a time); the
-// children's contributions to I^A and P_p are kept in depth-indexed stacks.
-// With P = double (mixed precision) the pivots D_i, D_i^-1 and every update
-// that divides by them are evaluated in FP64.
-template <class S, class P, int T>
+//   Minv[i][k] = -D_i^-1 S_i^T F[:, k]            k in subtree(i), k != i
+//   F[:, k]   <- X_i^T (F[:, k] + U_i Minv[i][k])  k in subtree(i)
+// Forward, bodies i = 0 .. n-1, columns k >= i of i's base branch:
+//   t = X_i P_parent[:, k],  Minv[i][k] -= D_i^-1 U_i^T t,  P_i[:, k] = S_i Minv[i][k] + t
+// Lanes 0..5 own column l of I^A_i in registers; the lane owning column k
+// (k = l + c T) holds F[:, k] and P[:, k] in registers. A child's I^A
+// contribution and P values pass through registers when the parent is the
+// next body processed (the first child is i + 1), and through per-branch-body
+// slots otherwise. With P = double (mixed precision) the pivots D_i, D_i^-1
+// and every update divided by them are evaluated in FP64.
+template <class S, class P, int T, int CPL>
 __device__ void ph_minv(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
@@ -162,108 +132,225 @@ __device__ void ph_minv(const Ctx<S>& c) {
   const int n = M.n;
   const int U = L.UNION;
   S* MI = W + L.MINV;
-  S* IAS = W + U + L.IAS;
-  S* IAT = W + U + L.IAT;
+  S* UB = W + U + L.UB;
+  P* DINV = reinterpret_cast<P*>(W + U + L.DINV);
   S* CT = W + U + L.CT;
-  S* FB = W + U + L.FB;
-  S* PST = W + U + L.PST;
-  P* DINV = reinterpret_cast<P*>(W + L.DINV);
+  S* BIA = W + U + L.BIA;
+  S* BP = W + U + L.BP;
   for (int e = l; e < n * n; e += T) MI[e] = S(0);
-  for (int e = l; e < 36 * M.maxd; e += T) IAS[e] = S(0);
-  for (int e = l; e < 6 * n; e += T) FB[e] = S(0);
+  for (int e = l; e < 36 * M.nbranch; e += T) BIA[e] = S(0);
   SYNC();
-  for (int k = n - 1; k >= 0; --k) {
-    const int p = M.parent[k];
-    const int d = M.depth[k];
-    const S* E = W + L.X + 12 * k;
+  S ia[6], carry[6], fb[CPL][6];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) carry[e] = S(0);
+#pragma unroll
+  for (int cc = 0; cc < CPL; ++cc)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) fb[cc][e] = S(0);
+  for (int i = n - 1; i >= 0; --i) {
+    const int p = M.parent[i];
+    const int br = M.branch[i];
+    const S* E = W + L.X + 12 * i;
     const S* r = E + 9;
-    const S* a = M.axis[k];
-    for (int e = l; e < 36; e += T) {
-      IAT[e] = i_entry(M.inert[k], e / 6, e % 6) + IAS[36 * d + e];
-      IAS[36 * d + e] = S(0);
+    const S* a = M.axis[i];
+    if (l < 6) {
+      const bool from_next = (i + 1 < n) && M.parent[i + 1] == i;
+#pragma unroll
+      for (int e = 0; e < 6; ++e)
+        ia[e] = i_entry(M.inert[i], e, l) + (from_next ? carry[e] : S(0)) +
+                (br >= 0 ? BIA[36 * br + 6 * l + e] : S(0));
+      UB[6 * i + l] = ia[0] * a[0] + ia[1] * a[1] + ia[2] * a[2];   // I^A symmetric
     }
     SYNC();
-    S* Uk = W + L.UB + 6 * k;
-    if (l < 6) Uk[l] = IAT[6 * l] * a[0] + IAT[6 * l + 1] * a[1] + IAT[6 * l + 2] * a[2];
-    SYNC();
-    const P Dk = P(a[0]) * P(Uk[0]) + P(a[1]) * P(Uk[1]) + P(a[2]) * P(Uk[2]);
+    S u[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) u[e] = UB[6 * i + e];
+    const P Dk = P(a[0]) * P(u[0]) + P(a[1]) * P(u[1]) + P(a[2]) * P(u[2]);
     const P Dinv = P(1) / Dk;
-    if (l == 0) DINV[k] = Dinv;
-    for (int kk = k + l; kk < M.sub_end[k]; kk += T) {
-      if (kk == k) MI[k * n + k] = S(Dinv);
-      else MI[k * n + kk] = S(-Dinv * (P(a[0]) * P(FB[kk]) + P(a[1]) * P(FB[n + kk]) + P(a[2]) * P(FB[2 * n + kk])));
+    if (l == 0) DINV[i] = Dinv;
+#pragma unroll
+    for (int cc = 0; cc < CPL; ++cc) {
+      const int k = l + cc * T;
+      if (k >= i && k < M.sub_end[i]) {
+        S mik;
+        if (k == i) mik = S(Dinv);
+        else mik = S(-Dinv * (P(a[0]) * P(fb[cc][0]) + P(a[1]) * P(fb[cc][1]) + P(a[2]) * P(fb[cc][2])));
+        MI[i * n + k] = mik;
+        if (p >= 0) {
+          S w[6];
+#pragma unroll
+          for (int e = 0; e < 6; ++e) w[e] = fb[cc][e] + u[e] * mik;
+          xt_mul(E, r, w, fb[cc]);
+        }
+      }
+    }
+    if (p >= 0 && l < 6) {
+      S acol[6], cx[6];
+      const P ul = P(u[l < 6 ? l : 0]) * Dinv;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) acol[e] = S(P(ia[e]) - P(u[e]) * ul);
+      xt_mul(E, r, acol, cx);                 // column l of C = X^T A
+#pragma unroll
+      for (int e = 0; e < 6; ++e) CT[6 * l + e] = cx[e];
     }
     SYNC();
-    if (p >= 0) {
-      for (int kk = k + l; kk < M.sub_end[k]; kk += T) {
-        S w[6], o[6];
-        const S mik = MI[k * n + kk];
+    if (p >= 0 && l < 6) {
+      // column l of X (6x6, X = [E 0; -E r~ E])
+      S xc[6];
+      if (l < 3) {
+        const S rt0 = l == 0 ? S(0) : (l == 1 ? -r[2] : r[1]);
+        const S rt1 = l == 0 ? r[2] : (l == 1 ? S(0) : -r[0]);
+        const S rt2 = l == 0 ? -r[1] : (l == 1 ? r[0] : S(0));
 #pragma unroll
-        for (int e = 0; e < 6; ++e) w[e] = FB[e * n + kk] + Uk[e] * mik;
-        xt_mul(E, r, w, o);
+        for (int e = 0; e < 3; ++e) {
+          xc[e] = E[3 * e + l];
+          xc[3 + e] = -(E[3 * e] * rt0 + E[3 * e + 1] * rt1 + E[3 * e + 2] * rt2);
+        }
+      } else {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) FB[e * n + kk] = o[e];
+        for (int e = 0; e < 3; ++e) { xc[e] = S(0); xc[3 + e] = E[3 * e + l - 3]; }
       }
-      for (int e = l; e < 36; e += T)
-        IAT[e] = S(P(IAT[e]) - P(Uk[e / 6]) * P(Uk[e % 6]) * Dinv);
-      SYNC();
-      if (l < 6) {                       // CT[:, l] = X^T IAT[:, l]
-        S col[6], o[6];
+      S it[6];                                 // column l of X^T A X = C X[:, l]
 #pragma unroll
-        for (int e = 0; e < 6; ++e) col[e] = IAT[6 * e + l];
-        xt_mul(E, r, col, o);
+      for (int e = 0; e < 6; ++e) it[e] = S(0);
 #pragma unroll
-        for (int e = 0; e < 6; ++e) CT[6 * e + l] = o[e];
+      for (int m = 0; m < 6; ++m)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) it[e] += CT[6 * m + e] * xc[m];
+      if (p == i - 1) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) carry[e] = it[e];
+      } else {
+        S* slot = BIA + 36 * M.branch[p] + 6 * l;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) slot[e] += it[e];
       }
-      SYNC();
-      if (l < 6) {                       // column l of X^T IA X = X^T (row l of CT)
-        S row[6], o[6];
-#pragma unroll
-        for (int e = 0; e < 6; ++e) row[e] = CT[6 * l + e];
-        xt_mul(E, r, row, o);
-        S* slot = IAS + 36 * (d - 1);
-#pragma unroll
-        for (int e = 0; e < 6; ++e) slot[6 * e + l] += o[e];
-      }
-      SYNC();
     }
   }
+  SYNC();
   // forward pass
-  for (int k = 0; k < n; ++k) {
-    const int p = M.parent[k];
-    const int d = M.depth[k];
-    const S* E = W + L.X + 12 * k;
+  S pc[CPL][6];
+#pragma unroll
+  for (int cc = 0; cc < CPL; ++cc)
+#pragma unroll
+    for (int e = 0; e < 6; ++e) pc[cc][e] = S(0);
+  for (int i = 0; i < n; ++i) {
+    const int p = M.parent[i];
+    const int br = M.branch[i];
+    const S* E = W + L.X + 12 * i;
     const S* r = E + 9;
-    const S* a = M.axis[k];
-    const S* Uk = W + L.UB + 6 * k;
-    const P Dinv = DINV[k];
-    for (int kk = k + l; kk < M.comp_hi[k]; kk += T) {
-      S t[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
-      S mk = MI[k * n + kk];
-      if (p >= 0) {
-        S pp[6];
+    const S* a = M.axis[i];
+    const S* Ui = UB + 6 * i;
+    const P Dinv = DINV[i];
 #pragma unroll
-        for (int e = 0; e < 6; ++e) pp[e] = PST[(6 * (d - 1) + e) * n + kk];
-        x_mul(E, r, pp, t);
-        P ut = P(Uk[0]) * P(t[0]);
+    for (int cc = 0; cc < CPL; ++cc) {
+      const int k = l + cc * T;
+      if (k >= i && k < M.comp_hi[i]) {
+        S t[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+        S mk = MI[i * n + k];
+        if (p >= 0) {
+          S pp[6];
+          if (p == i - 1) {
 #pragma unroll
-        for (int e = 1; e < 6; ++e) ut += P(Uk[e]) * P(t[e]);
-        mk = S(P(mk) - Dinv * ut);
-        MI[k * n + kk] = mk;
+            for (int e = 0; e < 6; ++e) pp[e] = pc[cc][e];
+          } else {
+#pragma unroll
+            for (int e = 0; e < 6; ++e) pp[e] = BP[(6 * M.branch[p] + e) * n + k];
+          }
+          x_mul(E, r, pp, t);
+          P ut = P(Ui[0]) * P(t[0]);
+#pragma unroll
+          for (int e = 1; e < 6; ++e) ut += P(Ui[e]) * P(t[e]);
+          mk = S(P(mk) - Dinv * ut);
+          MI[i * n + k] = mk;
+        }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) pc[cc][e] = (e < 3 ? a[e] * mk : S(0)) + t[e];
+        if (br >= 0) {
+#pragma unroll
+          for (int e = 0; e < 6; ++e) BP[(6 * br + e) * n + k] = pc[cc][e];
+        }
       }
-#pragma unroll
-      for (int e = 0; e < 6; ++e) PST[(6 * d + e) * n + kk] = (e < 3 ? a[e] * mk : S(0)) + t[e];
     }
-    SYNC();
   }
-  for (int e = l; e < n * n; e += T) {
-    const int i = e / n, j = e % n;
-    if (j < i) MI[e] = MI[j * n + i];
+  // mirror the columns this lane owns into the lower triangle
+#pragma unroll
+  for (int cc = 0; cc < CPL; ++cc) {
+    const int k = l + cc * T;
+    if (k < n)
+      for (int i = M.comp_lo[k]; i < k; ++i) MI[k * n + i] = MI[i * n + k];
   }
   SYNC();
 }
 
 // ---------------------------------------------------------------- B4
+// RNEA from the subspace table, for body k with root path m_0 .. m_d = k:
+//   v_m^(k) = sum_{e <= m} s_e^(k) qd_e   (velocity of body m in frame k)
+//   v_k = v_k^(k),  a_k = g^(k) + sum_m [ v_m^(k) x s_m^(k) qd_m + s_m^(k) qdd_m ]
+//   gamma_k = I_k v_k,  f_k = I_k a_k + v_k x* gamma_k
+// (the forward recursion v_i = X v_p + S qd_i, a_i = X a_p + S qdd_i + v_i x S qd_i
+// unrolled over the path). qdd_off < 0 means qdd = 0.
+template <class S, int T>
+__device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
+  const ModelDev<S>& M = c.M;
+  S* W = c.W;
+  const KnotLayout& L = M.L;
+  const int U = L.UNION;
+  for (int k = c.l; k < M.n; k += T) {
+    const int dk = M.depth[k];
+    const S* rows = W + L.SK + 8 * M.skoff[k];
+    S v[6], a[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) { v[e] = S(0); a[e] = rows[8 * (dk + 1) + e]; }
+    for (int d = 0; d <= dk; ++d) {
+      const S* s = rows + 8 * d;
+      const S qd = s[6];
+      S sq[6], t[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) { sq[e] = s[e] * qd; v[e] += sq[e]; }
+      crm_mul(v, sq, t);
+      S qdd = S(0);
+      if (qdd_off >= 0) qdd = W[qdd_off + M.perm[(int)s[7]]];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) a[e] += t[e] + s[e] * qdd;
+    }
+    S g[6], ia[6], vg[6];
+    i_mul(M.inert[k], v, g);
+    i_mul(M.inert[k], a, ia);
+    crf_mul(v, g, vg);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      W[L.V + 6 * k + e] = v[e];
+      W[L.GAM + 6 * k + e] = g[e];
+      W[U + L.A + 6 * k + e] = a[e];
+      W[U + L.FO + 6 * k + e] = ia[e] + vg[e];
+    }
+  }
+  SYNC();
+}
+
+// ---------------------------------------------------------------- B5
+// Joint forces from body forces: c_i = S_i^T F_i = sum_{k in subtree(i)} s_i^(k) . f_k
+// (the RNEA backward sweep F_p += X^T F_i, tau_i = S_i^T F_i, unrolled).
+template <class S, int T>
+__device__ void ph_joint_forces(const Ctx<S>& c, int f_off, int out_off) {
+  const ModelDev<S>& M = c.M;
+  S* W = c.W;
+  const KnotLayout& L = M.L;
+  for (int i = c.l; i < M.n; i += T) {
+    const int di = M.depth[i];
+    S acc = S(0);
+    for (int k = i; k < M.sub_end[i]; ++k) {
+      const S* s = W + L.SK + 8 * (M.skoff[k] + di);
+      const S* f = W + f_off + 6 * k;
+      acc += s[0] * f[0] + s[1] * f[1] + s[2] * f[2] + s[3] * f[3] + s[4] * f[4] + s[5] * f[5];
+    }
+    W[out_off + i] = acc;
+  }
+  SYNC();
+}
+
+// ---------------------------------------------------------------- B6
 template <class S, int T>
 __device__ void ph_fd(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
@@ -279,79 +366,63 @@ __device__ void ph_fd(const Ctx<S>& c) {
   SYNC();
 }
 
-// ---------------------------------------------------------------- B5
-// RNEA at the computed qdd: the accelerations change by da_i = X da_p + S qdd_i,
-// own forces by I da_i; accumulated forces are then rebuilt.
+// ---------------------------------------------------------------- B7
+// RNEA at the computed qdd: a_k += sum_m s_m^(k) qdd_m, f_k += I_k (that);
+// beta_k = (X_k a_p) x S_k with X_k a_p = a_k - (v_k x S_k) qd_k - S_k qdd_k
+// (so beta_k = (a_k - qd_k v_k x S_k) x S_k, as S x S = 0). Then the
+// accumulated forces F_i = f_i + sum_children X_c^T F_c (lanes over
+// components) and phi_i = S_i x* F_i.
 template <class S, int T>
-__device__ void ph_rnea_qdd_update(const Ctx<S>& c) {
+__device__ void ph_update_and_forces(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
   const KnotLayout& L = M.L;
-  const int l = c.l;
   const int U = L.UNION;
-  for (int k = 0; k < M.n; ++k) {
-    const int p = M.parent[k];
-    const S* E = W + L.X + 12 * k;
-    if (l < 6) {
-      S dp[6];
+  const int l = c.l;
+  for (int k = l; k < M.n; k += T) {
+    const int dk = M.depth[k];
+    const S* rows = W + L.SK + 8 * M.skoff[k];
+    S da[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+    for (int d = 0; d <= dk; ++d) {
+      const S* s = rows + 8 * d;
+      const S qdd = W[L.QDD + (int)s[7]];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) dp[e] = p < 0 ? S(0) : W[U + L.DA + 6 * p + e];
-      S sc = l < 3 ? M.axis[k][l] : S(0);
-      W[U + L.DA + 6 * k + l] = x_mul_c(E, E + 9, dp, l) + sc * W[L.QDD + k];
+      for (int e = 0; e < 6; ++e) da[e] += s[e] * qdd;
     }
-    SYNC();
-    if (l < 6) {
-      W[U + L.A + 6 * k + l] += W[U + L.DA + 6 * k + l];
-      const S x = W[U + L.FO + 6 * k + l] + i_mul_c(M.inert[k], W + U + L.DA + 6 * k, l);
-      W[U + L.FO + 6 * k + l] = x;
-      W[U + L.FA + 6 * k + l] = x;
+    const S* ax = M.axis[k];
+    const S* v = W + L.V + 6 * k;
+    const S qdk = W[L.QD + M.perm[k]];
+    S idt[6], vxs[6], w[6];
+    i_mul(M.inert[k], da, idt);
+    cross3(v, ax, vxs);
+    cross3(v + 3, ax, vxs + 3);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      w[e] = W[U + L.A + 6 * k + e] + da[e] - qdk * vxs[e];
+      W[U + L.FA + 6 * k + e] = W[U + L.FO + 6 * k + e] + idt[e];
     }
+    S* B = W + L.BET + 6 * k;
+    cross3(w, ax, B);
+    cross3(w + 3, ax, B + 3);
   }
   SYNC();
-}
-
-// ---------------------------------------------------------------- B6
-// Per-body terms of Alg. 2 that do not depend on the column:
-//   beta_i = (X_i a_p) x S_i, phi_i = S_i x* F_i (the backward-pass term of
-//   the q columns), and the subspaces s_i^(k) = kX_i S_i of every ancestor i of
-//   k expressed in frame k (s_k^(k) = S_k, s_i^(k) = X_k s_i^(p)).
-template <class S, int T>
-__device__ void ph_aux(const Ctx<S>& c) {
-  const ModelDev<S>& M = c.M;
-  S* W = c.W;
-  const KnotLayout& L = M.L;
-  const int U = L.UNION;
-  for (int k = c.l; k < M.n; k += T) {
+  for (int k = M.n - 1; k > 0; --k) {
     const int p = M.parent[k];
-    const S* E = W + L.X + 12 * k;
-    const S* a = M.axis[k];
-    S ap[6], w[6];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) ap[e] = p < 0 ? M.a0[e] : W[U + L.A + 6 * p + e];
-    x_mul(E, E + 9, ap, w);
-    S* B = W + L.BET + 6 * k;
-    cross3(w, a, B);             // (X a_p) x [a; 0] = [w_ang x a; w_lin x a]
-    cross3(w + 3, a, B + 3);
-    const S* F = W + U + L.FA + 6 * k;
-    S* Ph = W + L.PHI + 6 * k;    // [a; 0] x* F = [a x F_ang; a x F_lin]
-    cross3(a, F, Ph);
-    cross3(a, F + 3, Ph + 3);
-  }
-  for (int k = 0; k < M.n; ++k) {
-    const int dk = M.depth[k];
-    const int p = M.parent[k];
-    const S* E = W + L.X + 12 * k;
-    for (int d = c.l; d <= dk; d += T) {
-      S* row = W + L.SK + 8 * (M.skoff[k] + d);
-      if (d == dk) {
-        row[0] = M.axis[k][0]; row[1] = M.axis[k][1]; row[2] = M.axis[k][2];
-        row[3] = row[4] = row[5] = S(0);
-      } else {
-        x_mul(E, E + 9, W + L.SK + 8 * (M.skoff[p] + d), row);
-      }
+    if (p >= 0 && l < 6) {
+      const S* E = W + L.X + 12 * k;
+      W[U + L.FA + 6 * p + l] += xt_mul_c(E, E + 9, W + U + L.FA + 6 * k, l);
     }
-    SYNC();
+    if (p == k - 1) SYNC();
   }
+  SYNC();
+  for (int k = l; k < M.n; k += T) {
+    const S* F = W + U + L.FA + 6 * k;
+    const S* ax = M.axis[k];
+    S* Ph = W + L.PHI + 6 * k;                 // [a; 0] x* F = [a x F_ang; a x F_lin]
+    cross3(ax, F, Ph);
+    cross3(ax, F + 3, Ph + 3);
+  }
+  SYNC();
 }
 
 // ---------------------------------------------------------------- C
@@ -487,7 +558,7 @@ __device__ void ph_product(const Ctx<S>& c) {
 }
 
 // One warp processes knot points k0 .. k0 + 32/T - 1 (those < N).
-template <class S, int MODE, int T, int MAXD, bool MIXED>
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
 __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ sched, int nsteps,
                              S* Wwarp, int lane32, int k0, int N, const S* __restrict__ q,
                              const S* __restrict__ qd, const S* __restrict__ x3, S* __restrict__ out,
@@ -514,22 +585,23 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   }
   SYNC();
   ph_transforms<S, T>(c);
-  if (MODE == MODE_RNEA) {
-    ph_rnea_fwd<S, T>(c, L.TAU, true);
-    ph_rnea_bwd<S, T>(c);
-  } else if (MODE == MODE_MINV) {
-    ph_minv<S, P, T>(c);
+  if (MODE == MODE_MINV) {
+    ph_minv<S, P, T, CPL>(c);
   } else {
-    ph_rnea_fwd<S, T>(c, -1, false);
-    ph_rnea_bwd<S, T>(c);                 // CB = RNEA(q, qd, 0)
-    ph_minv<S, P, T>(c);
-    ph_fd<S, T>(c);
-    if (MODE == MODE_GRAD) {
-      ph_rnea_qdd_update<S, T>(c);
-      ph_rnea_bwd<S, T>(c);
-      ph_aux<S, T>(c);
-      ph_columns<S, T, MAXD>(c, sched, nsteps);
-      ph_product<S, T>(c);
+    ph_subspaces<S, T>(c);
+    if (MODE == MODE_RNEA) {
+      ph_rnea_bodies<S, T>(c, L.TAU);
+      ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);
+    } else {
+      ph_minv<S, P, T, CPL>(c);
+      ph_rnea_bodies<S, T>(c, -1);
+      ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);    // CB = RNEA(q, qd, 0)
+      ph_fd<S, T>(c);
+      if (MODE == MODE_GRAD) {
+        ph_update_and_forces<S, T>(c);
+        ph_columns<S, T, MAXD>(c, sched, nsteps);
+        ph_product<S, T>(c);
+      }
     }
   }
   // stage outputs in caller order
@@ -556,4 +628,3 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   }
   SYNC();
 }
-
