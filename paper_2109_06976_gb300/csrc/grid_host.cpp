@@ -31,20 +31,21 @@ KnotLayout make_layout(int n, int nsk, int nbranch, int ssize) {
   auto take = [&](int count) { int o = off; off += round_up(count, 4); return o; };
   L.Q = take(n); L.QD = take(n); L.TAU = take(n); L.QDD = take(n); L.CB = take(n);
   L.X = take(12 * n);
-  L.V = take(6 * n); L.GAM = take(6 * n); L.BET = take(6 * n); L.PHI = take(6 * n);
-  L.MINV = take(n * n);
+  L.V = take(8 * n); L.GAM = take(8 * n); L.BET = take(8 * n); L.PHI = take(8 * n);
+  L.MS = round_up(n, 4);
+  L.MINV = take(n * L.MS);
   L.SK = take(8 * nsk);
   L.UNION = off;
   int b = 0;
   auto tb = [&](int count) { int o = b; b += round_up(count, 4); return o; };
-  L.UB = tb(6 * n);
+  L.UB = tb(8 * n);
   L.DINV = tb(ssize == 4 ? 2 * n : n);     // doubles (mixed mode stores them in pairs of floats)
-  L.CT = tb(36);
+  L.CT = tb(48);
   L.BIA = tb(36 * nbranch);
   L.BP = tb(6 * n * nbranch);
   int r = 0;
   auto tr = [&](int count) { int o = r; r += round_up(count, 4); return o; };
-  L.A = tr(6 * n); L.FO = tr(6 * n); L.FA = tr(6 * n);
+  L.A = tr(8 * n); L.FO = tr(8 * n); L.FA = tr(8 * n); L.FSL = tr(8 * nbranch);
   int c = 0;
   auto tc = [&](int count) { int o = c; c += round_up(count, 4); return o; };
   L.DC = tc(2 * n * n); L.JS = tc(2 * n * n);

@@ -39,15 +39,16 @@ enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3 };
 struct KnotLayout {
   int Q, QD, TAU, QDD, CB;      // staged q, qd, tau (or qdd input), qdd, bias force / tau out
   int X;                        // per body E(9) r(3)
-  int V, GAM, BET, PHI;         // per body 6: v, gamma = I v, beta = (X a_parent) x S, phi = S x* F
-  int MINV;                     // n x n
+  int V, GAM, BET, PHI;         // per body 8 (6 used): v, gamma = I v, beta = (X a_parent) x S, phi = S x* F
+  int MINV, MS;                 // n x n with row stride MS (a multiple of 4)
   int SK;                       // per body (depth + 2) rows of 8: ancestor subspaces, then g^(k)
   int UNION;                    // start of the phase-dependent area
   // M^-1 temporaries, relative to UNION
-  int UB, DINV, CT, BIA, BP;    // U_i (6n), D_i^-1 (n, doubles in mixed mode), congruence exchange (36),
+  int UB, DINV, CT, BIA, BP;    // U_i (8n), D_i^-1 (n, doubles in mixed mode), congruence exchange (6 x 8),
                                 // branch-body I^A contributions (36 each), branch-body P columns (6n each)
   // RNEA temporaries, relative to UNION
-  int A, FO, FA;                // per body 6: acceleration, own force, accumulated force
+  int A, FO, FA, FSL;           // per body 8: acceleration, own force, accumulated force;
+                                // FSL: force contributions to branch bodies (8 each)
   // derivative-column / product temporaries, relative to UNION
   int DC, JS;                   // dc [n][2n], J staging [n][2n] (caller order)
   int stride;                   // scalars per knot

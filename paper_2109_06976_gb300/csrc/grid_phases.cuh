@@ -23,8 +23,9 @@
 template <class S>
 struct Ctx {
   const ModelDev<S>& M;
-  S* W;      // this knot point's workspace
-  int l;     // lane within the group, 0..T-1
+  S* W;        // this knot point's workspace
+  int l;       // lane within the group, 0..T-1
+  int lane32;  // lane within the warp
 };
 
 #ifndef GRID_SYNC
@@ -32,6 +33,9 @@ struct Ctx {
 #endif
 #ifndef GRID_ATOMIC_ADD
 #define GRID_ATOMIC_ADD(p, v) atomicAdd((p), (v))
+#endif
+#ifndef GRID_SHFL
+#define GRID_SHFL(v, src) __shfl_sync(0xffffffffu, (v), (src))
 #endif
 #define SYNC() GRID_SYNC()
 
@@ -82,26 +86,50 @@ __device__ void ph_subspaces(const Ctx<S>& c) {
   S* W = c.W;
   const KnotLayout& L = M.L;
   S* SK = W + L.SK;
+  // With one row id per lane, the lane's row of the previous body is kept in
+  // registers and reused when that body is the parent (always, for a chain).
+  const bool carry_ok = T > M.maxd;
+  S carry[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) carry[e] = S(0);
   for (int k = 0; k < M.n; ++k) {
     const int dk = M.depth[k];
     const int p = M.parent[k];
-    const S* E = W + L.X + 12 * k;
+    S E[12];
+    ld12(W + L.X + 12 * k, E);
     for (int rho = c.l; rho <= M.maxd; rho += T) {
-      if (rho < dk) {
-        const S* src = SK + 8 * (M.skoff[p] + rho);
-        S* dst = SK + 8 * (M.skoff[k] + rho);
-        x_mul(E, E + 9, src, dst);
-        dst[6] = src[6];
-        dst[7] = src[7];
-      } else if (rho == dk) {
+      if (rho == dk) {
+        S row[8] = {M.axis[k][0], M.axis[k][1], M.axis[k][2], S(0), S(0), S(0),
+                    W[L.QD + M.perm[k]], S(k)};
         S* dst = SK + 8 * (M.skoff[k] + dk);
-        dst[0] = M.axis[k][0]; dst[1] = M.axis[k][1]; dst[2] = M.axis[k][2];
-        dst[3] = dst[4] = dst[5] = S(0);
-        dst[6] = W[L.QD + M.perm[k]];
-        dst[7] = S(k);
-      } else if (rho == M.maxd) {
-        const S* src = p < 0 ? M.a0 : SK + 8 * (M.skoff[p] + M.depth[p] + 1);
-        x_mul(E, E + 9, src, SK + 8 * (M.skoff[k] + dk + 1));
+        st4(dst, row);
+        st4(dst + 4, row + 4);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) carry[e] = row[e];
+      } else if (rho < dk || rho == M.maxd) {
+        const bool grav = rho == M.maxd;
+        S src[8];
+        if (p < 0) {
+#pragma unroll
+          for (int e = 0; e < 6; ++e) src[e] = M.a0[e];
+          src[6] = src[7] = S(0);
+        } else if (carry_ok && p == k - 1) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) src[e] = carry[e];
+        } else {
+          const S* sp = SK + 8 * (M.skoff[p] + (grav ? M.depth[p] + 1 : rho));
+          ld4(sp, src);
+          ld4(sp + 4, src + 4);
+        }
+        S out[8];
+        x_mul(E, E + 9, src, out);
+        out[6] = src[6];
+        out[7] = src[7];
+        S* dst = SK + 8 * (M.skoff[k] + (grav ? dk + 1 : rho));
+        st4(dst, out);
+        st4(dst + 4, out + 4);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) carry[e] = out[e];
       }
     }
   }
@@ -137,7 +165,8 @@ __device__ void ph_minv(const Ctx<S>& c) {
   S* CT = W + U + L.CT;
   S* BIA = W + U + L.BIA;
   S* BP = W + U + L.BP;
-  for (int e = l; e < n * n; e += T) MI[e] = S(0);
+  const int MS = L.MS;
+  for (int e = l; e < n * MS; e += T) MI[e] = S(0);
   for (int e = l; e < 36 * M.nbranch; e += T) BIA[e] = S(0);
   SYNC();
   S ia[6], carry[6], fb[CPL][6];
@@ -159,12 +188,11 @@ __device__ void ph_minv(const Ctx<S>& c) {
       for (int e = 0; e < 6; ++e)
         ia[e] = i_entry(M.inert[i], e, l) + (from_next ? carry[e] : S(0)) +
                 (br >= 0 ? BIA[36 * br + 6 * l + e] : S(0));
-      UB[6 * i + l] = ia[0] * a[0] + ia[1] * a[1] + ia[2] * a[2];   // I^A symmetric
+      UB[8 * i + l] = ia[0] * a[0] + ia[1] * a[1] + ia[2] * a[2];   // I^A symmetric
     }
     SYNC();
     S u[6];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) u[e] = UB[6 * i + e];
+    ld6(UB + 8 * i, u);
     const P Dk = P(a[0]) * P(u[0]) + P(a[1]) * P(u[1]) + P(a[2]) * P(u[2]);
     const P Dinv = P(1) / Dk;
     if (l == 0) DINV[i] = Dinv;
@@ -175,7 +203,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
         S mik;
         if (k == i) mik = S(Dinv);
         else mik = S(-Dinv * (P(a[0]) * P(fb[cc][0]) + P(a[1]) * P(fb[cc][1]) + P(a[2]) * P(fb[cc][2])));
-        MI[i * n + k] = mik;
+        MI[i * MS + k] = mik;
         if (p >= 0) {
           S w[6];
 #pragma unroll
@@ -186,12 +214,14 @@ __device__ void ph_minv(const Ctx<S>& c) {
     }
     if (p >= 0 && l < 6) {
       S acol[6], cx[6];
-      const P ul = P(u[l < 6 ? l : 0]) * Dinv;
+      S u_l = u[0];
+#pragma unroll
+      for (int e = 1; e < 6; ++e) u_l = (l == e) ? u[e] : u_l;
+      const P ul = P(u_l) * Dinv;
 #pragma unroll
       for (int e = 0; e < 6; ++e) acol[e] = S(P(ia[e]) - P(u[e]) * ul);
       xt_mul(E, r, acol, cx);                 // column l of C = X^T A
-#pragma unroll
-      for (int e = 0; e < 6; ++e) CT[6 * l + e] = cx[e];
+      st6(CT + 8 * l, cx);
     }
     SYNC();
     if (p >= 0 && l < 6) {
@@ -214,9 +244,12 @@ __device__ void ph_minv(const Ctx<S>& c) {
 #pragma unroll
       for (int e = 0; e < 6; ++e) it[e] = S(0);
 #pragma unroll
-      for (int m = 0; m < 6; ++m)
+      for (int m = 0; m < 6; ++m) {
+        S cm[6];
+        ld6(CT + 8 * m, cm);
 #pragma unroll
-        for (int e = 0; e < 6; ++e) it[e] += CT[6 * m + e] * xc[m];
+        for (int e = 0; e < 6; ++e) it[e] += cm[e] * xc[m];
+      }
       if (p == i - 1) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) carry[e] = it[e];
@@ -240,14 +273,15 @@ __device__ void ph_minv(const Ctx<S>& c) {
     const S* E = W + L.X + 12 * i;
     const S* r = E + 9;
     const S* a = M.axis[i];
-    const S* Ui = UB + 6 * i;
+    S Ui[6];
+    ld6(UB + 8 * i, Ui);
     const P Dinv = DINV[i];
 #pragma unroll
     for (int cc = 0; cc < CPL; ++cc) {
       const int k = l + cc * T;
       if (k >= i && k < M.comp_hi[i]) {
         S t[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
-        S mk = MI[i * n + k];
+        S mk = MI[i * MS + k];
         if (p >= 0) {
           S pp[6];
           if (p == i - 1) {
@@ -262,7 +296,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
 #pragma unroll
           for (int e = 1; e < 6; ++e) ut += P(Ui[e]) * P(t[e]);
           mk = S(P(mk) - Dinv * ut);
-          MI[i * n + k] = mk;
+          MI[i * MS + k] = mk;
         }
 #pragma unroll
         for (int e = 0; e < 6; ++e) pc[cc][e] = (e < 3 ? a[e] * mk : S(0)) + t[e];
@@ -278,7 +312,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
   for (int cc = 0; cc < CPL; ++cc) {
     const int k = l + cc * T;
     if (k < n)
-      for (int i = M.comp_lo[k]; i < k; ++i) MI[k * n + i] = MI[i * n + k];
+      for (int i = M.comp_lo[k]; i < k; ++i) MI[k * MS + i] = MI[i * MS + k];
   }
   SYNC();
 }
@@ -301,9 +335,12 @@ __device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
     const S* rows = W + L.SK + 8 * M.skoff[k];
     S v[6], a[6];
 #pragma unroll
-    for (int e = 0; e < 6; ++e) { v[e] = S(0); a[e] = rows[8 * (dk + 1) + e]; }
+    for (int e = 0; e < 6; ++e) v[e] = S(0);
+    ld6(rows + 8 * (dk + 1), a);
     for (int d = 0; d <= dk; ++d) {
-      const S* s = rows + 8 * d;
+      S s[8];
+      ld4(rows + 8 * d, s);
+      ld4(rows + 8 * d + 4, s + 4);
       const S qd = s[6];
       S sq[6], t[6];
 #pragma unroll
@@ -319,12 +356,11 @@ __device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
     i_mul(M.inert[k], a, ia);
     crf_mul(v, g, vg);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      W[L.V + 6 * k + e] = v[e];
-      W[L.GAM + 6 * k + e] = g[e];
-      W[U + L.A + 6 * k + e] = a[e];
-      W[U + L.FO + 6 * k + e] = ia[e] + vg[e];
-    }
+    for (int e = 0; e < 6; ++e) ia[e] += vg[e];
+    st6(W + L.V + 8 * k, v);
+    st6(W + L.GAM + 8 * k, g);
+    st6(W + U + L.A + 8 * k, a);
+    st6(W + U + L.FO + 8 * k, ia);
   }
   SYNC();
 }
@@ -341,8 +377,9 @@ __device__ void ph_joint_forces(const Ctx<S>& c, int f_off, int out_off) {
     const int di = M.depth[i];
     S acc = S(0);
     for (int k = i; k < M.sub_end[i]; ++k) {
-      const S* s = W + L.SK + 8 * (M.skoff[k] + di);
-      const S* f = W + f_off + 6 * k;
+      S s[6], f[6];
+      ld6(W + L.SK + 8 * (M.skoff[k] + di), s);
+      ld6(W + f_off + 8 * k, f);
       acc += s[0] * f[0] + s[1] * f[1] + s[2] * f[2] + s[3] * f[3] + s[4] * f[4] + s[5] * f[5];
     }
     W[out_off + i] = acc;
@@ -360,7 +397,7 @@ __device__ void ph_fd(const Ctx<S>& c) {
   for (int i = c.l; i < n; i += T) {
     S acc = S(0);
     for (int j = M.comp_lo[i]; j < M.comp_hi[i]; ++j)
-      acc += W[L.MINV + i * n + j] * (W[L.TAU + M.perm[j]] - W[L.CB + j]);
+      acc += W[L.MINV + i * L.MS + j] * (W[L.TAU + M.perm[j]] - W[L.CB + j]);
     W[L.QDD + i] = acc;
   }
   SYNC();
@@ -379,18 +416,26 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
   const KnotLayout& L = M.L;
   const int U = L.UNION;
   const int l = c.l;
+  S* FA = W + U + L.FA;
+  S* FSL = W + U + L.FSL;
+  for (int e = l; e < 8 * M.nbranch; e += T) FSL[e] = S(0);
   for (int k = l; k < M.n; k += T) {
     const int dk = M.depth[k];
     const S* rows = W + L.SK + 8 * M.skoff[k];
     S da[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
     for (int d = 0; d <= dk; ++d) {
-      const S* s = rows + 8 * d;
+      S s[8];
+      ld4(rows + 8 * d, s);
+      ld4(rows + 8 * d + 4, s + 4);
       const S qdd = W[L.QDD + (int)s[7]];
 #pragma unroll
       for (int e = 0; e < 6; ++e) da[e] += s[e] * qdd;
     }
     const S* ax = M.axis[k];
-    const S* v = W + L.V + 6 * k;
+    S v[6], a[6], fo[6];
+    ld6(W + L.V + 8 * k, v);
+    ld6(W + U + L.A + 8 * k, a);
+    ld6(W + U + L.FO + 8 * k, fo);
     const S qdk = W[L.QD + M.perm[k]];
     S idt[6], vxs[6], w[6];
     i_mul(M.inert[k], da, idt);
@@ -398,29 +443,53 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
     cross3(v + 3, ax, vxs + 3);
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
-      w[e] = W[U + L.A + 6 * k + e] + da[e] - qdk * vxs[e];
-      W[U + L.FA + 6 * k + e] = W[U + L.FO + 6 * k + e] + idt[e];
+      w[e] = a[e] + da[e] - qdk * vxs[e];
+      fo[e] += idt[e];
     }
-    S* B = W + L.BET + 6 * k;
+    st6(FA + 8 * k, fo);
+    S B[6];
     cross3(w, ax, B);
     cross3(w + 3, ax, B + 3);
+    st6(W + L.BET + 8 * k, B);
   }
   SYNC();
-  for (int k = M.n - 1; k > 0; --k) {
+  // Leaves to root: lane l < 6 holds component l of F_k; the full vector is
+  // gathered by warp shuffles. A child's X^T F passes in a register to its
+  // parent when the parent is the next body (k - 1), else through a slot.
+  const int base = c.lane32 - l;
+  S carry = S(0);
+  for (int k = M.n - 1; k >= 0; --k) {
     const int p = M.parent[k];
-    if (p >= 0 && l < 6) {
-      const S* E = W + L.X + 12 * k;
-      W[U + L.FA + 6 * p + l] += xt_mul_c(E, E + 9, W + U + L.FA + 6 * k, l);
+    const int br = M.branch[k];
+    S fk = S(0);
+    if (l < 6) {
+      fk = FA[8 * k + l];
+      if (k + 1 < M.n && M.parent[k + 1] == k) fk += carry;
+      if (br >= 0) fk += FSL[8 * br + l];
     }
-    if (p == k - 1) SYNC();
+    S F[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) F[e] = GRID_SHFL(fk, base + e);
+    if (l < 6) {
+      FA[8 * k + l] = fk;
+      if (p >= 0) {
+        S E[12];
+        ld12(W + L.X + 12 * k, E);
+        const S cl = xt_mul_c(E, E + 9, F, l);
+        if (p == k - 1) carry = cl;
+        else FSL[8 * M.branch[p] + l] += cl;
+      }
+    }
   }
   SYNC();
   for (int k = l; k < M.n; k += T) {
-    const S* F = W + U + L.FA + 6 * k;
+    S F[6];
+    ld6(FA + 8 * k, F);
     const S* ax = M.axis[k];
-    S* Ph = W + L.PHI + 6 * k;                 // [a; 0] x* F = [a x F_ang; a x F_lin]
+    S Ph[6];                                   // [a; 0] x* F = [a x F_ang; a x F_lin]
     cross3(ax, F, Ph);
     cross3(ax, F + 3, Ph + 3);
+    st6(W + L.PHI + 8 * k, Ph);
   }
   SYNC();
 }
@@ -462,13 +531,14 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 #pragma unroll
       for (int e = 0; e < 6; ++e) { dv[e] = S(0); da[e] = S(0); }
     }
-    const S* E = W + L.X + 12 * k;
+    S E[12];
+    ld12(W + L.X + 12 * k, E);
     const S* r = E + 9;
     const S* ax = M.axis[k];
     const S qdk = W[L.QD + M.perm[k]];
     S v[6], g[6];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) { v[e] = W[L.V + 6 * k + e]; g[e] = W[L.GAM + 6 * k + e]; }
+    ld6(W + L.V + 8 * k, v);
+    ld6(W + L.GAM + 8 * k, g);
     S ndv[6], nda[6], vxs[6];
     x_mul(E, r, dv, ndv);
     x_mul(E, r, da, nda);
@@ -476,7 +546,8 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
     cross3(v + 3, ax, vxs + 3);
     if (root) {
       if (uq) {
-        const S* B = W + L.BET + 6 * k;
+        S B[6];
+        ld6(W + L.BET + 8 * k, B);
 #pragma unroll
         for (int e = 0; e < 6; ++e) { ndv[e] += vxs[e]; nda[e] += B[e]; }
       } else {
@@ -501,7 +572,8 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 #pragma unroll
     for (int e = 0; e < 6; ++e) df[e] += t1[e] + t2[e];
     if (root && uq) {
-      const S* Ph = W + L.PHI + 6 * k;
+      S Ph[6];
+      ld6(W + L.PHI + 8 * k, Ph);
 #pragma unroll
       for (int e = 0; e < 6; ++e) df[e] += Ph[e];
     }
@@ -511,7 +583,8 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 #pragma unroll
       for (int d = 0; d < MAXD; ++d) {
         if (d <= dk) {
-          const S* sr = rows + 8 * d;
+          S sr[6];
+          ld6(rows + 8 * d, sr);
           acc[d] += sr[0] * df[0] + sr[1] * df[1] + sr[2] * df[2] + sr[3] * df[3] + sr[4] * df[4] +
                     sr[5] * df[5];
         }
@@ -536,23 +609,41 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 
 // ---------------------------------------------------------------- D
 // J = -M^-1 dc, restricted to base-branch blocks, written in caller order.
-template <class S, int T>
+template <class S, int T, int CPL>
 __device__ void ph_product(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
   const KnotLayout& L = M.L;
-  const int n = M.n, n2 = 2 * n;
+  const int n = M.n, n2 = 2 * n, MS = L.MS;
   const int U = L.UNION;
   const S* DC = W + U + L.DC;
+  const S* MI = W + L.MINV;
   S* JS = W + U + L.JS;
-  for (int e = c.l; e < 2 * n * n; e += T) {
-    const int i = e / n2, col = e % n2;
+  constexpr int NM = CPL * T;                  // >= n, a multiple of 4
+  // Lane owns output columns col = l, l + T, ...: its dc column sits in
+  // registers and every M^-1 row is read with 128-bit loads.
+  for (int col = c.l; col < n2; col += T) {
     const int j = col < n ? col : col - n;
-    S acc = S(0);
-    if (M.comp_lo[j] <= i && i < M.comp_hi[j])
-      for (int m = M.comp_lo[j]; m < M.comp_hi[j]; ++m) acc += W[L.MINV + i * n + m] * DC[m * n2 + col];
+    const int lo = M.comp_lo[j], hi = M.comp_hi[j];
+    S dcr[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) dcr[m] = (m >= lo && m < hi) ? DC[m * n2 + col] : S(0);
     const int ucol = (col < n ? 0 : n) + M.perm[j];
-    JS[M.perm[i] * n2 + ucol] = -acc;
+    for (int i = 0; i < lo; ++i) JS[M.perm[i] * n2 + ucol] = S(0);     // other base branches
+    for (int i = hi; i < n; ++i) JS[M.perm[i] * n2 + ucol] = S(0);
+    for (int i = lo; i < hi; ++i) {
+      const S* mrow = MI + i * MS;
+      S acc = S(0);
+#pragma unroll
+      for (int m = 0; m < NM; m += 4) {
+        if (m < MS) {
+          S mm[4];
+          ld4(mrow + m, mm);
+          acc += mm[0] * dcr[m] + mm[1] * dcr[m + 1] + mm[2] * dcr[m + 2] + mm[3] * dcr[m + 3];
+        }
+      }
+      JS[M.perm[i] * n2 + ucol] = -acc;
+    }
   }
   SYNC();
 }
@@ -569,7 +660,7 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   constexpr int G = 32 / T;
   const int g = lane32 / T;
   S* W = Wwarp + g * L.stride;
-  const Ctx<S> c{M, W, lane32 % T};
+  const Ctx<S> c{M, W, lane32 % T, lane32};
   const int out_per = MODE == MODE_MINV ? n * n : (MODE == MODE_GRAD ? 2 * n * n : n);
   const int nvalid = min(G, N - k0);
   // stage inputs (coalesced across the warp)
@@ -600,7 +691,7 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
       if (MODE == MODE_GRAD) {
         ph_update_and_forces<S, T>(c);
         ph_columns<S, T, MAXD>(c, sched, nsteps);
-        ph_product<S, T>(c);
+        ph_product<S, T, CPL>(c);
       }
     }
   }
@@ -611,7 +702,7 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   } else if (MODE == MODE_FD) {
     for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.QDD + i];
   } else if (MODE == MODE_MINV) {
-    for (int e = c.l; e < n * n; e += T) OS[M.perm[e / n] * n + M.perm[e % n]] = W[L.MINV + e];
+    for (int e = c.l; e < n * n; e += T) OS[M.perm[e / n] * n + M.perm[e % n]] = W[L.MINV + (e / n) * L.MS + e % n];
   } else if (out2) {
     for (int i = c.l; i < n; i += T) W[L.CB + M.perm[i]] = W[L.QDD + i];
   }

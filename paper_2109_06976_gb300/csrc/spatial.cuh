@@ -129,3 +129,58 @@ __device__ __forceinline__ S i_entry(const S* in, int r, int c) {
   else v = (j == 0) ? -h[1] : h[0];
   return v;
 }
+
+// Vector shared-memory access for records aligned to 16 bytes (p must be).
+template <class S>
+__device__ __forceinline__ void ld2(const S* p, S* o) {
+#ifdef __CUDACC__
+  if constexpr (sizeof(S) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    o[0] = t.x; o[1] = t.y;
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    o[0] = t.x; o[1] = t.y;
+  }
+#else
+  o[0] = p[0]; o[1] = p[1];
+#endif
+}
+template <class S>
+__device__ __forceinline__ void ld4(const S* p, S* o) {
+#ifdef __CUDACC__
+  if constexpr (sizeof(S) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  } else {
+    ld2(p, o); ld2(p + 2, o + 2);
+  }
+#else
+  for (int e = 0; e < 4; ++e) o[e] = p[e];
+#endif
+}
+template <class S>
+__device__ __forceinline__ void st2(S* p, S a, S b) {
+#ifdef __CUDACC__
+  if constexpr (sizeof(S) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+#else
+  p[0] = a; p[1] = b;
+#endif
+}
+template <class S>
+__device__ __forceinline__ void st4(S* p, const S* v) {
+#ifdef __CUDACC__
+  if constexpr (sizeof(S) == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else { st2(p, v[0], v[1]); st2(p + 2, v[2], v[3]); }
+#else
+  for (int e = 0; e < 4; ++e) p[e] = v[e];
+#endif
+}
+// 6-vector stored in an 8-scalar record
+template <class S>
+__device__ __forceinline__ void ld6(const S* p, S* o) { ld4(p, o); ld2(p + 4, o + 4); }
+template <class S>
+__device__ __forceinline__ void st6(S* p, const S* v) { st4(p, v); st2(p + 4, v[4], v[5]); }
+// transform record E(9) r(3)
+template <class S>
+__device__ __forceinline__ void ld12(const S* p, S* o) { ld4(p, o); ld4(p + 4, o + 4); ld4(p + 8, o + 8); }

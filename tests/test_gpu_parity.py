@@ -12,7 +12,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 WORKLOAD = ["chain7", "tree12", "tree30"]
-RANDOM = [(3, 2), (6, 4), (9, 8), (13, 21), (1, 5)]
+RANDOM = [(3, 2), (6, 4), (9, 8), (13, 21), (1, 5), (20, 3), (32, 7)]
 TOL32 = 1e-4
 TOL64 = 1e-10
 
@@ -94,8 +94,13 @@ def test_lane_counts_agree(grid, key, lanes):
     m = grid.Model.from_robot(r)
     m.set_option("lanes", lanes)
     (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, 29, 7, torch.float64)
-    J = m.grad_fd(q, qd, tau).cpu().numpy()
-    assert col_rel_err(J, oracle.grad_fd(r, q64, qd64, tau64)) <= TOL64
+    try:
+        J = m.grad_fd(q, qd, tau).cpu().numpy()
+    except grid.GridError as e:
+        # a mapping whose per-warp workspace exceeds shared memory is refused
+        assert e.status == 1 and "shared memory" in str(e), e
+    else:
+        assert col_rel_err(J, oracle.grad_fd(r, q64, qd64, tau64)) <= TOL64
     (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, 29, 7, torch.float32)
     J = m.grad_fd(q, qd, tau).cpu().numpy()
     assert col_rel_err(J, oracle.grad_fd(r, q64, qd64, tau64)) <= TOL32
