@@ -128,6 +128,20 @@ grid_status grid_fd(const grid_model* model, int N, const float* q, const float*
 grid_status grid_grad_fd(const grid_model* model, int N, const float* q, const float* qd,
                          const float* tau, float* J, float* qdd, void* stream);
 
+/*
+ * grid_fd_vjp -- vector-Jacobian product through forward dynamics: for an
+ * upstream gradient gbar = dL/dqdd at qdd = FD(q, qd, tau),
+ *   dtau = M^-1 gbar,  dq = (dqdd/dq)^T gbar = -(dID/dq)^T M^-1 gbar,
+ *   dqd = (dqdd/dqd)^T gbar = -(dID/dqd)^T M^-1 gbar
+ * (Sec. IV-B, items 3 and 5, transposed). The RNEA derivatives are applied in
+ * reverse mode (one adjoint sweep); no n x 2n Jacobian is formed and the
+ * forward intermediates are recomputed from (q, qd, tau).
+ *   q, qd, tau, gbar [N][n] inputs; dq, dqd, dtau [N][n] outputs.
+ */
+grid_status grid_fd_vjp(const grid_model* model, int N, const float* q, const float* qd,
+                        const float* tau, const float* gbar, float* dq, float* dqd, float* dtau,
+                        void* stream);
+
 /* FP64 twins: same operations and layouts, the whole path in double. */
 grid_status grid_rnea_f64(const grid_model* model, int N, const double* q, const double* qd,
                           const double* qdd, double* tau, void* stream);
@@ -136,6 +150,9 @@ grid_status grid_fd_f64(const grid_model* model, int N, const double* q, const d
                         const double* tau, double* qdd, void* stream);
 grid_status grid_grad_fd_f64(const grid_model* model, int N, const double* q, const double* qd,
                              const double* tau, double* J, double* qdd, void* stream);
+grid_status grid_fd_vjp_f64(const grid_model* model, int N, const double* q, const double* qd,
+                            const double* tau, const double* gbar, double* dq, double* dqd,
+                            double* dtau, void* stream);
 
 /* grid_last_error -- thread-local description of the last failure ("" if none). */
 const char* grid_last_error(void);

@@ -20,7 +20,8 @@ import torch
 from . import _native
 from ._native import GRID_FP32, GRID_FP64, GRID_MIXED, GridError  # noqa: F401
 
-__all__ = ["Model", "GridError", "GRID_FP32", "GRID_MIXED", "GRID_FP64", "build"]
+__all__ = ["Model", "ForwardDynamics", "forward_dynamics", "GridError", "GRID_FP32", "GRID_MIXED",
+           "GRID_FP64", "build"]
 
 _PREC = {"fp32": GRID_FP32, "mixed": GRID_MIXED}
 
@@ -147,3 +148,38 @@ class Model:
         _native.call(self._fn("grid_grad_fd", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(J),
                      _ptr(qdd_out), self._stream())
         return (J, qdd_out) if return_qdd else J
+
+    def fd_vjp(self, q, qd, tau, gbar, out=None):
+        """Vector-Jacobian product through FD for gbar = dL/dqdd:
+        returns (dL/dq, dL/dqd, dL/dtau), each [N, n]. Forward intermediates are
+        recomputed from (q, qd, tau); no Jacobian is formed."""
+        N, dt, (q, qd, tau, gbar) = self._state(q, qd, tau, gbar)
+        if out is None:
+            out = tuple(torch.empty((N, self.n), dtype=dt, device=q.device) for _ in range(3))
+        dq, dqd, dtau = out
+        _native.call(self._fn("grid_fd_vjp", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(gbar),
+                     _ptr(dq), _ptr(dqd), _ptr(dtau), self._stream())
+        return dq, dqd, dtau
+
+
+class ForwardDynamics(torch.autograd.Function):
+    """qdd = FD(q, qd, tau) as a differentiable op. Forward: the FD kernel.
+    Backward: the vector-Jacobian-product kernel (reverse-mode RNEA sweep),
+    recomputing the forward intermediates; only q, qd, tau are saved."""
+
+    @staticmethod
+    def forward(ctx, model, q, qd, tau):
+        ctx.model = model
+        ctx.save_for_backward(q, qd, tau)
+        return model.fd(q, qd, tau).view(q.shape)
+
+    @staticmethod
+    def backward(ctx, gbar):
+        q, qd, tau = ctx.saved_tensors
+        dq, dqd, dtau = ctx.model.fd_vjp(q, qd, tau, gbar.contiguous())
+        return None, dq.view(q.shape), dqd.view(qd.shape), dtau.view(tau.shape)
+
+
+def forward_dynamics(model, q, qd, tau):
+    """Differentiable forward dynamics qdd = M^-1 (tau - RNEA(q, qd, 0))."""
+    return ForwardDynamics.apply(model, q, qd, tau)

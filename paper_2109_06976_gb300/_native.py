@@ -31,6 +31,8 @@ SIGNATURES = {
     "grid_minv_f64": [_P, _I, _P, _P, _P],
     "grid_fd_f64": [_P, _I, _P, _P, _P, _P, _P],
     "grid_grad_fd_f64": [_P, _I, _P, _P, _P, _P, _P, _P],
+    "grid_fd_vjp": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
+    "grid_fd_vjp_f64": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
 }
 
 

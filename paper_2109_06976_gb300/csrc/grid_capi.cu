@@ -12,18 +12,20 @@
 #include "grid_internal.h"
 
 template <class S, int MODE, bool MIXED>
-grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const S* x3, S* out, S* out2,
-                     cudaStream_t st);
+grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const S* x3, const S* x4,
+                     S* out, S* out2, S* out3, cudaStream_t st);
 
 #define GRID_DECLARE(S, MIXED)                                                                       \
   extern template grid_status dispatch<S, MODE_RNEA, MIXED>(const grid_model*, int, const S*,        \
-                                                            const S*, const S*, S*, S*, cudaStream_t); \
+                                                            const S*, const S*, const S*, S*, S*, S*, cudaStream_t); \
   extern template grid_status dispatch<S, MODE_MINV, MIXED>(const grid_model*, int, const S*,        \
-                                                            const S*, const S*, S*, S*, cudaStream_t); \
+                                                            const S*, const S*, const S*, S*, S*, S*, cudaStream_t); \
   extern template grid_status dispatch<S, MODE_FD, MIXED>(const grid_model*, int, const S*,          \
-                                                          const S*, const S*, S*, S*, cudaStream_t); \
+                                                          const S*, const S*, const S*, S*, S*, S*, cudaStream_t); \
   extern template grid_status dispatch<S, MODE_GRAD, MIXED>(const grid_model*, int, const S*,        \
-                                                            const S*, const S*, S*, S*, cudaStream_t);
+                                                            const S*, const S*, const S*, S*, S*, S*, cudaStream_t); \
+  extern template grid_status dispatch<S, MODE_VJP, MIXED>(const grid_model*, int, const S*,         \
+                                                           const S*, const S*, const S*, S*, S*, S*, cudaStream_t);
 GRID_DECLARE(float, false)
 GRID_DECLARE(float, true)
 GRID_DECLARE(double, false)
@@ -51,13 +53,13 @@ grid_status check_args(const grid_model* m, int N, std::initializer_list<const v
 }
 
 template <class S, int MODE>
-grid_status run(const grid_model* m, int N, const S* q, const S* qd, const S* x3, S* out, S* out2,
-                void* stream) {
+grid_status run(const grid_model* m, int N, const S* q, const S* qd, const S* x3, const S* x4, S* out,
+                S* out2, S* out3, void* stream) {
   if (N == 0) return GRID_OK;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (std::is_same<S, float>::value && m->prec == GRID_MIXED)
-    return dispatch<S, MODE, true>(m, N, q, qd, x3, out, out2, st);
-  return dispatch<S, MODE, false>(m, N, q, qd, x3, out, out2, st);
+    return dispatch<S, MODE, true>(m, N, q, qd, x3, x4, out, out2, out3, st);
+  return dispatch<S, MODE, false>(m, N, q, qd, x3, x4, out, out2, out3, st);
 }
 
 }  // namespace
@@ -145,47 +147,61 @@ grid_status grid_rnea(const grid_model* m, int N, const float* q, const float* q
                       float* tau, void* stream) {
   grid_status s = check_args<float>(m, N, {q, qd, tau}, {qdd});
   if (s != GRID_OK) return s;
-  return run<float, MODE_RNEA>(m, N, q, qd, qdd, tau, nullptr, stream);
+  return run<float, MODE_RNEA>(m, N, q, qd, qdd, nullptr, tau, nullptr, nullptr, stream);
 }
 grid_status grid_minv(const grid_model* m, int N, const float* q, float* Minv, void* stream) {
   grid_status s = check_args<float>(m, N, {q, Minv}, {});
   if (s != GRID_OK) return s;
-  return run<float, MODE_MINV>(m, N, q, nullptr, nullptr, Minv, nullptr, stream);
+  return run<float, MODE_MINV>(m, N, q, nullptr, nullptr, nullptr, Minv, nullptr, nullptr, stream);
 }
 grid_status grid_fd(const grid_model* m, int N, const float* q, const float* qd, const float* tau,
                     float* qdd, void* stream) {
   grid_status s = check_args<float>(m, N, {q, qd, tau, qdd}, {});
   if (s != GRID_OK) return s;
-  return run<float, MODE_FD>(m, N, q, qd, tau, qdd, nullptr, stream);
+  return run<float, MODE_FD>(m, N, q, qd, tau, nullptr, qdd, nullptr, nullptr, stream);
 }
 grid_status grid_grad_fd(const grid_model* m, int N, const float* q, const float* qd, const float* tau,
                          float* J, float* qdd, void* stream) {
   grid_status s = check_args<float>(m, N, {q, qd, tau, J}, {qdd});
   if (s != GRID_OK) return s;
-  return run<float, MODE_GRAD>(m, N, q, qd, tau, J, qdd, stream);
+  return run<float, MODE_GRAD>(m, N, q, qd, tau, nullptr, J, qdd, nullptr, stream);
 }
 grid_status grid_rnea_f64(const grid_model* m, int N, const double* q, const double* qd,
                           const double* qdd, double* tau, void* stream) {
   grid_status s = check_args<double>(m, N, {q, qd, tau}, {qdd});
   if (s != GRID_OK) return s;
-  return run<double, MODE_RNEA>(m, N, q, qd, qdd, tau, nullptr, stream);
+  return run<double, MODE_RNEA>(m, N, q, qd, qdd, nullptr, tau, nullptr, nullptr, stream);
 }
 grid_status grid_minv_f64(const grid_model* m, int N, const double* q, double* Minv, void* stream) {
   grid_status s = check_args<double>(m, N, {q, Minv}, {});
   if (s != GRID_OK) return s;
-  return run<double, MODE_MINV>(m, N, q, nullptr, nullptr, Minv, nullptr, stream);
+  return run<double, MODE_MINV>(m, N, q, nullptr, nullptr, nullptr, Minv, nullptr, nullptr, stream);
 }
 grid_status grid_fd_f64(const grid_model* m, int N, const double* q, const double* qd,
                         const double* tau, double* qdd, void* stream) {
   grid_status s = check_args<double>(m, N, {q, qd, tau, qdd}, {});
   if (s != GRID_OK) return s;
-  return run<double, MODE_FD>(m, N, q, qd, tau, qdd, nullptr, stream);
+  return run<double, MODE_FD>(m, N, q, qd, tau, nullptr, qdd, nullptr, nullptr, stream);
 }
 grid_status grid_grad_fd_f64(const grid_model* m, int N, const double* q, const double* qd,
                              const double* tau, double* J, double* qdd, void* stream) {
   grid_status s = check_args<double>(m, N, {q, qd, tau, J}, {qdd});
   if (s != GRID_OK) return s;
-  return run<double, MODE_GRAD>(m, N, q, qd, tau, J, qdd, stream);
+  return run<double, MODE_GRAD>(m, N, q, qd, tau, nullptr, J, qdd, nullptr, stream);
+}
+
+grid_status grid_fd_vjp(const grid_model* m, int N, const float* q, const float* qd, const float* tau,
+                        const float* gbar, float* dq, float* dqd, float* dtau, void* stream) {
+  grid_status s = check_args<float>(m, N, {q, qd, tau, gbar, dq, dqd, dtau}, {});
+  if (s != GRID_OK) return s;
+  return run<float, MODE_VJP>(m, N, q, qd, tau, gbar, dq, dqd, dtau, stream);
+}
+grid_status grid_fd_vjp_f64(const grid_model* m, int N, const double* q, const double* qd,
+                            const double* tau, const double* gbar, double* dq, double* dqd,
+                            double* dtau, void* stream) {
+  grid_status s = check_args<double>(m, N, {q, qd, tau, gbar, dq, dqd, dtau}, {});
+  if (s != GRID_OK) return s;
+  return run<double, MODE_VJP>(m, N, q, qd, tau, gbar, dq, dqd, dtau, stream);
 }
 
 }  // extern "C"

@@ -25,7 +25,7 @@ namespace {
 int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 // Per-knot shared-memory layout, in scalars of `ssize` bytes.
-KnotLayout make_layout(int n, int nsk, int nbranch, int ssize) {
+KnotLayout make_layout(int n, int nsk, int nbranch, int ssize, bool vjp) {
   KnotLayout L;
   int off = 0;
   auto take = [&](int count) { int o = off; off += round_up(count, 4); return o; };
@@ -46,9 +46,16 @@ KnotLayout make_layout(int n, int nsk, int nbranch, int ssize) {
   int r = 0;
   auto tr = [&](int count) { int o = r; r += round_up(count, 4); return o; };
   L.A = tr(8 * n); L.FO = tr(8 * n); L.FA = tr(8 * n); L.FSL = tr(8 * nbranch);
+  L.GB = L.LAM = L.PSI = L.AB = L.VB = L.SA = L.SV = L.DQ = L.DQD = 0;
+  if (vjp) {
+    r = std::max(r, b);          // gbar is staged before M^-1 runs: keep it clear of M^-1 temporaries
+    L.GB = tr(n); L.LAM = tr(n); L.PSI = tr(8 * n); L.AB = tr(8 * n); L.VB = tr(8 * n);
+    L.SA = tr(8 * nbranch); L.SV = tr(8 * nbranch); L.DQ = tr(n); L.DQD = tr(n);
+  }
   int c = 0;
   auto tc = [&](int count) { int o = c; c += round_up(count, 4); return o; };
   L.DC = tc(2 * n * n); L.JS = tc(2 * n * n);
+  if (vjp) { L.DC = 0; L.JS = r; c = r + round_up(3 * n, 4); }   // output staging after the VJP data
   off += std::max(b, std::max(r, c));
   // Knot stride: a multiple of 4 scalars, offset from a multiple of the bank
   // count so that groups of a warp touching the same field hit other banks.
@@ -217,7 +224,8 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
         D.sched[soff + s * T + l] = s < (int)lane[l].size() ? lane[l][s] : 0u;
     soff += S * T;
   }
-  D.L = make_layout(n, nsk, nbranch, 8);
+  D.L = make_layout(n, nsk, nbranch, 8, false);
+  D.LV = make_layout(n, nsk, nbranch, 8, true);
 
   // Float copy of everything; its own layout.
   ModelDev<float>& F = *mf;
@@ -241,6 +249,7 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
     for (int a = 0; a < 10; ++a) F.inert[k][a] = (float)D.inert[k][a];
   }
   for (int a = 0; a < 6; ++a) F.a0[a] = (float)D.a0[a];
-  F.L = make_layout(n, nsk, nbranch, 4);
+  F.L = make_layout(n, nsk, nbranch, 4, false);
+  F.LV = make_layout(n, nsk, nbranch, 4, true);
   return GRID_OK;
 }

@@ -12,7 +12,7 @@
 #endif
 
 // Kernel modes (one kernel template serves every entry point).
-enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3 };
+enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3, MODE_VJP = 4 };
 
 #define GRID_SCHED_MAX 4096    // step descriptors for all lane counts together
 #define GRID_NUM_LANE_CFG 3    // lanes per knot point: 8, 16, 32
@@ -51,6 +51,9 @@ struct KnotLayout {
                                 // FSL: force contributions to branch bodies (8 each)
   // derivative-column / product temporaries, relative to UNION
   int DC, JS;                   // dc [n][2n], J staging [n][2n] (caller order)
+  // vector-Jacobian product (VJP layout only), relative to UNION, after the RNEA temporaries
+  int GB, LAM, PSI, AB, VB, SA, SV, DQ, DQD;  // gbar (caller order), lambda, psi, adjoint seeds (8n each),
+                                              // branch slots (8 each), dL/dq, dL/dqd (internal order)
   int stride;                   // scalars per knot
 };
 
@@ -59,7 +62,8 @@ struct ModelDev {
   int n, maxd, nsk, ncomp, nbranch;
   int steps[GRID_NUM_LANE_CFG];      // steps per lane for 8, 16, 32 lanes
   int sched_off[GRID_NUM_LANE_CFG];  // offsets into sched
-  KnotLayout L;
+  KnotLayout L;                  // workspace of the RNEA / M^-1 / FD / gradient kernels
+  KnotLayout LV;                 // workspace of the vector-Jacobian-product kernel
   int parent[GRID_MAX_DOF];
   int depth[GRID_MAX_DOF];
   int sub_end[GRID_MAX_DOF];

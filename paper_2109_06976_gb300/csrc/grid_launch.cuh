@@ -24,8 +24,9 @@ __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
 __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict__ gm, int N,
                                                    const S* __restrict__ q, const S* __restrict__ qd,
-                                                   const S* __restrict__ x3, S* __restrict__ out,
-                                                   S* __restrict__ out2) {
+                                                   const S* __restrict__ x3, const S* __restrict__ x4,
+                                                   S* __restrict__ out, S* __restrict__ out2,
+                                                   S* __restrict__ out3) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int cfg = T == 8 ? 0 : (T == 16 ? 1 : 2);
   constexpr int head = align16(model_head_bytes<S>());
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict
   }
   __syncthreads();
   const int nsteps = (MODE == MODE_GRAD) ? M.steps[cfg] : 0;
+  const int stride = MODE == MODE_VJP ? M.LV.stride : M.L.stride;
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + head);
   for (int i = threadIdx.x; i < nsteps * T; i += blockDim.x) sched[i] = gm->sched[M.sched_off[cfg] + i];
   S* ws = reinterpret_cast<S*>(smem + head + align16(nsteps * T * 4));
@@ -44,10 +46,11 @@ __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict
   constexpr int G = 32 / T;
   const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  S* Wwarp = ws + warp * G * M.L.stride;
+  S* Wwarp = ws + warp * G * stride;
   const int ntiles = (N + G - 1) / G;
   for (int tile = blockIdx.x * wpb + warp; tile < ntiles; tile += gridDim.x * wpb)
-    process_tile<S, MODE, T, CPL, MAXD, MIXED>(M, sched, nsteps, Wwarp, lane32, tile * G, N, q, qd, x3, out, out2);
+    process_tile<S, MODE, T, CPL, MAXD, MIXED>(M, sched, nsteps, Wwarp, lane32, tile * G, N, q, qd, x3,
+                                               x4, out, out2, out3);
 }
 
 // ---------------------------------------------------------------- launcher
@@ -73,14 +76,15 @@ static inline DevInfo dev_info(int dev) {
 
 template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
 grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N,
-                     const S* q, const S* qd, const S* x3, S* out, S* out2, cudaStream_t st) {
+                     const S* q, const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3,
+                     cudaStream_t st) {
   auto kern = grid_kernel<S, MODE, T, CPL, MAXD, MIXED>;
   constexpr int cfg = T == 8 ? 0 : (T == 16 ? 1 : 2);
   constexpr int G = 32 / T;
   const int nsteps = (MODE == MODE_GRAD) ? hm->steps[cfg] : 0;
   const DevInfo di = dev_info(m->device);
   const size_t fixed = align16(model_head_bytes<S>()) + align16(nsteps * T * 4);
-  const size_t per_warp = (size_t)G * hm->L.stride * sizeof(S);
+  const size_t per_warp = (size_t)G * (MODE == MODE_VJP ? hm->LV.stride : hm->L.stride) * sizeof(S);
   int warps = kMaxWarps;
   while (warps > 1 && fixed + warps * per_warp > (size_t)di.smem_optin) --warps;
   const size_t smem = fixed + warps * per_warp;
@@ -111,7 +115,7 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
   const long tiles = (N + G - 1) / G;
   const long ctas_needed = (tiles + warps - 1) / warps;
   const int grid = (int)std::min<long>(ctas_needed, (long)di.nsm * per_sm);
-  kern<<<grid, threads, smem, st>>>(dm, N, q, qd, x3, out, out2);
+  kern<<<grid, threads, smem, st>>>(dm, N, q, qd, x3, x4, out, out2, out3);
   err = cudaGetLastError();
   if (err != cudaSuccess) {
     grid_set_error("kernel launch: %s", cudaGetErrorString(err));
@@ -122,16 +126,16 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
 
 template <class S, int MODE, int T, int CPL, bool MIXED>
 grid_status launch_d(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
-                     const S* qd, const S* x3, S* out, S* out2, cudaStream_t st) {
+                     const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st) {
   if (MODE == MODE_GRAD && hm->maxd > 8)
-    return launch_t<S, MODE, T, CPL, 32, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
-  return launch_t<S, MODE, T, CPL, 8, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
+    return launch_t<S, MODE, T, CPL, 32, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+  return launch_t<S, MODE, T, CPL, 8, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
 }
 
 // Picks the lane count T (option or by size) and the M^-1 columns per lane.
 template <class S, int MODE, bool MIXED>
-grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const S* x3, S* out, S* out2,
-                     cudaStream_t st) {
+grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const S* x3, const S* x4,
+                     S* out, S* out2, S* out3, cudaStream_t st) {
   const ModelDev<S>* hm;
   const ModelDev<S>* dm;
   if constexpr (std::is_same<S, float>::value) { hm = m->host_f; dm = m->dev_f; }
@@ -141,15 +145,15 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   if (T == 0) T = n <= 8 ? 8 : 16;
   const int cpl = (n + T - 1) / T;
   if (T == 8) {
-    if (cpl <= 1) return launch_d<S, MODE, 8, 1, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
-    if (cpl <= 2) return launch_d<S, MODE, 8, 2, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
-    return launch_d<S, MODE, 8, 4, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
+    if (cpl <= 1) return launch_d<S, MODE, 8, 1, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    if (cpl <= 2) return launch_d<S, MODE, 8, 2, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    return launch_d<S, MODE, 8, 4, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   }
   if (T == 16) {
-    if (cpl <= 1) return launch_d<S, MODE, 16, 1, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
-    return launch_d<S, MODE, 16, 2, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
+    if (cpl <= 1) return launch_d<S, MODE, 16, 1, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    return launch_d<S, MODE, 16, 2, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   }
-  if (T == 32) return launch_d<S, MODE, 32, 1, MIXED>(m, hm, dm, N, q, qd, x3, out, out2, st);
+  if (T == 32) return launch_d<S, MODE, 32, 1, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   grid_set_error("lanes option %d not in {0, 8, 16, 32}", T);
   return GRID_E_ARG;
 }
@@ -157,10 +161,12 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
 
 #define GRID_INSTANTIATE(S, MIXED)                                                                   \
   template grid_status dispatch<S, MODE_RNEA, MIXED>(const grid_model*, int, const S*, const S*,     \
-                                                     const S*, S*, S*, cudaStream_t);                \
+                                                     const S*, const S*, S*, S*, S*, cudaStream_t);  \
   template grid_status dispatch<S, MODE_MINV, MIXED>(const grid_model*, int, const S*, const S*,     \
-                                                     const S*, S*, S*, cudaStream_t);                \
+                                                     const S*, const S*, S*, S*, S*, cudaStream_t);  \
   template grid_status dispatch<S, MODE_FD, MIXED>(const grid_model*, int, const S*, const S*,       \
-                                                   const S*, S*, S*, cudaStream_t);                  \
+                                                   const S*, const S*, S*, S*, S*, cudaStream_t);  \
   template grid_status dispatch<S, MODE_GRAD, MIXED>(const grid_model*, int, const S*, const S*,     \
-                                                     const S*, S*, S*, cudaStream_t);
+                                                     const S*, const S*, S*, S*, S*, cudaStream_t);  \
+  template grid_status dispatch<S, MODE_VJP, MIXED>(const grid_model*, int, const S*, const S*,      \
+                                                    const S*, const S*, S*, S*, S*, cudaStream_t);

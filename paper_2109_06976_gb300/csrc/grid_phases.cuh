@@ -23,9 +23,10 @@
 template <class S>
 struct Ctx {
   const ModelDev<S>& M;
-  S* W;        // this knot point's workspace
-  int l;       // lane within the group, 0..T-1
-  int lane32;  // lane within the warp
+  const KnotLayout& L;  // workspace layout of this kernel mode
+  S* W;                 // this knot point's workspace
+  int l;                // lane within the group, 0..T-1
+  int lane32;           // lane within the warp
 };
 
 #ifndef GRID_SYNC
@@ -44,7 +45,7 @@ template <class S, int T>
 __device__ void ph_transforms(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   for (int k = c.l; k < M.n; k += T) {
     S qk = W[L.Q + M.perm[k]];
     S s, co;
@@ -84,7 +85,7 @@ template <class S, int T>
 __device__ void ph_subspaces(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   S* SK = W + L.SK;
   // With one row id per lane, the lane's row of the previous body is kept in
   // registers and reused when that body is the parent (always, for a chain).
@@ -155,7 +156,7 @@ template <class S, class P, int T, int CPL>
 __device__ void ph_minv(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   const int l = c.l;
   const int n = M.n;
   const int U = L.UNION;
@@ -328,7 +329,7 @@ template <class S, int T>
 __device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   const int U = L.UNION;
   for (int k = c.l; k < M.n; k += T) {
     const int dk = M.depth[k];
@@ -372,7 +373,7 @@ template <class S, int T>
 __device__ void ph_joint_forces(const Ctx<S>& c, int f_off, int out_off) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   for (int i = c.l; i < M.n; i += T) {
     const int di = M.depth[i];
     S acc = S(0);
@@ -392,7 +393,7 @@ template <class S, int T>
 __device__ void ph_fd(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   const int n = M.n;
   for (int i = c.l; i < n; i += T) {
     S acc = S(0);
@@ -413,7 +414,7 @@ template <class S, int T>
 __device__ void ph_update_and_forces(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   const int U = L.UNION;
   const int l = c.l;
   S* FA = W + U + L.FA;
@@ -510,7 +511,7 @@ template <class S, int T, int MAXD>
 __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, int nsteps) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   const int n = M.n;
   const int U = L.UNION;
   S* DC = W + U + L.DC;
@@ -613,7 +614,7 @@ template <class S, int T, int CPL>
 __device__ void ph_product(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
-  const KnotLayout& L = M.L;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   const int n = M.n, n2 = 2 * n, MS = L.MS;
   const int U = L.UNION;
   const S* DC = W + U + L.DC;
@@ -648,19 +649,145 @@ __device__ void ph_product(const Ctx<S>& c) {
   SYNC();
 }
 
+// ---------------------------------------------------------------- V
+// Vector-Jacobian product through FD. For gbar = dL/dqdd and lambda = M^-1 gbar:
+//   dL/dtau = lambda,  dL/dq = -(dID/dq)^T lambda,  dL/dqd = -(dID/dqd)^T lambda,
+// evaluated without forming dID by reverse-mode differentiation of RNEA. With
+// psi_k = sum_{m on the root path of k} lambda_m s_m^(k) (lambda used as a
+// joint velocity), lambda^T ID = sum_k psi_k . f_k, whose adjoint seeds are
+//   abar_k = I_k psi_k,  vbar_k = -psi_k x* gamma_k - I_k (v_k x psi_k).
+// One sweep from the leaves accumulates
+//   Abar_k = abar_k + sum_children X_c^T Abar_c,
+//   Vbar_k = vbar_k + (S_k qd_k) x* Abar_k + sum_children X_c^T Vbar_c,
+// and for joint k
+//   (dID/dqd)^T lambda |_k = S_k^T Vbar_k + Abar_k . (v_k x S_k)
+//   (dID/dq)^T lambda  |_k = Vbar_k . (v_k x S_k) + Abar_k . beta_k + F_k . (psi_k x S_k).
+template <class S, int T>
+__device__ void ph_vjp_seeds(const Ctx<S>& c) {
+  const ModelDev<S>& M = c.M;
+  S* W = c.W;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const int U = L.UNION;
+  const int n = M.n;
+  for (int i = c.l; i < n; i += T) {
+    S acc = S(0);
+    for (int j = M.comp_lo[i]; j < M.comp_hi[i]; ++j) acc += W[L.MINV + i * L.MS + j] * W[U + L.GB + M.perm[j]];
+    W[U + L.LAM + i] = acc;
+  }
+  SYNC();
+  for (int k = c.l; k < n; k += T) {
+    const int dk = M.depth[k];
+    const S* rows = W + L.SK + 8 * M.skoff[k];
+    S psi[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+    for (int d = 0; d <= dk; ++d) {
+      S s[8];
+      ld4(rows + 8 * d, s);
+      ld4(rows + 8 * d + 4, s + 4);
+      const S lam = W[U + L.LAM + (int)s[7]];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) psi[e] += s[e] * lam;
+    }
+    S v[6], g[6], t1[6], vxp[6], t2[6];
+    ld6(W + L.V + 8 * k, v);
+    ld6(W + L.GAM + 8 * k, g);
+    i_mul(M.inert[k], psi, t1);
+    st6(W + U + L.AB + 8 * k, t1);
+    crf_mul(psi, g, t1);
+    crm_mul(v, psi, vxp);
+    i_mul(M.inert[k], vxp, t2);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) t1[e] = -t1[e] - t2[e];
+    st6(W + U + L.VB + 8 * k, t1);
+    st6(W + U + L.PSI + 8 * k, psi);
+  }
+  for (int e = c.l; e < 8 * M.nbranch; e += T) { W[U + L.SA + e] = S(0); W[U + L.SV + e] = S(0); }
+  SYNC();
+}
+
+template <class S, int T>
+__device__ void ph_vjp_sweep(const Ctx<S>& c) {
+  const ModelDev<S>& M = c.M;
+  S* W = c.W;
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const int U = L.UNION;
+  const int l = c.l;
+  const int base = c.lane32 - l;
+  S* SA = W + U + L.SA;
+  S* SV = W + U + L.SV;
+  S ca = S(0), cv = S(0);
+  for (int k = M.n - 1; k >= 0; --k) {
+    const int p = M.parent[k];
+    const int br = M.branch[k];
+    const bool from_next = k + 1 < M.n && M.parent[k + 1] == k;
+    const S* ax = M.axis[k];
+    const S qdk = W[L.QD + M.perm[k]];
+    S ab = S(0), vb = S(0);
+    if (l < 6) {
+      ab = W[U + L.AB + 8 * k + l] + (from_next ? ca : S(0)) + (br >= 0 ? SA[8 * br + l] : S(0));
+      vb = W[U + L.VB + 8 * k + l] + (from_next ? cv : S(0)) + (br >= 0 ? SV[8 * br + l] : S(0));
+    }
+    S A[6], V[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) A[e] = GRID_SHFL(ab, base + e);
+    {
+      // (S qd) x* Abar = [a qd x Abar_ang; a qd x Abar_lin]
+      const S sq[3] = {ax[0] * qdk, ax[1] * qdk, ax[2] * qdk};
+      S t[6];
+      cross3(sq, A, t);
+      cross3(sq, A + 3, t + 3);
+      S add = t[0];
+#pragma unroll
+      for (int e = 1; e < 6; ++e) add = (l == e) ? t[e] : add;
+      if (l < 6) vb += add;
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e) V[e] = GRID_SHFL(vb, base + e);
+    if (l == 0) {
+      S v[6], B[6], F[6], psi[6], vxs[6], pxs[6];
+      ld6(W + L.V + 8 * k, v);
+      ld6(W + L.BET + 8 * k, B);
+      ld6(W + U + L.FA + 8 * k, F);
+      ld6(W + U + L.PSI + 8 * k, psi);
+      cross3(v, ax, vxs);
+      cross3(v + 3, ax, vxs + 3);
+      cross3(psi, ax, pxs);
+      cross3(psi + 3, ax, pxs + 3);
+      S gqd = ax[0] * V[0] + ax[1] * V[1] + ax[2] * V[2];
+      S gq = S(0);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        gqd += A[e] * vxs[e];
+        gq += V[e] * vxs[e] + A[e] * B[e] + F[e] * pxs[e];
+      }
+      W[U + L.DQ + k] = -gq;
+      W[U + L.DQD + k] = -gqd;
+    }
+    if (p >= 0 && l < 6) {
+      S E[12];
+      ld12(W + L.X + 12 * k, E);
+      const S xa = xt_mul_c(E, E + 9, A, l);
+      const S xv = xt_mul_c(E, E + 9, V, l);
+      if (p == k - 1) { ca = xa; cv = xv; }
+      else { SA[8 * M.branch[p] + l] += xa; SV[8 * M.branch[p] + l] += xv; }
+    }
+  }
+  SYNC();
+}
+
 // One warp processes knot points k0 .. k0 + 32/T - 1 (those < N).
 template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
 __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ sched, int nsteps,
                              S* Wwarp, int lane32, int k0, int N, const S* __restrict__ q,
-                             const S* __restrict__ qd, const S* __restrict__ x3, S* __restrict__ out,
-                             S* __restrict__ out2) {
+                             const S* __restrict__ qd, const S* __restrict__ x3,
+                             const S* __restrict__ x4, S* __restrict__ out, S* __restrict__ out2,
+                             S* __restrict__ out3) {
   using P = typename std::conditional<MIXED, double, S>::type;
-  const KnotLayout& L = M.L;
+  const KnotLayout& L = MODE == MODE_VJP ? M.LV : M.L;
   const int n = M.n;
   constexpr int G = 32 / T;
   const int g = lane32 / T;
   S* W = Wwarp + g * L.stride;
-  const Ctx<S> c{M, W, lane32 % T, lane32};
+  const Ctx<S> c{M, L, W, lane32 % T, lane32};
   const int out_per = MODE == MODE_MINV ? n * n : (MODE == MODE_GRAD ? 2 * n * n : n);
   const int nvalid = min(G, N - k0);
   // stage inputs (coalesced across the warp)
@@ -672,7 +799,8 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
     Wk[L.Q + i] = ok ? q[gi] : S(0);
     if (MODE != MODE_MINV) Wk[L.QD + i] = ok ? qd[gi] : S(0);
     if (MODE == MODE_RNEA) Wk[L.TAU + i] = (ok && x3) ? x3[gi] : S(0);
-    if (MODE == MODE_FD || MODE == MODE_GRAD) Wk[L.TAU + i] = ok ? x3[gi] : S(0);
+    if (MODE == MODE_FD || MODE == MODE_GRAD || MODE == MODE_VJP) Wk[L.TAU + i] = ok ? x3[gi] : S(0);
+    if (MODE == MODE_VJP) Wk[L.UNION + L.GB + i] = ok ? x4[gi] : S(0);
   }
   SYNC();
   ph_transforms<S, T>(c);
@@ -688,10 +816,14 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
       ph_rnea_bodies<S, T>(c, -1);
       ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);    // CB = RNEA(q, qd, 0)
       ph_fd<S, T>(c);
+      if (MODE == MODE_GRAD || MODE == MODE_VJP) ph_update_and_forces<S, T>(c);
       if (MODE == MODE_GRAD) {
-        ph_update_and_forces<S, T>(c);
         ph_columns<S, T, MAXD>(c, sched, nsteps);
         ph_product<S, T, CPL>(c);
+      }
+      if (MODE == MODE_VJP) {
+        ph_vjp_seeds<S, T>(c);
+        ph_vjp_sweep<S, T>(c);
       }
     }
   }
@@ -703,10 +835,27 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
     for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.QDD + i];
   } else if (MODE == MODE_MINV) {
     for (int e = c.l; e < n * n; e += T) OS[M.perm[e / n] * n + M.perm[e % n]] = W[L.MINV + (e / n) * L.MS + e % n];
+  } else if (MODE == MODE_VJP) {
+    for (int i = c.l; i < n; i += T) {
+      OS[M.perm[i]] = W[L.UNION + L.DQ + i];
+      OS[n + M.perm[i]] = W[L.UNION + L.DQD + i];
+      OS[2 * n + M.perm[i]] = W[L.UNION + L.LAM + i];
+    }
   } else if (out2) {
     for (int i = c.l; i < n; i += T) W[L.CB + M.perm[i]] = W[L.QDD + i];
   }
   SYNC();
+  if (MODE == MODE_VJP) {
+    for (int e = lane32; e < nvalid * n; e += 32) {
+      const int kk = e / n, r = e % n;
+      const S* os = Wwarp + kk * L.stride + L.UNION + L.JS;
+      out[(size_t)k0 * n + e] = os[r];
+      out2[(size_t)k0 * n + e] = os[n + r];
+      out3[(size_t)k0 * n + e] = os[2 * n + r];
+    }
+    SYNC();
+    return;
+  }
   for (int e = lane32; e < nvalid * out_per; e += 32) {
     const int kk = e / out_per, r = e % out_per;
     out[(size_t)k0 * out_per + e] = Wwarp[kk * L.stride + L.UNION + L.JS + r];
