@@ -174,6 +174,30 @@ def cpu_oracle_rate(robot, seconds_min=10.0, seconds_max=30.0, threads=None):
     return done / el, threads, done, el
 
 
+def serve_leg(grid, seconds, rate_hz=20000.0, seed=5005):
+    """Serving workload: open-loop Poisson arrivals at rate_hz, robot uniform
+    over the 7/12/30-DoF models, horizon uniform over {16, 32, 64, 128, 256};
+    1 s warm-up, then `seconds` measured. Native producer/consumer threads."""
+    names = ["chain7", "tree12", "tree30"]
+    models = [grid.Model.from_robot(gi.robot(r)) for r in names]
+    K = 1024
+    pools = [np.stack(gi.states(m.n, K, gi.workload_seed(5, K) + i)).astype(np.float32)
+             for i, m in enumerate(models)]
+    horizons = [16, 32, 64, 128, 256]
+    srv = grid.Server(models, ring_slots=2048, arena_bytes=1 << 30)
+    srv.start()
+    srv.bench(rate_hz, 1.0, seed, horizons, pools)
+    st = srv.bench(rate_hz, seconds, seed + 1, horizons, pools)
+    status = srv.stop()
+    srv.close()
+    return {"rate_hz": rate_hz, "seconds": seconds, "robots": names, "horizons": horizons,
+            "completed": int(st["completed"]), "knot_points_per_s": st["knot_points"] / st["wall_s"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "p50_ms_h128": st["p50_ms_h128"],
+            "p99_ms_h128": st["p99_ms_h128"], "max_ms": st["max_ms"], "refused": int(st["refused"]),
+            "status": int(st["status"]), "kernel_status": int(status),
+            "latency": "scheduled arrival to the host seeing the done flag"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -285,6 +309,10 @@ def run_ours(args):
     J1 = J[:KNOTS]
     sec1 = time_steps(lambda: model.grad_fd(q1, qd1, tau1, out=J1), 200, 20, stream, None)
 
+    serve = None
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        serve = serve_leg(grid, args.serve_seconds)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, threads, done, el = cpu_oracle_rate(robot)
@@ -315,6 +343,7 @@ def run_ours(args):
             "fp64_plain": {"value": fp64_value, "unit": UNIT, "knot_points_per_launch": Nd},
             "tree12": {"value": t12_value, "unit": UNIT, "knot_points_per_launch": Nk // 2},
             "latency_n128_us": sec1 / 200 * 1e6,
+            "serve": serve,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": args.steps,
@@ -334,6 +363,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--traj", type=int, default=TRAJ, help="trajectories of 128 knot points per step")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="measured seconds of the serving leg (0 to skip)")
     ap.add_argument("--only-main", action="store_true",
                     help="time only the main FP32 step (used for profiling captures)")
     args = ap.parse_args()

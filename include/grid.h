@@ -154,6 +154,61 @@ grid_status grid_fd_vjp_f64(const grid_model* model, int N, const double* q, con
                             const double* tau, const double* gbar, double* dq, double* dqd,
                             double* dtau, void* stream);
 
+/*
+ * Serving: a persistent kernel computes grid_grad_fd for a stream of requests
+ * (mixed robots and horizons) with continuous batching. Requests are published
+ * into a ring of `ring_slots` slots in mapped pinned host memory; their states
+ * and Jacobians live in a pinned I/O arena of `arena_bytes` that the GPU reads
+ * and writes directly. A submission is admitted when its ring slot is free and
+ * its I/O fits in the arena; otherwise it returns GRID_E_NOMEM and the caller
+ * retries after collecting results. Tiles of 2 knot points from all published
+ * requests are claimed by warps in publication order, so requests that arrive
+ * while others run start at once and overlap on the device. Every wait in the
+ * kernel is bounded: with no new work for the idle timeout (default 2 s) the
+ * kernel ends with GRID_E_TIMEOUT. All models must be FP32 models of the
+ * current device; the server runs in FP32 with 16 lanes per knot point.
+ */
+typedef struct grid_server grid_server;
+
+/* grid_server_create -- allocate the ring, control block and arena (host). */
+grid_status grid_server_create(const grid_model* const* models, int nmodels, int ring_slots,
+                               size_t arena_bytes, grid_server** out);
+/* grid_server_set_idle_timeout -- idle limit of the persistent kernel (before start). */
+grid_status grid_server_set_idle_timeout(grid_server* server, double seconds);
+/* grid_server_start -- launch the persistent kernel on `stream` (asynchronous). */
+grid_status grid_server_start(grid_server* server, void* stream);
+/*
+ * grid_server_submit -- copy one request's host states (q, qd, tau: [H][n],
+ * n of model `model`) into the arena and publish it; *request_id receives its
+ * id. GRID_E_NOMEM: no free slot or arena space right now.
+ */
+grid_status grid_server_submit(grid_server* server, int model, int H, const float* q,
+                               const float* qd, const float* tau, long long* request_id);
+/*
+ * grid_server_result -- wait up to wait_us microseconds (0 = poll once) for a
+ * request; on success copy its Jacobians [H][n][2n] to host J (NULL to skip)
+ * and release its slot and arena space. GRID_E_TIMEOUT if not done yet or the
+ * kernel has stopped.
+ */
+grid_status grid_server_result(grid_server* server, long long request_id, float* J, int wait_us);
+/* grid_server_stop -- ask the kernel to exit, wait for it, return its status. */
+grid_status grid_server_stop(grid_server* server);
+/* grid_server_kernel_status -- GRID_OK while healthy, GRID_E_TIMEOUT after an idle exit. */
+int grid_server_kernel_status(const grid_server* server);
+/* grid_server_destroy -- stop if running and free everything. */
+grid_status grid_server_destroy(grid_server* server);
+/*
+ * grid_server_bench -- open-loop Poisson load for `seconds` at `rate_hz`:
+ * robot uniform over the server's models, horizon uniform over horizons[nh],
+ * states sliced from pools[model] ([3][pool_knots][n]: q, qd, tau). Latency
+ * runs from each scheduled arrival to the host seeing its done flag.
+ * stats[9]: completed, knot points, wall s, p50 ms, p99 ms, p50 ms (H = 128),
+ * p99 ms (H = 128), max ms, refused submissions.
+ */
+grid_status grid_server_bench(grid_server* server, double rate_hz, double seconds,
+                              unsigned long long seed, const int* horizons, int nh,
+                              const float* const* pools, int pool_knots, double* stats);
+
 /* grid_last_error -- thread-local description of the last failure ("" if none). */
 const char* grid_last_error(void);
 

@@ -20,8 +20,8 @@ import torch
 from . import _native
 from ._native import GRID_FP32, GRID_FP64, GRID_MIXED, GridError  # noqa: F401
 
-__all__ = ["Model", "ForwardDynamics", "forward_dynamics", "GridError", "GRID_FP32", "GRID_MIXED",
-           "GRID_FP64", "build"]
+__all__ = ["Model", "Server", "ForwardDynamics", "forward_dynamics", "GridError", "GRID_FP32",
+           "GRID_MIXED", "GRID_FP64", "build"]
 
 _PREC = {"fp32": GRID_FP32, "mixed": GRID_MIXED}
 
@@ -183,3 +183,80 @@ class ForwardDynamics(torch.autograd.Function):
 def forward_dynamics(model, q, qd, tau):
     """Differentiable forward dynamics qdd = M^-1 (tau - RNEA(q, qd, 0))."""
     return ForwardDynamics.apply(model, q, qd, tau)
+
+
+class Server:
+    """Persistent-kernel server for gradient-of-FD requests of mixed robots and
+    horizons (continuous batching; see include/grid.h). Host-side arrays are
+    numpy float32 [H, n]."""
+
+    def __init__(self, models, ring_slots=256, arena_bytes=256 << 20, idle_timeout=2.0):
+        lib = _native.load()
+        self.models = list(models)
+        arr = (ctypes.c_void_p * len(self.models))(*[m.handle.value for m in self.models])
+        h = ctypes.c_void_p()
+        _native.check("grid_server_create", lib.grid_server_create(arr, len(self.models), ring_slots,
+                                                                   arena_bytes, ctypes.byref(h)))
+        self._h = h
+        _native.call("grid_server_set_idle_timeout", h, float(idle_timeout))
+        self._stream = None
+
+    def start(self, stream=None):
+        self._stream = stream or torch.cuda.Stream()
+        _native.call("grid_server_start", self._h, ctypes.c_void_p(self._stream.cuda_stream))
+
+    def submit(self, model_index, q, qd, tau):
+        """Returns a request id, or None if no slot / arena space is free now."""
+        arrs = [np.ascontiguousarray(x, dtype=np.float32) for x in (q, qd, tau)]
+        H = arrs[0].shape[0]
+        rid = ctypes.c_longlong()
+        st = _native.load().grid_server_submit(self._h, model_index, H,
+                                               *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                               ctypes.byref(rid))
+        if st == 5:           # GRID_E_NOMEM: not admitted now
+            return None
+        _native.check("grid_server_submit", st)
+        return rid.value
+
+    def result(self, rid, H, n, wait_us=1_000_000):
+        """Jacobians [H, n, 2n] (numpy), or None if not done within wait_us."""
+        J = np.empty((H, n, 2 * n), dtype=np.float32)
+        st = _native.load().grid_server_result(self._h, rid, J.ctypes.data_as(ctypes.c_void_p), int(wait_us))
+        if st == 6:
+            return None
+        _native.check("grid_server_result", st)
+        return J
+
+    def kernel_status(self):
+        return _native.load().grid_server_kernel_status(self._h)
+
+    def stop(self):
+        """Stop the persistent kernel; returns its status code (0 = ok)."""
+        return _native.load().grid_server_stop(self._h)
+
+    def bench(self, rate_hz, seconds, seed, horizons, pools):
+        """Open-loop Poisson benchmark (native producer/consumer threads).
+        pools[m]: float32 [3, K, n_m] (q, qd, tau). Returns a dict of stats."""
+        K = pools[0].shape[1]
+        keep = [np.ascontiguousarray(p, dtype=np.float32) for p in pools]
+        ptrs = (ctypes.c_void_p * len(keep))(*[p.ctypes.data for p in keep])
+        hz = (ctypes.c_int * len(horizons))(*horizons)
+        stats = (ctypes.c_double * 9)()
+        st = _native.load().grid_server_bench(self._h, float(rate_hz), float(seconds), int(seed), hz,
+                                              len(horizons), ptrs, K, stats)
+        keys = ["completed", "knot_points", "wall_s", "p50_ms", "p99_ms", "p50_ms_h128", "p99_ms_h128",
+                "max_ms", "refused"]
+        out = dict(zip(keys, list(stats)))
+        out["status"] = st
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _native.load().grid_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -33,6 +33,14 @@ SIGNATURES = {
     "grid_grad_fd_f64": [_P, _I, _P, _P, _P, _P, _P, _P],
     "grid_fd_vjp": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
     "grid_fd_vjp_f64": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
+    "grid_server_create": [_P, _I, _I, ctypes.c_size_t, ctypes.POINTER(_P)],
+    "grid_server_set_idle_timeout": [_P, ctypes.c_double],
+    "grid_server_start": [_P, _P],
+    "grid_server_submit": [_P, _I, _I, _P, _P, _P, ctypes.POINTER(ctypes.c_longlong)],
+    "grid_server_result": [_P, ctypes.c_longlong, _P, _I],
+    "grid_server_stop": [_P],
+    "grid_server_destroy": [_P],
+    "grid_server_bench": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong, _P, _I, _P, _I, _P],
 }
 
 
@@ -69,6 +77,8 @@ def load(build_if_missing: bool = False):
         lib.grid_last_error.restype = ctypes.c_char_p
         lib.grid_model_dof.argtypes = [_P]
         lib.grid_model_dof.restype = _I
+        lib.grid_server_kernel_status.argtypes = [_P]
+        lib.grid_server_kernel_status.restype = _I
         _lib = lib
         return lib
 
