@@ -175,7 +175,9 @@ grid_status grid_server_create(const grid_model* const* models, int nmodels, int
                                size_t arena_bytes, grid_server** out);
 /* grid_server_set_idle_timeout -- idle limit of the persistent kernel (before start). */
 grid_status grid_server_set_idle_timeout(grid_server* server, double seconds);
-/* grid_server_start -- launch the persistent kernel on `stream` (asynchronous). */
+/* grid_server_start -- launch the persistent kernel on `stream` (asynchronous; NULL = a
+ * non-blocking stream of the server's own, so that it neither waits for nor holds up
+ * work on the legacy default stream). */
 grid_status grid_server_start(grid_server* server, void* stream);
 /*
  * grid_server_submit -- copy one request's host states (q, qd, tau: [H][n],

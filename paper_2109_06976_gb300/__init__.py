@@ -202,8 +202,11 @@ class Server:
         self._stream = None
 
     def start(self, stream=None):
-        self._stream = stream or torch.cuda.Stream()
-        _native.call("grid_server_start", self._h, ctypes.c_void_p(self._stream.cuda_stream))
+        """Launch the persistent kernel (on its own non-blocking stream unless
+        one is given)."""
+        self._stream = stream
+        _native.call("grid_server_start", self._h,
+                     None if stream is None else ctypes.c_void_p(stream.cuda_stream))
 
     def submit(self, model_index, q, qd, tau):
         """Returns a request id, or None if no slot / arena space is free now."""

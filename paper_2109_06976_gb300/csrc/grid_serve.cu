@@ -194,6 +194,7 @@ struct grid_server {
   int units = 0;
   std::mutex mu;
   cudaStream_t stream = nullptr;
+  bool own_stream = false;
   bool running = false;
   size_t smem = 0;
   int grid = 0, threads = 0;
@@ -307,7 +308,15 @@ grid_status grid_server_set_idle_timeout(grid_server* s, double seconds) {
 
 grid_status grid_server_start(grid_server* s, void* stream) {
   if (!s || s->running) { grid_set_error("grid_server_start: bad server or already running"); return GRID_E_ARG; }
-  s->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (stream) {
+    s->stream = reinterpret_cast<cudaStream_t>(stream);
+  } else if (!s->own_stream) {
+    // a non-blocking stream of its own: the persistent kernel must not hold up
+    // (or wait for) work on the legacy default stream
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { grid_set_error("grid_server_start: %s", cudaGetErrorString(e)); return GRID_E_CUDA; }
+    s->own_stream = true;
+  }
   std::memset(s->ctl, 0, sizeof(ServeCtl));
   s->units = 0;
   cudaMemsetAsync(s->args.next_unit, 0, sizeof(int), s->stream);
@@ -428,6 +437,7 @@ grid_status grid_server_destroy(grid_server* s) {
   cudaFreeHost(s->arena);
   cudaFree(s->args.next_unit);
   cudaFree(s->args.tiles_done);
+  if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
   return GRID_OK;
 }
