@@ -211,6 +211,32 @@ grid_status grid_server_bench(grid_server* server, double rate_hz, double second
                               unsigned long long seed, const int* horizons, int nh,
                               const float* const* pools, int pool_knots, double* stats);
 
+/*
+ * grid_serve_batch_static -- gradient of FD for a fixed list of requests of
+ * mixed robots and horizons, without allocating anything. (The paper has no
+ * counterpart; this serves callers that may not allocate device memory once
+ * running, such as a real-time control loop, where cudaMalloc can synchronise
+ * the device and take unbounded time, or a host application that owns all
+ * device memory and only lends the library its buffers.)
+ *   models[nmodels]     FP32 models of the current device
+ *   req_model, req_H    host arrays [nreq]: model index and knot points
+ *   q, qd, tau          host arrays [nreq] of DEVICE pointers, each [H][n]
+ *   J                   host array [nreq] of DEVICE pointers, each [H][n][2n]
+ * Runs the serving kernel in one-shot form on `stream`. Its scratch (request
+ * descriptors, control block, counters) is a fixed array of about 18.5 KB that
+ * the library holds on every device it is loaded on until the process exits;
+ * 1 <= nreq <= 256 per call, larger lists are refused with GRID_E_ARG. The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Calls share the array and overwrite its contents, so calls that
+ * overlap on the GPU (different streams, or another call before this one's
+ * kernel has finished) race; serialise them.
+ */
+grid_status grid_serve_batch_static(const grid_model* const* models, int nmodels, int nreq,
+                                    const int* req_model, const int* req_H, const float* const* q,
+                                    const float* const* qd, const float* const* tau, float* const* J,
+                                    void* stream);
+
 /* grid_last_error -- thread-local description of the last failure ("" if none). */
 const char* grid_last_error(void);
 

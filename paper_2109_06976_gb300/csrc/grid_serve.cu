@@ -562,3 +562,153 @@ grid_status grid_server_bench(grid_server* s, double rate_hz, double seconds, un
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free batch entry point
+// Some callers may not allocate device memory once they are running: a
+// real-time control loop that must not call cudaMalloc (it can synchronise the
+// device and take unbounded time), or a host application that owns every byte
+// of the device and hands the library only its input and output buffers. For
+// them grid_serve_batch_static runs a fixed list of requests through the same
+// serving kernel in one-shot form, keeping the kernel's scratch (request
+// descriptors, control block, done flags and tile counters) in the fixed
+// file-scope array below instead of memory allocated per server.
+namespace {
+
+constexpr int kStaticMaxReq = 256;        // requests per call (the array's limit)
+
+struct StaticScratch {
+  ServeReq reqs[kStaticMaxReq];
+  ServeCtl ctl;
+  int done[kStaticMaxReq];
+  int next_unit;
+  int tiles_done[kStaticMaxReq];
+};
+
+// Lives on every device that loads this library until the process exits
+// (about 18.5 KB). In host code the name is only a stand-in for the symbol;
+// its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScratch)];
+
+std::mutex g_static_mu;
+void* g_static_addr[64] = {nullptr};      // per device, filled by the first call on it
+
+}  // namespace
+
+extern "C" grid_status grid_serve_batch_static(const grid_model* const* models, int nmodels, int nreq,
+                                               const int* req_model, const int* req_H,
+                                               const float* const* q, const float* const* qd,
+                                               const float* const* tau, float* const* J, void* stream) {
+  if (!models || nmodels < 1 || nmodels > kMaxModels || !req_model || !req_H || !q || !qd || !tau || !J) {
+    grid_set_error("grid_serve_batch_static: null or bad argument");
+    return GRID_E_ARG;
+  }
+  if (nreq < 1 || nreq > kStaticMaxReq) {
+    grid_set_error("grid_serve_batch_static: %d requests; one call takes 1 to %d", nreq, kStaticMaxReq);
+    return GRID_E_ARG;
+  }
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    grid_set_error("grid_serve_batch_static: no current device");
+    return GRID_E_CUDA;
+  }
+  ServeArgs a{};
+  int max_stride = 0, max_sched = 0;
+  for (int i = 0; i < nmodels; ++i) {
+    if (!models[i] || models[i]->device != dev) {
+      grid_set_error("grid_serve_batch_static: model %d missing or on another device", i);
+      return GRID_E_ARG;
+    }
+    a.models[i] = models[i]->dev_f;
+    max_stride = std::max(max_stride, models[i]->host_f->L.stride);
+    max_sched = std::max(max_sched, models[i]->host_f->steps[1] * kServeT);
+  }
+  // Set-up once per device, with that device current: the array's device address.
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+      e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
+      if (e != cudaSuccess) {
+        g_static_addr[dev] = nullptr;
+        grid_set_error("grid_serve_batch_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        return GRID_E_CUDA;
+      }
+    }
+    base = g_static_addr[dev];
+  }
+  // Descriptors and counters, prepared on the host stack and copied into the array
+  // (the previous call's contents are overwritten; counters start at zero).
+  StaticScratch h;
+  std::memset(&h, 0, sizeof(h));
+  int units = 0;
+  for (int i = 0; i < kStaticMaxReq; ++i) { h.reqs[i].seq = -1; h.done[i] = -1; }
+  for (int i = 0; i < nreq; ++i) {
+    const int m = req_model[i];
+    if (m < 0 || m >= nmodels || req_H[i] < 1 || !q[i] || !qd[i] || !tau[i] || !J[i] ||
+        ((uintptr_t)q[i] | (uintptr_t)qd[i] | (uintptr_t)tau[i] | (uintptr_t)J[i]) % sizeof(float)) {
+      grid_set_error("grid_serve_batch_static: request %d has a bad model, horizon or pointer", i);
+      return GRID_E_ARG;
+    }
+    ServeReq& r = h.reqs[i];
+    r.q = (unsigned long long)q[i];
+    r.qd = (unsigned long long)qd[i];
+    r.tau = (unsigned long long)tau[i];
+    r.J = (unsigned long long)J[i];
+    r.model = m;
+    r.H = req_H[i];
+    r.first_unit = units;
+    r.nunits = (req_H[i] + kServeG - 1) / kServeG;
+    r.seq = i;
+    units += r.nunits;
+  }
+  h.ctl.published_units = units;         // everything is published up front ...
+  h.ctl.stop = 1;                         // ... and warps leave once the units run out
+  StaticScratch* d = reinterpret_cast<StaticScratch*>(base);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  e = cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    grid_set_error("grid_serve_batch_static: copy of descriptors: %s", cudaGetErrorString(e));
+    return GRID_E_CUDA;
+  }
+  a.nmodels = nmodels;
+  a.ring = nreq;
+  a.sched_words = max_sched;
+  a.ws_stride = kServeG * max_stride;
+  a.reqs = d->reqs;
+  a.ctl = &d->ctl;
+  a.done = d->done;
+  a.next_unit = &d->next_unit;
+  a.tiles_done = d->tiles_done;
+  a.idle_ns = 1000000000ull;
+  const size_t per_warp = align16s(model_head_bytes<float>()) + align16s(a.sched_words * 4) +
+                          (size_t)a.ws_stride * 4;
+  int optin = 0, nsm = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int warps = kMaxWarps;
+  while (warps > 1 && warps * per_warp > (size_t)optin) --warps;
+  if (warps * per_warp > (size_t)optin) {
+    grid_set_error("grid_serve_batch_static: per-warp workspace %zu B exceeds shared memory", per_warp);
+    return GRID_E_ARG;
+  }
+  e = cudaFuncSetAttribute(grid_serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) {
+    grid_set_error("grid_serve_batch_static: cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    return GRID_E_CUDA;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_serve_kernel, 32 * warps, warps * per_warp);
+  if (per_sm < 1) {
+    grid_set_error("grid_serve_batch_static: kernel does not fit on an SM");
+    return GRID_E_CUDA;
+  }
+  const int blocks = std::min(nsm * per_sm, (units + warps - 1) / warps);
+  grid_serve_kernel<<<blocks, 32 * warps, warps * per_warp, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    grid_set_error("grid_serve_batch_static: launch: %s", cudaGetErrorString(e));
+    return GRID_E_CUDA;
+  }
+  return GRID_OK;
+}
