@@ -40,7 +40,7 @@ KnotLayout make_layout(int n, int nsk, int nbranch, int ssize, bool vjp) {
   auto tb = [&](int count) { int o = b; b += round_up(count, 4); return o; };
   L.UB = tb(8 * n);
   L.DINV = tb(ssize == 4 ? 2 * n : n);     // doubles (mixed mode stores them in pairs of floats)
-  L.CT = tb(48);
+  L.CT = tb(96);                           // two 6 x 8 buffers, alternating by body
   L.BIA = tb(36 * nbranch);
   L.BP = tb(6 * n * nbranch);
   int r = 0;
@@ -166,6 +166,21 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
     D.inert[k][7] = p[7] - m * cx * cy;
     D.inert[k][8] = p[8] - m * cx * cz;
     D.inert[k][9] = p[9] - m * cy * cz;
+    // full 6x6 spatial inertia [Ibar h~; h~^T m1], stored by columns
+    const double* in = D.inert[k];
+    const double h[3] = {in[1], in[2], in[3]};
+    const double Ib[3][3] = {{in[4], in[7], in[8]}, {in[7], in[5], in[9]}, {in[8], in[9], in[6]}};
+    const double hx[3][3] = {{0, -h[2], h[1]}, {h[2], 0, -h[0]}, {-h[1], h[0], 0}};
+    double I6[6][6];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        I6[a][b] = Ib[a][b];
+        I6[a][b + 3] = hx[a][b];
+        I6[a + 3][b] = hx[b][a];
+        I6[a + 3][b + 3] = a == b ? m : 0.0;
+      }
+    for (int col = 0; col < 6; ++col)
+      for (int row = 0; row < 6; ++row) D.Icol[k][col][row] = I6[row][col];
   }
   D.a0[0] = D.a0[1] = D.a0[2] = 0.0;
   D.a0[3] = -gravity[0]; D.a0[4] = -gravity[1]; D.a0[5] = -gravity[2];
@@ -244,11 +259,14 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
   std::memcpy(F.et_ident, D.et_ident, sizeof(D.et_ident));
   std::memcpy(F.sched, D.sched, sizeof(D.sched));
   for (int k = 0; k < GRID_MAX_DOF; ++k) {
-    for (int a = 0; a < 3; ++a) { F.axis[k][a] = (float)D.axis[k][a]; F.rT[k][a] = (float)D.rT[k][a]; }
+    for (int a = 0; a < 4; ++a) F.axis[k][a] = (float)D.axis[k][a];
+    for (int a = 0; a < 3; ++a) F.rT[k][a] = (float)D.rT[k][a];
     for (int a = 0; a < 9; ++a) F.ET[k][a] = (float)D.ET[k][a];
-    for (int a = 0; a < 10; ++a) F.inert[k][a] = (float)D.inert[k][a];
+    for (int a = 0; a < 12; ++a) F.inert[k][a] = (float)D.inert[k][a];
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 8; ++b) F.Icol[k][a][b] = (float)D.Icol[k][a][b];
   }
-  for (int a = 0; a < 6; ++a) F.a0[a] = (float)D.a0[a];
+  for (int a = 0; a < 8; ++a) F.a0[a] = (float)D.a0[a];
   F.L = make_layout(n, nsk, nbranch, 4, false);
   F.LV = make_layout(n, nsk, nbranch, 4, true);
   return GRID_OK;

@@ -44,7 +44,7 @@ struct KnotLayout {
   int SK;                       // per body (depth + 2) rows of 8: ancestor subspaces, then g^(k)
   int UNION;                    // start of the phase-dependent area
   // M^-1 temporaries, relative to UNION
-  int UB, DINV, CT, BIA, BP;    // U_i (8n), D_i^-1 (n, doubles in mixed mode), congruence exchange (6 x 8),
+  int UB, DINV, CT, BIA, BP;    // U_i (8n), D_i^-1 (n, doubles in mixed mode), congruence exchange (2 x 6 x 8),
                                 // branch-body I^A contributions (36 each), branch-body P columns (6n each)
   // RNEA temporaries, relative to UNION
   int A, FO, FA, FSL;           // per body 8: acceleration, own force, accumulated force;
@@ -73,11 +73,12 @@ struct ModelDev {
   int skoff[GRID_MAX_DOF];       // first subspace row of body k
   int branch[GRID_MAX_DOF];      // slot of a body with >= 2 children, else -1
   int et_ident[GRID_MAX_DOF];
-  S axis[GRID_MAX_DOF][3];
+  alignas(16) S axis[GRID_MAX_DOF][4];   // unit axis, padded
   S ET[GRID_MAX_DOF][9];
   S rT[GRID_MAX_DOF][3];
-  S inert[GRID_MAX_DOF][10];     // m, h = m c (3), Ibar about the origin: xx yy zz xy xz yz
-  S a0[6];                       // base acceleration -g
+  alignas(16) S inert[GRID_MAX_DOF][12]; // m, h = m c (3), Ibar about the origin: xx yy zz xy xz yz, pad
+  alignas(16) S Icol[GRID_MAX_DOF][6][8];// columns of the 6x6 spatial inertia, padded
+  alignas(16) S a0[8];                   // base acceleration -g, padded
   uint32_t sched[GRID_SCHED_MAX];
 };
 

@@ -82,57 +82,61 @@ __device__ void ph_transforms(const Ctx<S>& c) {
 // s_m^(k) = X_k s_m^(parent k). Row id rho (d, or maxd for gravity) belongs to
 // lane rho mod T, which therefore only reads rows it wrote itself.
 template <class S, int T>
-__device__ void ph_subspaces(const Ctx<S>& c) {
+__device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E, S* carry) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
   const KnotLayout L = c.L;   // by value: offsets stay in registers
   S* SK = W + L.SK;
-  // With one row id per lane, the lane's row of the previous body is kept in
-  // registers and reused when that body is the parent (always, for a chain).
-  const bool carry_ok = T > M.maxd;
+  const int dk = M.depth[k];
+  const int p = M.parent[k];
+  const bool carry_ok = T > M.maxd;        // one row id per lane: reuse the previous body's row
+  for (int rho = c.l; rho <= M.maxd; rho += T) {
+    if (rho == dk) {
+      S row[8] = {M.axis[k][0], M.axis[k][1], M.axis[k][2], S(0), S(0), S(0),
+                  W[L.QD + M.perm[k]], S(k)};
+      S* dst = SK + 8 * (M.skoff[k] + dk);
+      st4(dst, row);
+      st4(dst + 4, row + 4);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) carry[e] = row[e];
+    } else if (rho < dk || rho == M.maxd) {
+      const bool grav = rho == M.maxd;
+      S src[8];
+      if (p < 0) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) src[e] = M.a0[e];
+        src[6] = src[7] = S(0);
+      } else if (carry_ok && p == k - 1) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) src[e] = carry[e];
+      } else {
+        const S* sp = SK + 8 * (M.skoff[p] + (grav ? M.depth[p] + 1 : rho));
+        ld4(sp, src);
+        ld4(sp + 4, src + 4);
+      }
+      S out[8];
+      x_mul(E, E + 9, src, out);
+      out[6] = src[6];
+      out[7] = src[7];
+      S* dst = SK + 8 * (M.skoff[k] + (grav ? dk + 1 : rho));
+      st4(dst, out);
+      st4(dst + 4, out + 4);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) carry[e] = out[e];
+    }
+  }
+}
+
+template <class S, int T>
+__device__ void ph_subspaces(const Ctx<S>& c) {
+  const KnotLayout L = c.L;   // by value: offsets stay in registers
   S carry[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) carry[e] = S(0);
-  for (int k = 0; k < M.n; ++k) {
-    const int dk = M.depth[k];
-    const int p = M.parent[k];
+  for (int k = 0; k < c.M.n; ++k) {
     S E[12];
-    ld12(W + L.X + 12 * k, E);
-    for (int rho = c.l; rho <= M.maxd; rho += T) {
-      if (rho == dk) {
-        S row[8] = {M.axis[k][0], M.axis[k][1], M.axis[k][2], S(0), S(0), S(0),
-                    W[L.QD + M.perm[k]], S(k)};
-        S* dst = SK + 8 * (M.skoff[k] + dk);
-        st4(dst, row);
-        st4(dst + 4, row + 4);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) carry[e] = row[e];
-      } else if (rho < dk || rho == M.maxd) {
-        const bool grav = rho == M.maxd;
-        S src[8];
-        if (p < 0) {
-#pragma unroll
-          for (int e = 0; e < 6; ++e) src[e] = M.a0[e];
-          src[6] = src[7] = S(0);
-        } else if (carry_ok && p == k - 1) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) src[e] = carry[e];
-        } else {
-          const S* sp = SK + 8 * (M.skoff[p] + (grav ? M.depth[p] + 1 : rho));
-          ld4(sp, src);
-          ld4(sp + 4, src + 4);
-        }
-        S out[8];
-        x_mul(E, E + 9, src, out);
-        out[6] = src[6];
-        out[7] = src[7];
-        S* dst = SK + 8 * (M.skoff[k] + (grav ? dk + 1 : rho));
-        st4(dst, out);
-        st4(dst + 4, out + 4);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) carry[e] = out[e];
-      }
-    }
+    ld12(c.W + L.X + 12 * k, E);
+    subspace_step<S, T>(c, k, E, carry);
   }
   SYNC();
 }
@@ -152,7 +156,7 @@ __device__ void ph_subspaces(const Ctx<S>& c) {
 // next body processed (the first child is i + 1), and through per-branch-body
 // slots otherwise. With P = double (mixed precision) the pivots D_i, D_i^-1
 // and every update divided by them are evaluated in FP64.
-template <class S, class P, int T, int CPL>
+template <class S, class P, int T, int CPL, bool WITH_SK>
 __device__ void ph_minv(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
@@ -160,17 +164,17 @@ __device__ void ph_minv(const Ctx<S>& c) {
   const int l = c.l;
   const int n = M.n;
   const int U = L.UNION;
+  const int MS = L.MS;
+  const int base = c.lane32 - l;
   S* MI = W + L.MINV;
   S* UB = W + U + L.UB;
   P* DINV = reinterpret_cast<P*>(W + U + L.DINV);
-  S* CT = W + U + L.CT;
   S* BIA = W + U + L.BIA;
   S* BP = W + U + L.BP;
-  const int MS = L.MS;
   for (int e = l; e < n * MS; e += T) MI[e] = S(0);
   for (int e = l; e < 36 * M.nbranch; e += T) BIA[e] = S(0);
   SYNC();
-  S ia[6], carry[6], fb[CPL][6];
+  S carry[6], fb[CPL][6];
 #pragma unroll
   for (int e = 0; e < 6; ++e) carry[e] = S(0);
 #pragma unroll
@@ -180,20 +184,29 @@ __device__ void ph_minv(const Ctx<S>& c) {
   for (int i = n - 1; i >= 0; --i) {
     const int p = M.parent[i];
     const int br = M.branch[i];
-    const S* E = W + L.X + 12 * i;
+    S E[12];
+    ld12(W + L.X + 12 * i, E);
     const S* r = E + 9;
-    const S* a = M.axis[i];
-    if (l < 6) {
-      const bool from_next = (i + 1 < n) && M.parent[i + 1] == i;
+    const S a[3] = {M.axis[i][0], M.axis[i][1], M.axis[i][2]};
+    S ia[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+    S ul = S(0);
+    if (l < 6) {                              // column l of I^A_i
+      ld6(M.Icol[i][l], ia);
+      if (i + 1 < n && M.parent[i + 1] == i) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e)
-        ia[e] = i_entry(M.inert[i], e, l) + (from_next ? carry[e] : S(0)) +
-                (br >= 0 ? BIA[36 * br + 6 * l + e] : S(0));
-      UB[8 * i + l] = ia[0] * a[0] + ia[1] * a[1] + ia[2] * a[2];   // I^A symmetric
+        for (int e = 0; e < 6; ++e) ia[e] += carry[e];
+      }
+      if (br >= 0) {
+        const S* sl = BIA + 36 * br + 6 * l;  // 6-scalar rows: scalar loads
+#pragma unroll
+        for (int e = 0; e < 6; ++e) ia[e] += sl[e];
+      }
+      ul = ia[0] * a[0] + ia[1] * a[1] + ia[2] * a[2];   // U_l (I^A symmetric)
+      UB[8 * i + l] = ul;
     }
-    SYNC();
     S u[6];
-    ld6(UB + 8 * i, u);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) u[e] = GRID_SHFL(ul, base + e);
     const P Dk = P(a[0]) * P(u[0]) + P(a[1]) * P(u[1]) + P(a[2]) * P(u[2]);
     const P Dinv = P(1) / Dk;
     if (l == 0) DINV[i] = Dinv;
@@ -213,44 +226,22 @@ __device__ void ph_minv(const Ctx<S>& c) {
         }
       }
     }
+    S* CT = W + U + L.CT + 48 * (i & 1);     // alternate buffers: no second barrier needed
     if (p >= 0 && l < 6) {
       S acol[6], cx[6];
-      S u_l = u[0];
+      const P ulD = P(ul) * Dinv;
 #pragma unroll
-      for (int e = 1; e < 6; ++e) u_l = (l == e) ? u[e] : u_l;
-      const P ul = P(u_l) * Dinv;
-#pragma unroll
-      for (int e = 0; e < 6; ++e) acol[e] = S(P(ia[e]) - P(u[e]) * ul);
+      for (int e = 0; e < 6; ++e) acol[e] = S(P(ia[e]) - P(u[e]) * ulD);
       xt_mul(E, r, acol, cx);                 // column l of C = X^T A
       st6(CT + 8 * l, cx);
     }
     SYNC();
     if (p >= 0 && l < 6) {
-      // column l of X (6x6, X = [E 0; -E r~ E])
-      S xc[6];
-      if (l < 3) {
-        const S rt0 = l == 0 ? S(0) : (l == 1 ? -r[2] : r[1]);
-        const S rt1 = l == 0 ? r[2] : (l == 1 ? S(0) : -r[0]);
-        const S rt2 = l == 0 ? -r[1] : (l == 1 ? r[0] : S(0));
+      // column l of X^T A X = X^T C^T e_l = X^T (row l of C); C symmetric-congruent
+      S rowl[6], it[6];
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-          xc[e] = E[3 * e + l];
-          xc[3 + e] = -(E[3 * e] * rt0 + E[3 * e + 1] * rt1 + E[3 * e + 2] * rt2);
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 3; ++e) { xc[e] = S(0); xc[3 + e] = E[3 * e + l - 3]; }
-      }
-      S it[6];                                 // column l of X^T A X = C X[:, l]
-#pragma unroll
-      for (int e = 0; e < 6; ++e) it[e] = S(0);
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        S cm[6];
-        ld6(CT + 8 * m, cm);
-#pragma unroll
-        for (int e = 0; e < 6; ++e) it[e] += cm[e] * xc[m];
-      }
+      for (int m = 0; m < 6; ++m) rowl[m] = CT[8 * m + l];
+      xt_mul(E, r, rowl, it);
       if (p == i - 1) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) carry[e] = it[e];
@@ -262,16 +253,19 @@ __device__ void ph_minv(const Ctx<S>& c) {
     }
   }
   SYNC();
-  // forward pass
-  S pc[CPL][6];
+  // forward pass (with the subspace-table step of the same body, for ILP)
+  S pc[CPL][6], skc[8];
 #pragma unroll
   for (int cc = 0; cc < CPL; ++cc)
 #pragma unroll
     for (int e = 0; e < 6; ++e) pc[cc][e] = S(0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) skc[e] = S(0);
   for (int i = 0; i < n; ++i) {
     const int p = M.parent[i];
     const int br = M.branch[i];
-    const S* E = W + L.X + 12 * i;
+    S E[12];
+    ld12(W + L.X + 12 * i, E);
     const S* r = E + 9;
     const S* a = M.axis[i];
     S Ui[6];
@@ -307,6 +301,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
         }
       }
     }
+    if (WITH_SK) subspace_step<S, T>(c, i, E, skc);
   }
   // mirror the columns this lane owns into the lower triangle
 #pragma unroll
@@ -805,14 +800,14 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   SYNC();
   ph_transforms<S, T>(c);
   if (MODE == MODE_MINV) {
-    ph_minv<S, P, T, CPL>(c);
+    ph_minv<S, P, T, CPL, false>(c);
   } else {
-    ph_subspaces<S, T>(c);
     if (MODE == MODE_RNEA) {
+      ph_subspaces<S, T>(c);
       ph_rnea_bodies<S, T>(c, L.TAU);
       ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);
     } else {
-      ph_minv<S, P, T, CPL>(c);
+      ph_minv<S, P, T, CPL, true>(c);           // also builds the subspace table
       ph_rnea_bodies<S, T>(c, -1);
       ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);    // CB = RNEA(q, qd, 0)
       ph_fd<S, T>(c);
