@@ -125,6 +125,26 @@ def dist_setup(n_gpus):
     return dist.get_rank(), dist.get_world_size(), local, dist
 
 
+def max_over_ranks(sec, dist=None, device="cuda"):
+    """Largest elapsed time over all ranks (the whole job ends with the slowest)."""
+    if dist is None:
+        return sec
+    import torch
+    t = torch.tensor([sec], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank):
+    """Each rank draws its own trajectories (weak scaling: independent shards)."""
+    return gi.workload_seed(2, KNOTS) + 7919 * rank
+
+
+def aggregate_value(world, knots_per_rank, steps, sec):
+    """Whole-job throughput: every rank's knot points over the slowest rank's time."""
+    return world * knots_per_rank * steps / sec
+
+
 def time_steps(fn, steps, warmup, stream, dist=None):
     """W untimed steps, then K steps bracketed by barrier + synchronize; CUDA
     events on the launching stream. Returns (seconds, max over ranks)."""
@@ -145,12 +165,7 @@ def time_steps(fn, steps, warmup, stream, dist=None):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sec = e0.elapsed_time(e1) / 1e3
-    if dist:
-        t = torch.tensor([sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-    return sec
+    return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
 
 
 def cpu_oracle_rate(robot, seconds_min=10.0, seconds_max=30.0, threads=None):
@@ -243,7 +258,7 @@ def run_ours(args):
     model = grid.Model.from_robot(robot)
     n = robot.n
     Nk = args.traj * KNOTS
-    seed = gi.workload_seed(2, KNOTS) + 7919 * rank
+    seed = rank_seed(rank)
     q, qd, tau = (torch.from_numpy(x.astype(np.float32)).cuda()
                   for x in gi.states(n, Nk, seed))
     J = torch.empty((Nk, n, 2 * n), device="cuda")
@@ -257,7 +272,7 @@ def run_ours(args):
         sec = time_steps(step, args.steps, args.warmup, stream, dist)
     clocks = clk.summary()
     ms = sec / args.steps * 1e3
-    value = world * Nk * args.steps / sec
+    value = aggregate_value(world, Nk, args.steps, sec)
     flops_knot = grad_fd_flops_per_knot(robot.parent)
     achieved_tflops = flops_knot * Nk / (ms / 1e3) / 1e12
     dram = NCU_DRAM_BYTES_PER_KNOT.get(kernel_source_hash())
