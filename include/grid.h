@@ -129,6 +129,15 @@ grid_status grid_grad_fd(const grid_model* model, int N, const float* q, const f
                          const float* tau, float* J, float* qdd, void* stream);
 
 /*
+ * grid_grad_rnea -- analytical gradient of inverse dynamics (Sec. IV-B, fourth
+ * item; Alg. 1 / Alg. 2 and their backward pass) at the given (q, qd, qdd):
+ *   dID [N][n][2n] output; row i is tau_i, columns 0..n-1 are d/dq_j,
+ *   columns n..2n-1 are d/dqd_j. qdd NULL means qdd = 0.
+ */
+grid_status grid_grad_rnea(const grid_model* model, int N, const float* q, const float* qd,
+                           const float* qdd, float* dID, void* stream);
+
+/*
  * grid_fd_vjp -- vector-Jacobian product through forward dynamics: for an
  * upstream gradient gbar = dL/dqdd at qdd = FD(q, qd, tau),
  *   dtau = M^-1 gbar,  dq = (dqdd/dq)^T gbar = -(dID/dq)^T M^-1 gbar,
@@ -150,6 +159,8 @@ grid_status grid_fd_f64(const grid_model* model, int N, const double* q, const d
                         const double* tau, double* qdd, void* stream);
 grid_status grid_grad_fd_f64(const grid_model* model, int N, const double* q, const double* qd,
                              const double* tau, double* J, double* qdd, void* stream);
+grid_status grid_grad_rnea_f64(const grid_model* model, int N, const double* q, const double* qd,
+                               const double* qdd, double* dID, void* stream);
 grid_status grid_fd_vjp_f64(const grid_model* model, int N, const double* q, const double* qd,
                             const double* tau, const double* gbar, double* dq, double* dqd,
                             double* dtau, void* stream);

@@ -139,6 +139,14 @@ class Model:
                      self._stream())
         return qdd
 
+    def grad_rnea(self, q, qd, qdd=None, out=None):
+        """[dID/dq | dID/dqd] at (q, qd, qdd), [N, n, 2n]."""
+        N, dt, (q, qd, qdd) = self._state(q, qd, qdd)
+        D = out if out is not None else torch.empty((N, self.n, 2 * self.n), dtype=dt, device=q.device)
+        _native.call(self._fn("grid_grad_rnea", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(D),
+                     self._stream())
+        return D
+
     def grad_fd(self, q, qd, tau, out=None, qdd_out=None, return_qdd=False):
         """J = [dqdd/dq | dqdd/dqd], [N, n, 2n]; optionally also qdd [N, n]."""
         N, dt, (q, qd, tau) = self._state(q, qd, tau)

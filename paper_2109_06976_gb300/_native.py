@@ -32,6 +32,8 @@ SIGNATURES = {
     "grid_fd_f64": [_P, _I, _P, _P, _P, _P, _P],
     "grid_grad_fd_f64": [_P, _I, _P, _P, _P, _P, _P, _P],
     "grid_fd_vjp": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
+    "grid_grad_rnea": [_P, _I, _P, _P, _P, _P, _P],
+    "grid_grad_rnea_f64": [_P, _I, _P, _P, _P, _P, _P],
     "grid_fd_vjp_f64": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
     "grid_server_create": [_P, _I, _I, ctypes.c_size_t, ctypes.POINTER(_P)],
     "grid_server_set_idle_timeout": [_P, ctypes.c_double],

@@ -25,6 +25,8 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   extern template grid_status dispatch<S, MODE_GRAD, MIXED>(const grid_model*, int, const S*,        \
                                                             const S*, const S*, const S*, S*, S*, S*, cudaStream_t); \
   extern template grid_status dispatch<S, MODE_VJP, MIXED>(const grid_model*, int, const S*,         \
+                                                           const S*, const S*, const S*, S*, S*, S*, cudaStream_t); \
+  extern template grid_status dispatch<S, MODE_GRAD_ID, MIXED>(const grid_model*, int, const S*,     \
                                                            const S*, const S*, const S*, S*, S*, S*, cudaStream_t);
 GRID_DECLARE(float, false)
 GRID_DECLARE(float, true)
@@ -202,6 +204,19 @@ grid_status grid_fd_vjp_f64(const grid_model* m, int N, const double* q, const d
   grid_status s = check_args<double>(m, N, {q, qd, tau, gbar, dq, dqd, dtau}, {});
   if (s != GRID_OK) return s;
   return run<double, MODE_VJP>(m, N, q, qd, tau, gbar, dq, dqd, dtau, stream);
+}
+
+grid_status grid_grad_rnea(const grid_model* m, int N, const float* q, const float* qd, const float* qdd,
+                           float* dID, void* stream) {
+  grid_status s = check_args<float>(m, N, {q, qd, dID}, {qdd});
+  if (s != GRID_OK) return s;
+  return run<float, MODE_GRAD_ID>(m, N, q, qd, qdd, nullptr, dID, nullptr, nullptr, stream);
+}
+grid_status grid_grad_rnea_f64(const grid_model* m, int N, const double* q, const double* qd,
+                               const double* qdd, double* dID, void* stream) {
+  grid_status s = check_args<double>(m, N, {q, qd, dID}, {qdd});
+  if (s != GRID_OK) return s;
+  return run<double, MODE_GRAD_ID>(m, N, q, qd, qdd, nullptr, dID, nullptr, nullptr, stream);
 }
 
 }  // extern "C"

@@ -12,7 +12,7 @@
 #endif
 
 // Kernel modes (one kernel template serves every entry point).
-enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3, MODE_VJP = 4 };
+enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3, MODE_VJP = 4, MODE_GRAD_ID = 5 };
 
 #define GRID_SCHED_MAX 4096    // step descriptors for all lane counts together
 #define GRID_NUM_LANE_CFG 3    // lanes per knot point: 8, 16, 32

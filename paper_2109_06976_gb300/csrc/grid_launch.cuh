@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict
     for (int i = threadIdx.x; i < head / 16; i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
-  const int nsteps = (MODE == MODE_GRAD) ? M.steps[cfg] : 0;
+  const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? M.steps[cfg] : 0;
   const int stride = MODE == MODE_VJP ? M.LV.stride : M.L.stride;
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + head);
   for (int i = threadIdx.x; i < nsteps * T; i += blockDim.x) sched[i] = gm->sched[M.sched_off[cfg] + i];
@@ -81,7 +81,7 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
   auto kern = grid_kernel<S, MODE, T, CPL, MAXD, MIXED>;
   constexpr int cfg = T == 8 ? 0 : (T == 16 ? 1 : 2);
   constexpr int G = 32 / T;
-  const int nsteps = (MODE == MODE_GRAD) ? hm->steps[cfg] : 0;
+  const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? hm->steps[cfg] : 0;
   const DevInfo di = dev_info(m->device);
   const size_t fixed = align16(model_head_bytes<S>()) + align16(nsteps * T * 4);
   const size_t per_warp = (size_t)G * (MODE == MODE_VJP ? hm->LV.stride : hm->L.stride) * sizeof(S);
@@ -127,7 +127,7 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
 template <class S, int MODE, int T, int CPL, bool MIXED>
 grid_status launch_d(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                      const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st) {
-  if (MODE == MODE_GRAD && hm->maxd > 8)
+  if ((MODE == MODE_GRAD || MODE == MODE_GRAD_ID) && hm->maxd > 8)
     return launch_t<S, MODE, T, CPL, 32, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   return launch_t<S, MODE, T, CPL, 8, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
 }
@@ -169,4 +169,6 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   template grid_status dispatch<S, MODE_GRAD, MIXED>(const grid_model*, int, const S*, const S*,     \
                                                      const S*, const S*, S*, S*, S*, cudaStream_t);  \
   template grid_status dispatch<S, MODE_VJP, MIXED>(const grid_model*, int, const S*, const S*,      \
-                                                    const S*, const S*, S*, S*, S*, cudaStream_t);
+                                                    const S*, const S*, S*, S*, S*, cudaStream_t);   \
+  template grid_status dispatch<S, MODE_GRAD_ID, MIXED>(const grid_model*, int, const S*, const S*,  \
+                                                        const S*, const S*, S*, S*, S*, cudaStream_t);

@@ -405,7 +405,7 @@ __device__ void ph_fd(const Ctx<S>& c) {
 // (so beta_k = (a_k - qd_k v_k x S_k) x S_k, as S x S = 0). Then the
 // accumulated forces F_i = f_i + sum_children X_c^T F_c (lanes over
 // components) and phi_i = S_i x* F_i.
-template <class S, int T>
+template <class S, int T, bool ADD_QDD>
 __device__ void ph_update_and_forces(const Ctx<S>& c) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
@@ -419,13 +419,15 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
     const int dk = M.depth[k];
     const S* rows = W + L.SK + 8 * M.skoff[k];
     S da[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
-    for (int d = 0; d <= dk; ++d) {
-      S s[8];
-      ld4(rows + 8 * d, s);
-      ld4(rows + 8 * d + 4, s + 4);
-      const S qdd = W[L.QDD + (int)s[7]];
+    if (ADD_QDD) {                          // accelerations so far exclude qdd
+      for (int d = 0; d <= dk; ++d) {
+        S s[8];
+        ld4(rows + 8 * d, s);
+        ld4(rows + 8 * d + 4, s + 4);
+        const S qdd = W[L.QDD + (int)s[7]];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) da[e] += s[e] * qdd;
+        for (int e = 0; e < 6; ++e) da[e] += s[e] * qdd;
+      }
     }
     const S* ax = M.axis[k];
     S v[6], a[6], fo[6];
@@ -783,7 +785,7 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   const int g = lane32 / T;
   S* W = Wwarp + g * L.stride;
   const Ctx<S> c{M, L, W, lane32 % T, lane32};
-  const int out_per = MODE == MODE_MINV ? n * n : (MODE == MODE_GRAD ? 2 * n * n : n);
+  const int out_per = MODE == MODE_MINV ? n * n : ((MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? 2 * n * n : n);
   const int nvalid = min(G, N - k0);
   // stage inputs (coalesced across the warp)
   for (int e = lane32; e < G * n; e += 32) {
@@ -793,7 +795,7 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
     const size_t gi = (size_t)k0 * n + e;
     Wk[L.Q + i] = ok ? q[gi] : S(0);
     if (MODE != MODE_MINV) Wk[L.QD + i] = ok ? qd[gi] : S(0);
-    if (MODE == MODE_RNEA) Wk[L.TAU + i] = (ok && x3) ? x3[gi] : S(0);
+    if (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) Wk[L.TAU + i] = (ok && x3) ? x3[gi] : S(0);
     if (MODE == MODE_FD || MODE == MODE_GRAD || MODE == MODE_VJP) Wk[L.TAU + i] = ok ? x3[gi] : S(0);
     if (MODE == MODE_VJP) Wk[L.UNION + L.GB + i] = ok ? x4[gi] : S(0);
   }
@@ -802,16 +804,20 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   if (MODE == MODE_MINV) {
     ph_minv<S, P, T, CPL, false>(c);
   } else {
-    if (MODE == MODE_RNEA) {
+    if (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) {
       ph_subspaces<S, T>(c);
-      ph_rnea_bodies<S, T>(c, L.TAU);
-      ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);
+      ph_rnea_bodies<S, T>(c, L.TAU);                 // qdd given (caller order)
+      if (MODE == MODE_RNEA) ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);
+      if (MODE == MODE_GRAD_ID) {
+        ph_update_and_forces<S, T, false>(c);
+        ph_columns<S, T, MAXD>(c, sched, nsteps);     // dc = [dID/dq | dID/dqd]
+      }
     } else {
       ph_minv<S, P, T, CPL, true>(c);           // also builds the subspace table
       ph_rnea_bodies<S, T>(c, -1);
       ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);    // CB = RNEA(q, qd, 0)
       ph_fd<S, T>(c);
-      if (MODE == MODE_GRAD || MODE == MODE_VJP) ph_update_and_forces<S, T>(c);
+      if (MODE == MODE_GRAD || MODE == MODE_VJP) ph_update_and_forces<S, T, true>(c);
       if (MODE == MODE_GRAD) {
         ph_columns<S, T, MAXD>(c, sched, nsteps);
         ph_product<S, T, CPL>(c);
@@ -830,6 +836,12 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
     for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.QDD + i];
   } else if (MODE == MODE_MINV) {
     for (int e = c.l; e < n * n; e += T) OS[M.perm[e / n] * n + M.perm[e % n]] = W[L.MINV + (e / n) * L.MS + e % n];
+  } else if (MODE == MODE_GRAD_ID) {
+    const S* DC = W + L.UNION + L.DC;
+    for (int e = c.l; e < 2 * n * n; e += T) {        // dc is [i][u n + j]; stage in caller order
+      const int i = e / (2 * n), col = e % (2 * n), j = col < n ? col : col - n;
+      OS[M.perm[i] * 2 * n + (col < n ? 0 : n) + M.perm[j]] = DC[e];
+    }
   } else if (MODE == MODE_VJP) {
     for (int i = c.l; i < n; i += T) {
       OS[M.perm[i]] = W[L.UNION + L.DQ + i];

@@ -78,6 +78,10 @@ def test_all_outputs_match_oracle(grid, key, dtype, N):
     qdd_ref = oracle.fd(r, q64, qd64, tau64)
     e = vec_rel_err(m.fd(q, qd, tau).cpu().numpy(), qdd_ref, fl)
     assert e <= tol, f"fd {e}"
+    dID = m.grad_rnea(q, qd, tau).cpu().numpy()             # tau values used as accelerations
+    rq, rqd = oracle.grad_rnea(r, q64, qd64, tau64)
+    e = col_rel_err(dID, np.concatenate([rq, rqd], axis=2), fl)
+    assert e <= tol, f"grad_rnea {e}"
     J, qdd = m.grad_fd(q, qd, tau, return_qdd=True)
     e = col_rel_err(J.cpu().numpy(), oracle.grad_fd(r, q64, qd64, tau64), fl)
     assert e <= tol, f"grad_fd {e}"
