@@ -24,43 +24,47 @@ namespace {
 
 int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
-// Per-knot shared-memory layout, in scalars of `ssize` bytes.
-KnotLayout make_layout(int n, int nsk, int nbranch, int ssize, bool vjp) {
+// Per-knot shared-memory layout, in scalars of `ssize` bytes. kind: 0 gradient
+// of FD (J stored directly), 1 staged outputs (RNEA, M^-1, FD, gradient of ID),
+// 2 vector-Jacobian product.
+KnotLayout make_layout(int n, int nsk, int nbranch, int ssize, int kind) {
   KnotLayout L;
+  std::memset(&L, 0, sizeof(L));
   int off = 0;
   auto take = [&](int count) { int o = off; off += round_up(count, 4); return o; };
   L.Q = take(n); L.QD = take(n); L.TAU = take(n); L.QDD = take(n); L.CB = take(n);
   L.X = take(12 * n);
-  L.V = take(8 * n); L.GAM = take(8 * n); L.BET = take(8 * n); L.PHI = take(8 * n);
+  L.VG = take(12 * n); L.BPH = take(12 * n);
   L.MS = round_up(n, 4);
   L.MINV = take(n * L.MS);
   L.SK = take(8 * nsk);
   L.UNION = off;
-  int b = 0;
+  int b = 0;                                     // M^-1 temporaries
   auto tb = [&](int count) { int o = b; b += round_up(count, 4); return o; };
   L.UB = tb(8 * n);
-  L.DINV = tb(ssize == 4 ? 2 * n : n);     // doubles (mixed mode stores them in pairs of floats)
-  L.CT = tb(96);                           // two 6 x 8 buffers, alternating by body
+  L.DINV = tb(ssize == 4 ? 2 * n : n);           // doubles (mixed mode stores them in pairs of floats)
+  L.CT = tb(96);                                 // two 6 x 8 buffers, alternating by body
   L.BIA = tb(36 * nbranch);
   L.BP = tb(6 * n * nbranch);
-  int r = 0;
+  int r = 0;                                     // RNEA temporaries
   auto tr = [&](int count) { int o = r; r += round_up(count, 4); return o; };
-  L.A = tr(8 * n); L.FO = tr(8 * n); L.FA = tr(8 * n); L.FSL = tr(8 * nbranch);
-  L.GB = L.LAM = L.PSI = L.AB = L.VB = L.SA = L.SV = L.DQ = L.DQD = 0;
-  if (vjp) {
-    r = std::max(r, b);          // gbar is staged before M^-1 runs: keep it clear of M^-1 temporaries
+  L.A = tr(8 * n); L.F = tr(8 * n); L.FSL = tr(8 * nbranch);
+  r = std::max(r, b);                            // gravity rows are written while M^-1 runs
+  L.GR = tr(8 * n);
+  if (kind == 2) {
     L.GB = tr(n); L.LAM = tr(n); L.PSI = tr(8 * n); L.AB = tr(8 * n); L.VB = tr(8 * n);
     L.SA = tr(8 * nbranch); L.SV = tr(8 * nbranch); L.DQ = tr(n); L.DQD = tr(n);
   }
-  int c = 0;
-  auto tc = [&](int count) { int o = c; c += round_up(count, 4); return o; };
-  L.DC = tc(2 * n * n); L.JS = tc(2 * n * n);
-  if (vjp) { L.DC = 0; L.JS = r; c = r + round_up(3 * n, 4); }   // output staging after the VJP data
-  off += std::max(b, std::max(r, c));
-  // Knot stride: a multiple of 4 scalars, offset from a multiple of the bank
-  // count so that groups of a warp touching the same field hit other banks.
-  if (ssize == 4) L.stride = round_up(off, 32) + 4;
-  else L.stride = round_up(off, 16) + 4;
+  int c = 2 * n * n;                             // dc
+  L.DC = 0;
+  int u = std::max(b, std::max(r, c));
+  if (kind == 1) { L.JS = u; u += round_up(2 * n * n, 4); }
+  if (kind == 2) { L.JS = u; u += round_up(3 * n, 4); }
+  off += round_up(u, 4);
+  // Knot stride: 16 bytes more than a multiple of 32 bytes, so that the groups of
+  // a warp touching the same field start in different bank quads.
+  const int q = 32 / ssize;                      // scalars per 32 bytes
+  L.stride = round_up(off, q) + q / 2;
   return L;
 }
 
@@ -134,7 +138,7 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
   for (int k = 0; k < n; ++k) {
     maxd = std::max(maxd, dep[k] + 1);
     D.skoff[k] = nsk;
-    nsk += dep[k] + 2;                      // ancestor subspaces and the gravity row
+    nsk += dep[k] + 1;                      // ancestor subspaces (gravity rows live in the union)
     int nk = 0;
     for (int m = k + 1; m < n; ++m) nk += par[m] == k;
     D.branch[k] = nk >= 2 ? nbranch++ : -1;
@@ -239,8 +243,9 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
         D.sched[soff + s * T + l] = s < (int)lane[l].size() ? lane[l][s] : 0u;
     soff += S * T;
   }
-  D.L = make_layout(n, nsk, nbranch, 8, false);
-  D.LV = make_layout(n, nsk, nbranch, 8, true);
+  D.L = make_layout(n, nsk, nbranch, 8, 0);
+  D.LS = make_layout(n, nsk, nbranch, 8, 1);
+  D.LV = make_layout(n, nsk, nbranch, 8, 2);
 
   // Float copy of everything; its own layout.
   ModelDev<float>& F = *mf;
@@ -267,7 +272,8 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
       for (int b = 0; b < 8; ++b) F.Icol[k][a][b] = (float)D.Icol[k][a][b];
   }
   for (int a = 0; a < 8; ++a) F.a0[a] = (float)D.a0[a];
-  F.L = make_layout(n, nsk, nbranch, 4, false);
-  F.LV = make_layout(n, nsk, nbranch, 4, true);
+  F.L = make_layout(n, nsk, nbranch, 4, 0);
+  F.LS = make_layout(n, nsk, nbranch, 4, 1);
+  F.LV = make_layout(n, nsk, nbranch, 4, 2);
   return GRID_OK;
 }

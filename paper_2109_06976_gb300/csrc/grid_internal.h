@@ -1,6 +1,7 @@
 // Internal model representation shared by the host builder and the kernels.
 #pragma once
 
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/grid.h"
@@ -39,18 +40,19 @@ enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3, MODE_VJP = 4, M
 struct KnotLayout {
   int Q, QD, TAU, QDD, CB;      // staged q, qd, tau (or qdd input), qdd, bias force / tau out
   int X;                        // per body E(9) r(3)
-  int V, GAM, BET, PHI;         // per body 8 (6 used): v, gamma = I v, beta = (X a_parent) x S, phi = S x* F
+  int VG, BPH;                  // per body 12: v | gamma = I v, and beta = (X a_parent) x S | phi = S x* F
   int MINV, MS;                 // n x n with row stride MS (a multiple of 4)
-  int SK;                       // per body (depth + 2) rows of 8: ancestor subspaces, then g^(k)
+  int SK;                       // per body (depth + 1) rows of 8: ancestor subspaces s_m^(k)
   int UNION;                    // start of the phase-dependent area
   // M^-1 temporaries, relative to UNION
   int UB, DINV, CT, BIA, BP;    // U_i (8n), D_i^-1 (n, doubles in mixed mode), congruence exchange (2 x 6 x 8),
                                 // branch-body I^A contributions (36 each), branch-body P columns (6n each)
   // RNEA temporaries, relative to UNION
-  int A, FO, FA, FSL;           // per body 8: acceleration, own force, accumulated force;
-                                // FSL: force contributions to branch bodies (8 each)
-  // derivative-column / product temporaries, relative to UNION
-  int DC, JS;                   // dc [n][2n], J staging [n][2n] (caller order)
+  int A, F, FSL, GR;            // per body 8: acceleration, force (own, then accumulated in place);
+                                // FSL: force contributions to branch bodies (8 each);
+                                // GR: gravity rows g^(k) = kX_0 a_0 (8 per body), clear of the M^-1 area
+  // derivative-column temporaries and output staging, relative to UNION
+  int DC, JS;                   // dc [n][2n]; output staging in caller order (not in the gradient layout)
   // vector-Jacobian product (VJP layout only), relative to UNION, after the RNEA temporaries
   int GB, LAM, PSI, AB, VB, SA, SV, DQ, DQD;  // gbar (caller order), lambda, psi, adjoint seeds (8n each),
                                               // branch slots (8 each), dL/dq, dL/dqd (internal order)
@@ -62,7 +64,8 @@ struct ModelDev {
   int n, maxd, nsk, ncomp, nbranch;
   int steps[GRID_NUM_LANE_CFG];      // steps per lane for 8, 16, 32 lanes
   int sched_off[GRID_NUM_LANE_CFG];  // offsets into sched
-  KnotLayout L;                  // workspace of the RNEA / M^-1 / FD / gradient kernels
+  KnotLayout L;                  // workspace of the gradient-of-FD kernel (J is stored directly)
+  KnotLayout LS;                 // workspace of the RNEA / M^-1 / FD / gradient-of-ID kernels (staged outputs)
   KnotLayout LV;                 // workspace of the vector-Jacobian-product kernel
   int parent[GRID_MAX_DOF];
   int depth[GRID_MAX_DOF];
@@ -77,15 +80,22 @@ struct ModelDev {
   S ET[GRID_MAX_DOF][9];
   S rT[GRID_MAX_DOF][3];
   alignas(16) S inert[GRID_MAX_DOF][12]; // m, h = m c (3), Ibar about the origin: xx yy zz xy xz yz, pad
-  alignas(16) S Icol[GRID_MAX_DOF][6][8];// columns of the 6x6 spatial inertia, padded
   alignas(16) S a0[8];                   // base acceleration -g, padded
+  // -- not staged into shared memory:
+  alignas(16) S Icol[GRID_MAX_DOF][6][8];// columns of the 6x6 spatial inertia, padded
   uint32_t sched[GRID_SCHED_MAX];
 };
 
-// Bytes of ModelDev that every CTA copies into shared memory (everything but
-// the schedules, whose lane-count slice is copied separately).
+template <int MODE, class S>
+GRID_HD inline const KnotLayout& layout_of(const ModelDev<S>& m) {
+  return MODE == MODE_VJP ? m.LV : (MODE == MODE_GRAD ? m.L : m.LS);
+}
+
+// Bytes of ModelDev that every CTA copies into shared memory (everything up to
+// the inertia column table, which is read from device memory, and the
+// schedules, whose lane-count slice is copied separately).
 template <class S>
-GRID_HD constexpr int model_head_bytes() { return (int)(sizeof(ModelDev<S>) - sizeof(uint32_t) * GRID_SCHED_MAX); }
+GRID_HD constexpr int model_head_bytes() { return (int)offsetof(ModelDev<S>, Icol); }
 
 struct grid_model {
   int n;

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict
   }
   __syncthreads();
   const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? M.steps[cfg] : 0;
-  const int stride = MODE == MODE_VJP ? M.LV.stride : M.L.stride;
+  const int stride = layout_of<MODE>(M).stride;
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + head);
   for (int i = threadIdx.x; i < nsteps * T; i += blockDim.x) sched[i] = gm->sched[M.sched_off[cfg] + i];
   S* ws = reinterpret_cast<S*>(smem + head + align16(nsteps * T * 4));
@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict
   S* Wwarp = ws + warp * G * stride;
   const int ntiles = (N + G - 1) / G;
   for (int tile = blockIdx.x * wpb + warp; tile < ntiles; tile += gridDim.x * wpb)
-    process_tile<S, MODE, T, CPL, MAXD, MIXED>(M, sched, nsteps, Wwarp, lane32, tile * G, N, q, qd, x3,
-                                               x4, out, out2, out3);
+    process_tile<S, MODE, T, CPL, MAXD, MIXED>(M, gm, sched, nsteps, Wwarp, lane32, tile * G, N, q, qd,
+                                               x3, x4, out, out2, out3);
 }
 
 // ---------------------------------------------------------------- launcher
@@ -84,33 +84,44 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
   const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? hm->steps[cfg] : 0;
   const DevInfo di = dev_info(m->device);
   const size_t fixed = align16(model_head_bytes<S>()) + align16(nsteps * T * 4);
-  const size_t per_warp = (size_t)G * (MODE == MODE_VJP ? hm->LV.stride : hm->L.stride) * sizeof(S);
-  int warps = kMaxWarps;
-  while (warps > 1 && fixed + warps * per_warp > (size_t)di.smem_optin) --warps;
-  const size_t smem = fixed + warps * per_warp;
-  if (smem > (size_t)di.smem_optin) {
-    grid_set_error("knot workspace needs %zu B of shared memory (limit %d); use more lanes",
-                   smem, di.smem_optin);
-    return GRID_E_ARG;
-  }
-  // Opt in to large dynamic shared memory once per instantiation and size.
-  static std::atomic<size_t> opted{0};
+  const size_t per_warp = (size_t)G * layout_of<MODE>(*hm).stride * sizeof(S);
+  // Opt in to large dynamic shared memory once per instantiation.
+  static std::atomic<int> opted{0};
   cudaError_t err = cudaSuccess;
-  if (smem > opted.load()) {
+  if (!opted.load()) {
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)di.smem_optin);
     if (err != cudaSuccess) {
       grid_set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(err));
       return GRID_E_CUDA;
     }
-    opted.store((size_t)di.smem_optin);
+    opted.store(1);
   }
+  // Warps per CTA: the count that keeps the most warps resident per SM (ties go
+  // to larger CTAs, which share one copy of the model among more warps). The
+  // choice is cached per instantiation and workspace size.
+  static std::atomic<unsigned long long> cached{0};
+  int warps = 0, per_sm = 0, best = 0;
+  const unsigned long long c0 = cached.load();
+  if (c0 && (c0 >> 16) == (unsigned long long)(fixed + per_warp)) {
+    warps = (int)((c0 >> 8) & 0xff);
+    per_sm = (int)(c0 & 0xff);
+  } else {
+    for (int w = kMaxWarps; w >= 1; --w) {
+      const size_t sm_w = fixed + w * per_warp;
+      if (sm_w > (size_t)di.smem_optin) continue;
+      int b = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * w, sm_w);
+      if (b * w > best) { best = b * w; warps = w; per_sm = b; }
+    }
+    if (warps) cached.store(((unsigned long long)(fixed + per_warp) << 16) | (warps << 8) | (per_sm & 0xff));
+  }
+  if (warps == 0) {
+    grid_set_error("knot workspace needs %zu B of shared memory per warp (limit %d); use more lanes",
+                   fixed + per_warp, di.smem_optin);
+    return GRID_E_ARG;
+  }
+  const size_t smem = fixed + warps * per_warp;
   const int threads = 32 * warps;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
-  if (per_sm < 1) {
-    grid_set_error("kernel does not fit on an SM (%zu B shared per CTA)", smem);
-    return GRID_E_CUDA;
-  }
   if (m->ctas_opt > 0 && m->ctas_opt < per_sm) per_sm = m->ctas_opt;
   const long tiles = (N + G - 1) / G;
   const long ctas_needed = (tiles + warps - 1) / warps;

@@ -23,6 +23,7 @@
 template <class S>
 struct Ctx {
   const ModelDev<S>& M;
+  const ModelDev<S>* gM;  // the same model in device memory (tables not staged in shared memory)
   const KnotLayout& L;  // workspace layout of this kernel mode
   S* W;                 // this knot point's workspace
   int l;                // lane within the group, 0..T-1
@@ -78,7 +79,8 @@ __device__ void ph_transforms(const Ctx<S>& c) {
 // Subspace rows of body k (8 scalars each, from SK + 8 * skoff[k]):
 //   row d = 0..depth_k : s_m^(k) = kX_m S_m for the ancestor m of k at depth d
 //                        (m = k at d = depth_k); slot 6 = qd_m, slot 7 = m
-//   row depth_k + 1    : g^(k) = kX_0 a_0 (the base acceleration -g in frame k)
+// and the gravity row g^(k) = kX_0 a_0 (the base acceleration -g in frame k),
+// kept in the phase-local area GR.
 // s_m^(k) = X_k s_m^(parent k). Row id rho (d, or maxd for gravity) belongs to
 // lane rho mod T, which therefore only reads rows it wrote itself.
 template <class S, int T>
@@ -87,6 +89,7 @@ __device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E
   S* W = c.W;
   const KnotLayout L = c.L;   // by value: offsets stay in registers
   S* SK = W + L.SK;
+  S* GR = W + L.UNION + L.GR;
   const int dk = M.depth[k];
   const int p = M.parent[k];
   const bool carry_ok = T > M.maxd;        // one row id per lane: reuse the previous body's row
@@ -110,7 +113,7 @@ __device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E
 #pragma unroll
         for (int e = 0; e < 8; ++e) src[e] = carry[e];
       } else {
-        const S* sp = SK + 8 * (M.skoff[p] + (grav ? M.depth[p] + 1 : rho));
+        const S* sp = grav ? GR + 8 * p : SK + 8 * (M.skoff[p] + rho);
         ld4(sp, src);
         ld4(sp + 4, src + 4);
       }
@@ -118,7 +121,7 @@ __device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E
       x_mul(E, E + 9, src, out);
       out[6] = src[6];
       out[7] = src[7];
-      S* dst = SK + 8 * (M.skoff[k] + (grav ? dk + 1 : rho));
+      S* dst = grav ? GR + 8 * k : SK + 8 * (M.skoff[k] + rho);
       st4(dst, out);
       st4(dst + 4, out + 4);
 #pragma unroll
@@ -191,7 +194,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
     S ia[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
     S ul = S(0);
     if (l < 6) {                              // column l of I^A_i
-      ld6(M.Icol[i][l], ia);
+      ld6(c.gM->Icol[i][l], ia);
       if (i + 1 < n && M.parent[i + 1] == i) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) ia[e] += carry[e];
@@ -332,7 +335,7 @@ __device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
     S v[6], a[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) v[e] = S(0);
-    ld6(rows + 8 * (dk + 1), a);
+    ld6(W + U + L.GR + 8 * k, a);
     for (int d = 0; d <= dk; ++d) {
       S s[8];
       ld4(rows + 8 * d, s);
@@ -353,10 +356,10 @@ __device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
     crf_mul(v, g, vg);
 #pragma unroll
     for (int e = 0; e < 6; ++e) ia[e] += vg[e];
-    st6(W + L.V + 8 * k, v);
-    st6(W + L.GAM + 8 * k, g);
+    st6(W + L.VG + 12 * k, v);
+    st6u(W + L.VG + 12 * k + 6, g);
     st6(W + U + L.A + 8 * k, a);
-    st6(W + U + L.FO + 8 * k, ia);
+    st6(W + U + L.F + 8 * k, ia);
   }
   SYNC();
 }
@@ -412,7 +415,7 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
   const KnotLayout L = c.L;   // by value: offsets stay in registers
   const int U = L.UNION;
   const int l = c.l;
-  S* FA = W + U + L.FA;
+  S* FA = W + U + L.F;                     // own forces, made accumulated in place
   S* FSL = W + U + L.FSL;
   for (int e = l; e < 8 * M.nbranch; e += T) FSL[e] = S(0);
   for (int k = l; k < M.n; k += T) {
@@ -431,9 +434,9 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
     }
     const S* ax = M.axis[k];
     S v[6], a[6], fo[6];
-    ld6(W + L.V + 8 * k, v);
+    ld6(W + L.VG + 12 * k, v);
     ld6(W + U + L.A + 8 * k, a);
-    ld6(W + U + L.FO + 8 * k, fo);
+    ld6(FA + 8 * k, fo);
     const S qdk = W[L.QD + M.perm[k]];
     S idt[6], vxs[6], w[6];
     i_mul(M.inert[k], da, idt);
@@ -448,7 +451,7 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
     S B[6];
     cross3(w, ax, B);
     cross3(w + 3, ax, B + 3);
-    st6(W + L.BET + 8 * k, B);
+    st6(W + L.BPH + 12 * k, B);
   }
   SYNC();
   // Leaves to root: lane l < 6 holds component l of F_k; the full vector is
@@ -487,7 +490,7 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
     S Ph[6];                                   // [a; 0] x* F = [a x F_ang; a x F_lin]
     cross3(ax, F, Ph);
     cross3(ax, F + 3, Ph + 3);
-    st6(W + L.PHI + 8 * k, Ph);
+    st6u(W + L.BPH + 12 * k + 6, Ph);
   }
   SYNC();
 }
@@ -534,9 +537,10 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
     const S* r = E + 9;
     const S* ax = M.axis[k];
     const S qdk = W[L.QD + M.perm[k]];
-    S v[6], g[6];
-    ld6(W + L.V + 8 * k, v);
-    ld6(W + L.GAM + 8 * k, g);
+    S vg[12];
+    ld12(W + L.VG + 12 * k, vg);
+    const S* v = vg;
+    const S* g = vg + 6;
     S ndv[6], nda[6], vxs[6];
     x_mul(E, r, dv, ndv);
     x_mul(E, r, da, nda);
@@ -545,7 +549,7 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
     if (root) {
       if (uq) {
         S B[6];
-        ld6(W + L.BET + 8 * k, B);
+        ld6(W + L.BPH + 12 * k, B);
 #pragma unroll
         for (int e = 0; e < 6; ++e) { ndv[e] += vxs[e]; nda[e] += B[e]; }
       } else {
@@ -571,7 +575,7 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
     for (int e = 0; e < 6; ++e) df[e] += t1[e] + t2[e];
     if (root && uq) {
       S Ph[6];
-      ld6(W + L.PHI + 8 * k, Ph);
+      ld6u(W + L.BPH + 12 * k + 6, Ph);
 #pragma unroll
       for (int e = 0; e < 6; ++e) df[e] += Ph[e];
     }
@@ -608,7 +612,7 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 // ---------------------------------------------------------------- D
 // J = -M^-1 dc, restricted to base-branch blocks, written in caller order.
 template <class S, int T, int CPL>
-__device__ void ph_product(const Ctx<S>& c) {
+__device__ void ph_product(const Ctx<S>& c, S* __restrict__ J) {
   const ModelDev<S>& M = c.M;
   S* W = c.W;
   const KnotLayout L = c.L;   // by value: offsets stay in registers
@@ -616,10 +620,11 @@ __device__ void ph_product(const Ctx<S>& c) {
   const int U = L.UNION;
   const S* DC = W + U + L.DC;
   const S* MI = W + L.MINV;
-  S* JS = W + U + L.JS;
   constexpr int NM = CPL * T;                  // >= n, a multiple of 4
   // Lane owns output columns col = l, l + T, ...: its dc column sits in
-  // registers and every M^-1 row is read with 128-bit loads.
+  // registers and every M^-1 row is read with 128-bit loads. J (this knot
+  // point's [n][2n] block in caller order, or NULL for a padding knot point) is
+  // written directly: the group's lanes cover consecutive columns of a row.
   for (int col = c.l; col < n2; col += T) {
     const int j = col < n ? col : col - n;
     const int lo = M.comp_lo[j], hi = M.comp_hi[j];
@@ -627,8 +632,10 @@ __device__ void ph_product(const Ctx<S>& c) {
 #pragma unroll
     for (int m = 0; m < NM; ++m) dcr[m] = (m >= lo && m < hi) ? DC[m * n2 + col] : S(0);
     const int ucol = (col < n ? 0 : n) + M.perm[j];
-    for (int i = 0; i < lo; ++i) JS[M.perm[i] * n2 + ucol] = S(0);     // other base branches
-    for (int i = hi; i < n; ++i) JS[M.perm[i] * n2 + ucol] = S(0);
+    if (J) {
+      for (int i = 0; i < lo; ++i) J[M.perm[i] * n2 + ucol] = S(0);     // other base branches
+      for (int i = hi; i < n; ++i) J[M.perm[i] * n2 + ucol] = S(0);
+    }
     for (int i = lo; i < hi; ++i) {
       const S* mrow = MI + i * MS;
       S acc = S(0);
@@ -640,7 +647,7 @@ __device__ void ph_product(const Ctx<S>& c) {
           acc += mm[0] * dcr[m] + mm[1] * dcr[m + 1] + mm[2] * dcr[m + 2] + mm[3] * dcr[m + 3];
         }
       }
-      JS[M.perm[i] * n2 + ucol] = -acc;
+      if (J) J[M.perm[i] * n2 + ucol] = -acc;
     }
   }
   SYNC();
@@ -684,9 +691,10 @@ __device__ void ph_vjp_seeds(const Ctx<S>& c) {
 #pragma unroll
       for (int e = 0; e < 6; ++e) psi[e] += s[e] * lam;
     }
-    S v[6], g[6], t1[6], vxp[6], t2[6];
-    ld6(W + L.V + 8 * k, v);
-    ld6(W + L.GAM + 8 * k, g);
+    S vg[12], t1[6], vxp[6], t2[6];
+    ld12(W + L.VG + 12 * k, vg);
+    const S* v = vg;
+    const S* g = vg + 6;
     i_mul(M.inert[k], psi, t1);
     st6(W + U + L.AB + 8 * k, t1);
     crf_mul(psi, g, t1);
@@ -741,9 +749,9 @@ __device__ void ph_vjp_sweep(const Ctx<S>& c) {
     for (int e = 0; e < 6; ++e) V[e] = GRID_SHFL(vb, base + e);
     if (l == 0) {
       S v[6], B[6], F[6], psi[6], vxs[6], pxs[6];
-      ld6(W + L.V + 8 * k, v);
-      ld6(W + L.BET + 8 * k, B);
-      ld6(W + U + L.FA + 8 * k, F);
+      ld6(W + L.VG + 12 * k, v);
+      ld6(W + L.BPH + 12 * k, B);
+      ld6(W + U + L.F + 8 * k, F);
       ld6(W + U + L.PSI + 8 * k, psi);
       cross3(v, ax, vxs);
       cross3(v + 3, ax, vxs + 3);
@@ -771,21 +779,21 @@ __device__ void ph_vjp_sweep(const Ctx<S>& c) {
   SYNC();
 }
 
-// One warp processes knot points k0 .. k0 + 32/T - 1 (those < N).
+// One warp processes knot points k0 .. k0 + 32/T - 1 (those < N). M is the
+// shared-memory copy of the model, gM the same model in device memory.
 template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
-__device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ sched, int nsteps,
-                             S* Wwarp, int lane32, int k0, int N, const S* __restrict__ q,
+__device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const uint32_t* __restrict__ sched,
+                             int nsteps, S* Wwarp, int lane32, int k0, int N, const S* __restrict__ q,
                              const S* __restrict__ qd, const S* __restrict__ x3,
                              const S* __restrict__ x4, S* __restrict__ out, S* __restrict__ out2,
                              S* __restrict__ out3) {
   using P = typename std::conditional<MIXED, double, S>::type;
-  const KnotLayout& L = MODE == MODE_VJP ? M.LV : M.L;
+  const KnotLayout& L = layout_of<MODE>(M);
   const int n = M.n;
   constexpr int G = 32 / T;
   const int g = lane32 / T;
   S* W = Wwarp + g * L.stride;
-  const Ctx<S> c{M, L, W, lane32 % T, lane32};
-  const int out_per = MODE == MODE_MINV ? n * n : ((MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? 2 * n * n : n);
+  const Ctx<S> c{M, gM, L, W, lane32 % T, lane32};
   const int nvalid = min(G, N - k0);
   // stage inputs (coalesced across the warp)
   for (int e = lane32; e < G * n; e += 32) {
@@ -803,56 +811,47 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
   ph_transforms<S, T>(c);
   if (MODE == MODE_MINV) {
     ph_minv<S, P, T, CPL, false>(c);
+  } else if (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) {
+    ph_subspaces<S, T>(c);
+    ph_rnea_bodies<S, T>(c, L.TAU);                 // qdd given (caller order)
+    if (MODE == MODE_RNEA) ph_joint_forces<S, T>(c, L.UNION + L.F, L.CB);
+    if (MODE == MODE_GRAD_ID) {
+      ph_update_and_forces<S, T, false>(c);
+      ph_columns<S, T, MAXD>(c, sched, nsteps);     // dc = [dID/dq | dID/dqd]
+    }
   } else {
-    if (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) {
-      ph_subspaces<S, T>(c);
-      ph_rnea_bodies<S, T>(c, L.TAU);                 // qdd given (caller order)
-      if (MODE == MODE_RNEA) ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);
-      if (MODE == MODE_GRAD_ID) {
-        ph_update_and_forces<S, T, false>(c);
-        ph_columns<S, T, MAXD>(c, sched, nsteps);     // dc = [dID/dq | dID/dqd]
-      }
-    } else {
-      ph_minv<S, P, T, CPL, true>(c);           // also builds the subspace table
-      ph_rnea_bodies<S, T>(c, -1);
-      ph_joint_forces<S, T>(c, L.UNION + L.FO, L.CB);    // CB = RNEA(q, qd, 0)
-      ph_fd<S, T>(c);
-      if (MODE == MODE_GRAD || MODE == MODE_VJP) ph_update_and_forces<S, T, true>(c);
-      if (MODE == MODE_GRAD) {
-        ph_columns<S, T, MAXD>(c, sched, nsteps);
-        ph_product<S, T, CPL>(c);
-      }
-      if (MODE == MODE_VJP) {
-        ph_vjp_seeds<S, T>(c);
-        ph_vjp_sweep<S, T>(c);
-      }
+    ph_minv<S, P, T, CPL, true>(c);                 // also builds the subspace table
+    ph_rnea_bodies<S, T>(c, -1);
+    ph_joint_forces<S, T>(c, L.UNION + L.F, L.CB);  // CB = RNEA(q, qd, 0)
+    ph_fd<S, T>(c);
+    ph_update_and_forces<S, T, true>(c);
+    if (MODE == MODE_GRAD) {
+      ph_columns<S, T, MAXD>(c, sched, nsteps);
+      ph_product<S, T, CPL>(c, g < nvalid ? out + (size_t)(k0 + g) * 2 * n * n : nullptr);
+    }
+    if (MODE == MODE_VJP) {
+      ph_vjp_seeds<S, T>(c);
+      ph_vjp_sweep<S, T>(c);
     }
   }
-  // stage outputs in caller order
-  S* OS = W + L.UNION + L.JS;
-  if (MODE == MODE_RNEA) {
-    for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.CB + i];
-  } else if (MODE == MODE_FD) {
-    for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.QDD + i];
-  } else if (MODE == MODE_MINV) {
-    for (int e = c.l; e < n * n; e += T) OS[M.perm[e / n] * n + M.perm[e % n]] = W[L.MINV + (e / n) * L.MS + e % n];
-  } else if (MODE == MODE_GRAD_ID) {
-    const S* DC = W + L.UNION + L.DC;
-    for (int e = c.l; e < 2 * n * n; e += T) {        // dc is [i][u n + j]; stage in caller order
-      const int i = e / (2 * n), col = e % (2 * n), j = col < n ? col : col - n;
-      OS[M.perm[i] * 2 * n + (col < n ? 0 : n) + M.perm[j]] = DC[e];
+  if constexpr (MODE == MODE_GRAD) {
+    if (out2) {                                     // qdd in caller order
+      for (int i = c.l; i < n; i += T) W[L.CB + M.perm[i]] = W[L.QDD + i];
+      SYNC();
+      for (int e = lane32; e < nvalid * n; e += 32) {
+        const int kk = e / n, r = e % n;
+        out2[(size_t)k0 * n + e] = Wwarp[kk * L.stride + L.CB + r];
+      }
     }
-  } else if (MODE == MODE_VJP) {
+    SYNC();
+  } else if constexpr (MODE == MODE_VJP) {
+    S* OS = W + L.UNION + L.JS;
     for (int i = c.l; i < n; i += T) {
       OS[M.perm[i]] = W[L.UNION + L.DQ + i];
       OS[n + M.perm[i]] = W[L.UNION + L.DQD + i];
       OS[2 * n + M.perm[i]] = W[L.UNION + L.LAM + i];
     }
-  } else if (out2) {
-    for (int i = c.l; i < n; i += T) W[L.CB + M.perm[i]] = W[L.QDD + i];
-  }
-  SYNC();
-  if (MODE == MODE_VJP) {
+    SYNC();
     for (int e = lane32; e < nvalid * n; e += 32) {
       const int kk = e / n, r = e % n;
       const S* os = Wwarp + kk * L.stride + L.UNION + L.JS;
@@ -861,17 +860,28 @@ __device__ void process_tile(const ModelDev<S>& M, const uint32_t* __restrict__ 
       out3[(size_t)k0 * n + e] = os[2 * n + r];
     }
     SYNC();
-    return;
-  }
-  for (int e = lane32; e < nvalid * out_per; e += 32) {
-    const int kk = e / out_per, r = e % out_per;
-    out[(size_t)k0 * out_per + e] = Wwarp[kk * L.stride + L.UNION + L.JS + r];
-  }
-  if (MODE == MODE_GRAD && out2) {
-    for (int e = lane32; e < nvalid * n; e += 32) {
-      const int kk = e / n, r = e % n;
-      out2[(size_t)k0 * n + e] = Wwarp[kk * L.stride + L.CB + r];
+  } else {
+    // stage outputs in caller order, then store them with coalesced writes
+    const int out_per = MODE == MODE_MINV ? n * n : (MODE == MODE_GRAD_ID ? 2 * n * n : n);
+    S* OS = W + L.UNION + L.JS;
+    if (MODE == MODE_RNEA) {
+      for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.CB + i];
+    } else if (MODE == MODE_FD) {
+      for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.QDD + i];
+    } else if (MODE == MODE_MINV) {
+      for (int e = c.l; e < n * n; e += T) OS[M.perm[e / n] * n + M.perm[e % n]] = W[L.MINV + (e / n) * L.MS + e % n];
+    } else {
+      const S* DC = W + L.UNION + L.DC;
+      for (int e = c.l; e < 2 * n * n; e += T) {    // dc is [i][u n + j]
+        const int i = e / (2 * n), col = e % (2 * n), j = col < n ? col : col - n;
+        OS[M.perm[i] * 2 * n + (col < n ? 0 : n) + M.perm[j]] = DC[e];
+      }
     }
+    SYNC();
+    for (int e = lane32; e < nvalid * out_per; e += 32) {
+      const int kk = e / out_per, r = e % out_per;
+      out[(size_t)k0 * out_per + e] = Wwarp[kk * L.stride + L.UNION + L.JS + r];
+    }
+    SYNC();
   }
-  SYNC();
 }

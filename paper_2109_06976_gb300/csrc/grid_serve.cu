@@ -154,11 +154,13 @@ __global__ void __launch_bounds__(32 * kMaxWarps) grid_serve_kernel(ServeArgs a)
     }
     const int k0 = (u - first) * kServeG;
     if (M.maxd > 8)
-      process_tile<float, MODE_GRAD, kServeT, kServeCPL, 32, false>(M, sched, nsteps, W, lane, k0, H, q, qd,
-                                                                  tau, nullptr, J, nullptr, nullptr);
+      process_tile<float, MODE_GRAD, kServeT, kServeCPL, 32, false>(M, a.models[mi], sched, nsteps, W, lane,
+                                                                  k0, H, q, qd, tau, nullptr, J, nullptr,
+                                                                  nullptr);
     else
-      process_tile<float, MODE_GRAD, kServeT, kServeCPL, 8, false>(M, sched, nsteps, W, lane, k0, H, q, qd,
-                                                                 tau, nullptr, J, nullptr, nullptr);
+      process_tile<float, MODE_GRAD, kServeT, kServeCPL, 8, false>(M, a.models[mi], sched, nsteps, W, lane,
+                                                                 k0, H, q, qd, tau, nullptr, J, nullptr,
+                                                                 nullptr);
     __threadfence_system();                // this tile's Jacobians are visible to the host
     __syncwarp();
     if (lane == 0) {

@@ -184,3 +184,8 @@ __device__ __forceinline__ void st6(S* p, const S* v) { st4(p, v); st2(p + 4, v[
 // transform record E(9) r(3)
 template <class S>
 __device__ __forceinline__ void ld12(const S* p, S* o) { ld4(p, o); ld4(p + 4, o + 4); ld4(p + 8, o + 8); }
+// 6-vector at an 8-byte (not 16-byte) aligned address
+template <class S>
+__device__ __forceinline__ void ld6u(const S* p, S* o) { ld2(p, o); ld2(p + 2, o + 2); ld2(p + 4, o + 4); }
+template <class S>
+__device__ __forceinline__ void st6u(S* p, const S* v) { st2(p, v[0], v[1]); st2(p + 2, v[2], v[3]); st2(p + 4, v[4], v[5]); }
