@@ -144,6 +144,10 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
     D.branch[k] = nk >= 2 ? nbranch++ : -1;
   }
   D.maxd = maxd; D.nsk = nsk; D.ncomp = ncomp; D.nbranch = nbranch;
+  if (nsk > 1023) {
+    grid_set_error("grid_create: subspace table of %d rows exceeds the step descriptor", nsk);
+    return GRID_E_TOPOLOGY;
+  }
   for (int k = 0; k < n; ++k) {
     int c = perm[k];
     D.parent[k] = par[k]; D.depth[k] = dep[k]; D.sub_end[k] = send[k];
@@ -204,7 +208,8 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
         Unit un;
         for (size_t s = 0; s < path.size(); ++s) {
           int b = path[s];
-          uint32_t d = (uint32_t)b | ((uint32_t)(u * n + j) << 5) | STEP_VALID;
+          uint32_t d = (uint32_t)b | ((uint32_t)(u * n + j) << 5) | STEP_VALID |
+                       ((uint32_t)dep[b] << 17) | ((uint32_t)D.skoff[b] << 22);
           if (s == 0) d |= STEP_RESET | STEP_ROOT;
           if (!owned[b]) { d |= STEP_OWNED; owned[b] = 1; }
           if (s + 1 == path.size()) d |= STEP_FLUSH;

@@ -27,6 +27,8 @@ enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3, MODE_VJP = 4, M
 //   bit 14     FLUSH: last step of a path; accumulators are written out
 //   bit 15     UQ: column is d/dq_j (else d/dqd_j)
 //   bit 16     VALID: real work (padding steps have it clear)
+//   bits 17-21 depth of body k
+//   bits 22-31 first subspace row of body k (skoff[k])
 #define STEP_BODY(s) ((int)((s) & 31u))
 #define STEP_COL(s) ((int)(((s) >> 5) & 63u))
 #define STEP_RESET (1u << 11)
@@ -35,6 +37,8 @@ enum { MODE_RNEA = 0, MODE_MINV = 1, MODE_FD = 2, MODE_GRAD = 3, MODE_VJP = 4, M
 #define STEP_FLUSH (1u << 14)
 #define STEP_UQ (1u << 15)
 #define STEP_VALID (1u << 16)
+#define STEP_DEPTH(s) ((int)(((s) >> 17) & 31u))
+#define STEP_SKOFF(s) ((int)((s) >> 22))
 
 // Offsets (in scalars) of the per-knot shared-memory workspace.
 struct KnotLayout {

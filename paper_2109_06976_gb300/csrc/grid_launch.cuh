@@ -153,7 +153,7 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   else { hm = m->host_d; dm = m->dev_d; }
   int T = m->lanes_opt;
   const int n = hm->n;
-  if (T == 0) T = n <= 8 ? 8 : 16;
+  if (T == 0) T = n <= 12 ? 8 : 16;
   const int cpl = (n + T - 1) / T;
   if (T == 8) {
     if (cpl <= 1) return launch_d<S, MODE, 8, 1, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);

@@ -532,11 +532,17 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 #pragma unroll
       for (int e = 0; e < 6; ++e) { dv[e] = S(0); da[e] = S(0); }
     }
+    const int dk = STEP_DEPTH(st);
+    const S* rows = W + L.SK + 8 * STEP_SKOFF(st);
     S E[12];
     ld12(W + L.X + 12 * k, E);
     const S* r = E + 9;
-    const S* ax = M.axis[k];
-    const S qdk = W[L.QD + M.perm[k]];
+    S ax[4], in[12];
+    ld4(M.axis[k], ax);
+    ld4(M.inert[k], in);
+    ld4(M.inert[k] + 4, in + 4);
+    ld4(M.inert[k] + 8, in + 8);
+    const S qdk = rows[8 * dk + 6];            // qd_k is stored in body k's own subspace row
     S vg[12];
     ld12(W + L.VG + 12 * k, vg);
     const S* v = vg;
@@ -567,9 +573,9 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
       for (int e = 0; e < 6; ++e) nda[e] += t[e];
     }
     S df[6], t1[6], t2[6], idv[6];
-    i_mul(M.inert[k], nda, df);
+    i_mul(in, nda, df);
     crf_mul(ndv, g, t1);
-    i_mul(M.inert[k], ndv, idv);
+    i_mul(in, ndv, idv);
     crf_mul(v, idv, t2);
 #pragma unroll
     for (int e = 0; e < 6; ++e) df[e] += t1[e] + t2[e];
@@ -579,9 +585,7 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 #pragma unroll
       for (int e = 0; e < 6; ++e) df[e] += Ph[e];
     }
-    const int dk = M.depth[k];
     if (st & STEP_OWNED) {
-      const S* rows = W + L.SK + 8 * M.skoff[k];
 #pragma unroll
       for (int d = 0; d < MAXD; ++d) {
         if (d <= dk) {
