@@ -195,3 +195,31 @@ def test_repeatable(grid):
     a = m.grad_fd(q, qd, tau)
     b = m.grad_fd(q, qd, tau)
     assert torch.equal(a, b)
+
+
+def test_precision_report_tree30(grid, capsys):
+    """Per-output error of the FP32 and mixed (FP64 pivots) forms against the
+    FP64 oracle on the 30-DoF tree at N = 128 and 1024 (max and median over
+    knot points of the per-knot worst column). Printed for the record."""
+    r = gi.tree30()
+    lines = []
+    for prec in ("fp32", "mixed"):
+        m = _model(grid, "tree30", prec)
+        for N in (128, 1024):
+            (q, qd, tau), (q64, qd64, tau64) = _inputs(30, N, gi.workload_seed(3, N), torch.float32)
+            ref_tau = oracle.rnea(r, q64, qd64, tau64, nthreads=8)
+            ref_mi = oracle.minv(r, q64, nthreads=8)
+            ref_J, ref_qdd = oracle.grad_fd(r, q64, qd64, tau64, nthreads=8, with_qdd=True)
+            J, qdd = m.grad_fd(q, qd, tau, return_qdd=True)
+            outs = {
+                "rnea": (m.rnea(q, qd, tau).cpu().numpy()[:, :, None], ref_tau[:, :, None]),
+                "minv": (m.minv(q).cpu().numpy(), ref_mi),
+                "fd": (m.fd(q, qd, tau).cpu().numpy()[:, :, None], ref_qdd[:, :, None]),
+                "grad_fd": (J.cpu().numpy(), ref_J),
+            }
+            for name, (x, y) in outs.items():
+                mx, p50 = col_rel_err_stats(x, y)
+                lines.append(f"tree30 {prec:5s} N={N:4d} {name:8s} max {mx:.2e} p50 {p50:.2e}")
+                assert mx <= TOL32, lines[-1]
+    with capsys.disabled():
+        print("\n" + "\n".join(lines))
