@@ -10,7 +10,10 @@
  * spatial inertias I_i.
  *
  * Conventions for every compute call:
- *   - State arrays are caller-owned DEVICE memory, knot-major and row-major:
+ *   - State arrays are caller-owned memory addressable by the device: device
+ *     memory, or pinned host memory (cudaHostAlloc / cudaMallocHost, mapped in
+ *     the unified address space), which the kernels then read and write
+ *     directly over the CPU-GPU link (zero copy). They are knot-major and row-major:
  *     q[k*n + i] is joint i of knot point k. Matrices per knot point are
  *     row-major and contiguous: Minv[k*n*n + i*n + j], J[k*2n*n + i*2n + c].
  *     Joint order is the caller's numbering given to grid_create.

@@ -93,8 +93,8 @@ class Model:
             if t is None:
                 out.append(None)
                 continue
-            if not (isinstance(t, torch.Tensor) and t.is_cuda):
-                raise TypeError("states must be CUDA tensors")
+            if not (isinstance(t, torch.Tensor) and (t.is_cuda or t.is_pinned())):
+                raise TypeError("states must be CUDA tensors or pinned host tensors (zero copy)")
             if t.shape[-1] != self.n:
                 raise ValueError(f"last dimension must be n = {self.n}")
             t2 = t.reshape(-1, self.n).contiguous()
@@ -108,6 +108,15 @@ class Model:
         return N, dtype, out
 
     @staticmethod
+    def _empty(shape, dtype, like):
+        """Output buffer next to the inputs: device memory, or pinned host memory
+        when the inputs are pinned host tensors (the kernel then reads and writes
+        host memory directly over the CPU-GPU link)."""
+        if like.is_cuda:
+            return torch.empty(shape, dtype=dtype, device=like.device)
+        return torch.empty(shape, dtype=dtype).pin_memory()
+
+    @staticmethod
     def _fn(name, dtype):
         return name + ("_f64" if dtype == torch.float64 else "")
 
@@ -119,7 +128,7 @@ class Model:
     def rnea(self, q, qd, qdd=None, out=None):
         """tau = ID(q, qd, qdd), [N, n]."""
         N, dt, (q, qd, qdd) = self._state(q, qd, qdd)
-        tau = out if out is not None else torch.empty((N, self.n), dtype=dt, device=q.device)
+        tau = out if out is not None else self._empty((N, self.n), dt, q)
         _native.call(self._fn("grid_rnea", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(tau),
                      self._stream())
         return tau
@@ -127,14 +136,14 @@ class Model:
     def minv(self, q, out=None):
         """M(q)^-1, [N, n, n] (full symmetric)."""
         N, dt, (q,) = self._state(q)
-        Mi = out if out is not None else torch.empty((N, self.n, self.n), dtype=dt, device=q.device)
+        Mi = out if out is not None else self._empty((N, self.n, self.n), dt, q)
         _native.call(self._fn("grid_minv", dt), self._h, N, _ptr(q), _ptr(Mi), self._stream())
         return Mi
 
     def fd(self, q, qd, tau, out=None):
         """qdd = M^-1 (tau - RNEA(q, qd, 0)), [N, n]."""
         N, dt, (q, qd, tau) = self._state(q, qd, tau)
-        qdd = out if out is not None else torch.empty((N, self.n), dtype=dt, device=q.device)
+        qdd = out if out is not None else self._empty((N, self.n), dt, q)
         _native.call(self._fn("grid_fd", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(qdd),
                      self._stream())
         return qdd
@@ -142,7 +151,7 @@ class Model:
     def grad_rnea(self, q, qd, qdd=None, out=None):
         """[dID/dq | dID/dqd] at (q, qd, qdd), [N, n, 2n]."""
         N, dt, (q, qd, qdd) = self._state(q, qd, qdd)
-        D = out if out is not None else torch.empty((N, self.n, 2 * self.n), dtype=dt, device=q.device)
+        D = out if out is not None else self._empty((N, self.n, 2 * self.n), dt, q)
         _native.call(self._fn("grid_grad_rnea", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(D),
                      self._stream())
         return D
@@ -150,9 +159,9 @@ class Model:
     def grad_fd(self, q, qd, tau, out=None, qdd_out=None, return_qdd=False):
         """J = [dqdd/dq | dqdd/dqd], [N, n, 2n]; optionally also qdd [N, n]."""
         N, dt, (q, qd, tau) = self._state(q, qd, tau)
-        J = out if out is not None else torch.empty((N, self.n, 2 * self.n), dtype=dt, device=q.device)
+        J = out if out is not None else self._empty((N, self.n, 2 * self.n), dt, q)
         if return_qdd and qdd_out is None:
-            qdd_out = torch.empty((N, self.n), dtype=dt, device=q.device)
+            qdd_out = self._empty((N, self.n), dt, q)
         _native.call(self._fn("grid_grad_fd", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(J),
                      _ptr(qdd_out), self._stream())
         return (J, qdd_out) if return_qdd else J
@@ -163,7 +172,7 @@ class Model:
         recomputed from (q, qd, tau); no Jacobian is formed."""
         N, dt, (q, qd, tau, gbar) = self._state(q, qd, tau, gbar)
         if out is None:
-            out = tuple(torch.empty((N, self.n), dtype=dt, device=q.device) for _ in range(3))
+            out = tuple(self._empty((N, self.n), dt, q) for _ in range(3))
         dq, dqd, dtau = out
         _native.call(self._fn("grid_fd_vjp", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(gbar),
                      _ptr(dq), _ptr(dqd), _ptr(dtau), self._stream())

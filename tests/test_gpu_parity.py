@@ -223,3 +223,23 @@ def test_precision_report_tree30(grid, capsys):
                 assert mx <= TOL32, lines[-1]
     with capsys.disabled():
         print("\n" + "\n".join(lines))
+
+
+def test_zero_copy_host_buffers(grid):
+    """Pinned host buffers passed straight to the kernels (read and written over
+    the CPU-GPU link) give the same results as device buffers."""
+    r = gi.chain7()
+    m = _model(grid, "chain7")
+    (q, qd, tau), _ = _inputs(7, 301, 19, torch.float32)
+    J_dev, qdd_dev = m.grad_fd(q, qd, tau, return_qdd=True)
+    hq, hqd, htau = (t.cpu().pin_memory() for t in (q, qd, tau))
+    J_host, qdd_host = m.grad_fd(hq, hqd, htau, return_qdd=True)
+    torch.cuda.synchronize()
+    assert not J_host.is_cuda and J_host.is_pinned()
+    assert torch.equal(J_host, J_dev.cpu()) and torch.equal(qdd_host, qdd_dev.cpu())
+    gb = torch.from_numpy(gi.upstream(7, 301, 19).astype(np.float32))
+    dv = m.fd_vjp(q, qd, tau, gb.cuda())
+    hv = m.fd_vjp(hq, hqd, htau, gb.pin_memory())
+    torch.cuda.synchronize()
+    for a, b in zip(dv, hv):
+        assert torch.equal(a.cpu(), b)
