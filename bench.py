@@ -259,6 +259,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     robot = gi.chain7()
     model = grid.Model.from_robot(robot)
+    model.set_option("specialize", args.specialize)
     n = robot.n
     Nk = args.traj * KNOTS
     seed = rank_seed(rank)
@@ -313,6 +314,15 @@ def run_ours(args):
     sec_zc = time_steps(e2e_zc_step, e2e_steps, 2, stream, dist)
     e2e_zc_value = aggregate_value(world, Nk, e2e_steps, sec_zc)
     e2e_value = max(e2e_copy_value, e2e_zc_value)
+
+    # The same step in the kernel that reads the topology at run time (the
+    # chain-specialised kernel is kept only if it is the faster one).
+    mgen = grid.Model.from_robot(robot)
+    mgen.set_option("specialize", 1 - args.specialize)
+    gen_steps = max(3, args.steps // 4)
+    sec_gen = time_steps(lambda: mgen.grad_fd(q, qd, tau, out=J), gen_steps, 2, stream, dist)
+    other_value = aggregate_value(world, Nk, gen_steps, sec_gen)
+    mgen.close()
 
     # FP64 plain form on the same GPU (smaller batch, same per-knot work)
     Nd = 256 * KNOTS
@@ -370,6 +380,10 @@ def run_ours(args):
                     "zero_copy": e2e_zc_value, "copies": e2e_copy_value,
                     "note": "pinned host buffers every step; value = the faster of zero copy "
                             "(kernel reads/writes host memory) and explicit H2D + kernel + D2H"},
+            "topology": {"kernel": "chain-specialised" if args.specialize else "run-time topology",
+                         "other_kernel_value": other_value, "unit": UNIT,
+                         "note": "the same step in the other kernel (run-time topology vs the chain "
+                                 "compiled for its length)"},
             "fp64_plain": {"value": fp64_value, "unit": UNIT, "knot_points_per_launch": Nd},
             "tree12": {"value": t12_value, "unit": UNIT, "knot_points_per_launch": Nk // 2},
             "latency_n128_us": sec1 / 200 * 1e6,
@@ -396,6 +410,8 @@ def main():
     ap.add_argument("--traj", type=int, default=TRAJ, help="trajectories of 128 knot points per step")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="measured seconds of the serving leg (0 to skip)")
+    ap.add_argument("--specialize", type=int, default=1, choices=[0, 1],
+                    help="1: chain-specialised kernel for the 7-DoF chain; 0: run-time topology kernel")
     ap.add_argument("--only-main", action="store_true",
                     help="time only the main FP32 step (used for profiling captures)")
     args = ap.parse_args()

@@ -83,6 +83,9 @@ grid_status grid_create(int n, const int* parent, const double* axis, const doub
   m->prec = prec == GRID_FP64 ? GRID_FP32 : prec;
   m->lanes_opt = 0;
   m->ctas_opt = 0;
+  m->specialize_opt = 1;
+  m->chain = n >= 1 && parent != nullptr;
+  for (int i = 0; m->chain && i < n; ++i) m->chain = parent[i] == i - 1;
   m->host_f = new ModelDev<float>();
   m->host_d = new ModelDev<double>();
   grid_status s = grid_build_model(n, parent, axis, X_tree, inertia, gravity, m->host_f, m->host_d);
@@ -135,6 +138,9 @@ grid_status grid_set_option(grid_model* m, const char* key, int value) {
       grid_set_error("precision must be GRID_FP32 or GRID_MIXED"); return GRID_E_ARG;
     }
     m->prec = (grid_precision)value;
+  } else if (k == "specialize") {
+    if (value != 0 && value != 1) { grid_set_error("specialize must be 0 or 1"); return GRID_E_ARG; }
+    m->specialize_opt = value;
   } else if (k == "ctas_per_sm") {
     if (value < 0) { grid_set_error("ctas_per_sm must be >= 0"); return GRID_E_ARG; }
     m->ctas_opt = value;

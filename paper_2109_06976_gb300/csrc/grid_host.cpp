@@ -22,52 +22,6 @@ extern "C" const char* grid_last_error(void) { return g_err; }
 
 namespace {
 
-int round_up(int x, int a) { return (x + a - 1) / a * a; }
-
-// Per-knot shared-memory layout, in scalars of `ssize` bytes. kind: 0 gradient
-// of FD (J stored directly), 1 staged outputs (RNEA, M^-1, FD, gradient of ID),
-// 2 vector-Jacobian product.
-KnotLayout make_layout(int n, int nsk, int nbranch, int ssize, int kind) {
-  KnotLayout L;
-  std::memset(&L, 0, sizeof(L));
-  int off = 0;
-  auto take = [&](int count) { int o = off; off += round_up(count, 4); return o; };
-  L.Q = take(n); L.QD = take(n); L.TAU = take(n); L.QDD = take(n); L.CB = take(n);
-  L.X = take(12 * n);
-  L.VG = take(12 * n); L.BPH = take(12 * n);
-  L.MS = round_up(n, 4);
-  L.MINV = take(n * L.MS);
-  L.SK = take(8 * nsk);
-  L.UNION = off;
-  int b = 0;                                     // M^-1 temporaries
-  auto tb = [&](int count) { int o = b; b += round_up(count, 4); return o; };
-  L.UB = tb(8 * n);
-  L.DINV = tb(ssize == 4 ? 2 * n : n);           // doubles (mixed mode stores them in pairs of floats)
-  L.CT = tb(96);                                 // two 6 x 8 buffers, alternating by body
-  L.BIA = tb(36 * nbranch);
-  L.BP = tb(6 * n * nbranch);
-  int r = 0;                                     // RNEA temporaries
-  auto tr = [&](int count) { int o = r; r += round_up(count, 4); return o; };
-  L.A = tr(8 * n); L.F = tr(8 * n); L.FSL = tr(8 * nbranch);
-  r = std::max(r, b);                            // gravity rows are written while M^-1 runs
-  L.GR = tr(8 * n);
-  if (kind == 2) {
-    L.GB = tr(n); L.LAM = tr(n); L.PSI = tr(8 * n); L.AB = tr(8 * n); L.VB = tr(8 * n);
-    L.SA = tr(8 * nbranch); L.SV = tr(8 * nbranch); L.DQ = tr(n); L.DQD = tr(n);
-  }
-  int c = 2 * n * n;                             // dc
-  L.DC = 0;
-  int u = std::max(b, std::max(r, c));
-  if (kind == 1) { L.JS = u; u += round_up(2 * n * n, 4); }
-  if (kind == 2) { L.JS = u; u += round_up(3 * n, 4); }
-  off += round_up(u, 4);
-  // Knot stride: 16 bytes more than a multiple of 32 bytes, so that the groups of
-  // a warp touching the same field start in different bank quads.
-  const int q = 32 / ssize;                      // scalars per 32 bytes
-  L.stride = round_up(off, q) + q / 2;
-  return L;
-}
-
 struct Unit {            // one root-to-leaf path of one derivative column
   std::vector<uint32_t> steps;
 };

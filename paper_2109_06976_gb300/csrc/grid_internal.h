@@ -63,6 +63,61 @@ struct KnotLayout {
   int stride;                   // scalars per knot
 };
 
+GRID_HD constexpr int grid_round_up(int x, int m) { return (x + m - 1) / m * m; }
+GRID_HD constexpr int grid_imax(int a, int b) { return a > b ? a : b; }
+GRID_HD constexpr int grid_take(int& off, int count) {
+  const int o = off;
+  off += grid_round_up(count, 4);
+  return o;
+}
+
+// Workspace layout of one knot point for n bodies, nsk subspace rows and
+// nbranch branch bodies. ssize is the scalar size in bytes; kind 0 is the
+// gradient-of-FD kernel (J stored directly), 1 the kernels that stage their
+// outputs, 2 the vector-Jacobian product. Evaluated on the host for every model
+// and at compile time for the topology-specialised kernels.
+GRID_HD constexpr KnotLayout make_layout(int n, int nsk, int nbranch, int ssize, int kind) {
+  KnotLayout L{};
+  int off = 0;
+  L.Q = grid_take(off, n); L.QD = grid_take(off, n); L.TAU = grid_take(off, n);
+  L.QDD = grid_take(off, n); L.CB = grid_take(off, n);
+  L.X = grid_take(off, 12 * n);
+  L.VG = grid_take(off, 12 * n); L.BPH = grid_take(off, 12 * n);
+  L.MS = grid_round_up(n, 4);
+  L.MINV = grid_take(off, n * L.MS);
+  L.SK = grid_take(off, 8 * nsk);
+  L.UNION = off;
+  int b = 0;                                          // M^-1 temporaries
+  L.UB = grid_take(b, 8 * n);
+  L.DINV = grid_take(b, ssize == 4 ? 2 * n : n);      // doubles (mixed mode stores them in pairs of floats)
+  L.CT = grid_take(b, 96);                            // two 6 x 8 buffers, alternating by body
+  L.BIA = grid_take(b, 36 * nbranch);
+  L.BP = grid_take(b, 6 * n * nbranch);
+  int r = 0;                                          // RNEA temporaries
+  L.A = grid_take(r, 8 * n); L.F = grid_take(r, 8 * n); L.FSL = grid_take(r, 8 * nbranch);
+  r = grid_imax(r, b);                                // gravity rows are written while M^-1 runs
+  L.GR = grid_take(r, 8 * n);
+  if (kind == 2) {
+    L.GB = grid_take(r, n); L.LAM = grid_take(r, n); L.PSI = grid_take(r, 8 * n);
+    L.AB = grid_take(r, 8 * n); L.VB = grid_take(r, 8 * n);
+    L.SA = grid_take(r, 8 * nbranch); L.SV = grid_take(r, 8 * nbranch);
+    L.DQ = grid_take(r, n); L.DQD = grid_take(r, n);
+  }
+  const int c = 2 * n * n;                            // dc
+  L.DC = 0;
+  int u = grid_imax(b, grid_imax(r, c));
+  if (kind == 1) { L.JS = u; u += grid_round_up(2 * n * n, 4); }
+  if (kind == 2) { L.JS = u; u += grid_round_up(3 * n, 4); }
+  off += grid_round_up(u, 4);
+  // Knot stride: 16 bytes more than a multiple of 32 bytes, so that the groups of
+  // a warp touching the same field start in different bank quads.
+  const int q = 32 / ssize;                           // scalars per 32 bytes
+  L.stride = grid_round_up(off, q) + q / 2;
+  return L;
+}
+
+GRID_HD constexpr int layout_kind(int mode) { return mode == MODE_GRAD ? 0 : (mode == MODE_VJP ? 2 : 1); }
+
 template <class S>
 struct ModelDev {
   int n, maxd, nsk, ncomp, nbranch;
@@ -107,6 +162,8 @@ struct grid_model {
   grid_precision prec;
   int lanes_opt;
   int ctas_opt;
+  int chain;                     // parent[i] = i - 1 for every body (a serial chain)
+  int specialize_opt;            // use the topology-specialised kernels where one exists (default 1)
   ModelDev<float>* dev_f;        // device copies
   ModelDev<double>* dev_d;
   ModelDev<float>* host_f;       // host mirrors (for launch decisions)

@@ -21,8 +21,8 @@
 // ---------------------------------------------------------------- kernel
 __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
 
-template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
-__global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict__ gm, int N,
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N>
+__global__ void __launch_bounds__(128, CHAIN_N > 0 ? 4 : 1) grid_kernel(const ModelDev<S>* __restrict__ gm, int N,
                                                    const S* __restrict__ q, const S* __restrict__ qd,
                                                    const S* __restrict__ x3, const S* __restrict__ x4,
                                                    S* __restrict__ out, S* __restrict__ out2,
@@ -38,7 +38,9 @@ __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict
   }
   __syncthreads();
   const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? M.steps[cfg] : 0;
-  const int stride = layout_of<MODE>(M).stride;
+  int stride;
+  if constexpr (CHAIN_N > 0) stride = ChainTopo<S, MODE, CHAIN_N>::layout().stride;
+  else stride = layout_of<MODE>(M).stride;
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + head);
   for (int i = threadIdx.x; i < nsteps * T; i += blockDim.x) sched[i] = gm->sched[M.sched_off[cfg] + i];
   S* ws = reinterpret_cast<S*>(smem + head + align16(nsteps * T * 4));
@@ -49,8 +51,8 @@ __global__ void __launch_bounds__(128) grid_kernel(const ModelDev<S>* __restrict
   S* Wwarp = ws + warp * G * stride;
   const int ntiles = (N + G - 1) / G;
   for (int tile = blockIdx.x * wpb + warp; tile < ntiles; tile += gridDim.x * wpb)
-    process_tile<S, MODE, T, CPL, MAXD, MIXED>(M, gm, sched, nsteps, Wwarp, lane32, tile * G, N, q, qd,
-                                               x3, x4, out, out2, out3);
+    process_tile<S, MODE, T, CPL, MAXD, MIXED, CHAIN_N>(M, gm, sched, nsteps, Wwarp, lane32, tile * G, N,
+                                                        q, qd, x3, x4, out, out2, out3);
 }
 
 // ---------------------------------------------------------------- launcher
@@ -74,11 +76,18 @@ static inline DevInfo dev_info(int dev) {
   return cache[dev];
 }
 
-template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N = 0>
 grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N,
                      const S* q, const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3,
                      cudaStream_t st) {
-  auto kern = grid_kernel<S, MODE, T, CPL, MAXD, MIXED>;
+  auto kern = grid_kernel<S, MODE, T, CPL, MAXD, MIXED, CHAIN_N>;
+  if constexpr (CHAIN_N > 0) {
+    // the compile-time layout must be the one the host built for this model
+    if (hm->n != CHAIN_N || ChainTopo<S, MODE, CHAIN_N>::layout().stride != layout_of<MODE>(*hm).stride) {
+      grid_set_error("chain kernel for %d bodies does not match the model", CHAIN_N);
+      return GRID_E_TOPOLOGY;
+    }
+  }
   constexpr int cfg = T == 8 ? 0 : (T == 16 ? 1 : 2);
   constexpr int G = 32 / T;
   const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? hm->steps[cfg] : 0;
@@ -143,6 +152,13 @@ grid_status launch_d(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
   return launch_t<S, MODE, T, CPL, 8, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
 }
 
+// Serial chains of 2 .. kChainMaxN bodies run a kernel compiled for their
+// length (grid_chain.cu); 8 lanes per knot point.
+constexpr int kChainMaxN = 8;
+template <class S, int MODE>
+grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
+                         const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
+
 // Picks the lane count T (option or by size) and the M^-1 columns per lane.
 template <class S, int MODE, bool MIXED>
 grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const S* x3, const S* x4,
@@ -153,6 +169,10 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   else { hm = m->host_d; dm = m->dev_d; }
   int T = m->lanes_opt;
   const int n = hm->n;
+  if constexpr (std::is_same<S, float>::value && MODE == MODE_GRAD && !MIXED) {
+    if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
+      return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+  }
   if (T == 0) T = n <= 12 ? 8 : 16;
   const int cpl = (n + T - 1) / T;
   if (T == 8) {

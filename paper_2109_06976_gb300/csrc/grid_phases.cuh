@@ -20,14 +20,60 @@
 #include "grid_internal.h"
 #include "spatial.cuh"
 
-template <class S>
+// ---------------------------------------------------------------- topology
+// The robot's topology as the phases see it. RtTopo reads the staged model
+// (any tree in depth-first numbering). ChainTopo is the serial chain
+// parent(i) = i - 1 of N bodies: depths, subtree ranges, subspace-table
+// offsets and the workspace layout follow from N at compile time, so loops
+// over bodies unroll and their indices fold (per-body constants such as axes
+// and inertias stay in the staged model).
+template <class S, int MODE>
+struct RtTopo {
+  static constexpr int kUnroll = 1;
+  const ModelDev<S>& M;
+  __device__ explicit RtTopo(const ModelDev<S>& m) : M(m) {}
+  __device__ const KnotLayout& layout() const { return layout_of<MODE>(M); }
+  __device__ int n() const { return M.n; }
+  __device__ int maxd() const { return M.maxd; }
+  __device__ int nbranch() const { return M.nbranch; }
+  __device__ int parent(int i) const { return M.parent[i]; }
+  __device__ int depth(int i) const { return M.depth[i]; }
+  __device__ int sub_end(int i) const { return M.sub_end[i]; }
+  __device__ int comp_lo(int i) const { return M.comp_lo[i]; }
+  __device__ int comp_hi(int i) const { return M.comp_hi[i]; }
+  __device__ int perm(int i) const { return M.perm[i]; }
+  __device__ int skoff(int i) const { return M.skoff[i]; }
+  __device__ int branch(int i) const { return M.branch[i]; }
+};
+
+template <class S, int MODE, int N>
+struct ChainTopo {
+  static constexpr int kUnroll = N;
+  __device__ explicit ChainTopo(const ModelDev<S>&) {}
+  GRID_HD static constexpr KnotLayout layout() {
+    return make_layout(N, N * (N + 1) / 2, 0, (int)sizeof(S), layout_kind(MODE));
+  }
+  GRID_HD static constexpr int n() { return N; }
+  GRID_HD static constexpr int maxd() { return N; }       // depth levels
+  GRID_HD static constexpr int nbranch() { return 0; }
+  GRID_HD static constexpr int parent(int i) { return i - 1; }
+  GRID_HD static constexpr int depth(int i) { return i; }
+  GRID_HD static constexpr int sub_end(int) { return N; }
+  GRID_HD static constexpr int comp_lo(int) { return 0; }
+  GRID_HD static constexpr int comp_hi(int) { return N; }
+  GRID_HD static constexpr int perm(int i) { return i; }
+  GRID_HD static constexpr int skoff(int i) { return i * (i + 1) / 2; }
+  GRID_HD static constexpr int branch(int) { return -1; }
+};
+
+template <class S, class Tp>
 struct Ctx {
   const ModelDev<S>& M;
   const ModelDev<S>* gM;  // the same model in device memory (tables not staged in shared memory)
-  const KnotLayout& L;  // workspace layout of this kernel mode
-  S* W;                 // this knot point's workspace
-  int l;                // lane within the group, 0..T-1
-  int lane32;           // lane within the warp
+  Tp tp;                  // topology
+  S* W;                   // this knot point's workspace
+  int l;                  // lane within the group, 0..T-1
+  int lane32;             // lane within the warp
 };
 
 #ifndef GRID_SYNC
@@ -42,13 +88,14 @@ struct Ctx {
 #define SYNC() GRID_SYNC()
 
 // ---------------------------------------------------------------- B1
-template <class S, int T>
-__device__ void ph_transforms(const Ctx<S>& c) {
+template <class S, int T, class Tp>
+__device__ void ph_transforms(const Ctx<S, Tp>& c) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
-  for (int k = c.l; k < M.n; k += T) {
-    S qk = W[L.Q + M.perm[k]];
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
+  for (int k = c.l; k < tp.n(); k += T) {
+    S qk = W[L.Q + tp.perm(k)];
     S s, co;
     if constexpr (std::is_same<S, float>::value) sincosf(qk, &s, &co); else sincos(qk, &s, &co);
     const S* a = M.axis[k];
@@ -83,27 +130,28 @@ __device__ void ph_transforms(const Ctx<S>& c) {
 // kept in the phase-local area GR.
 // s_m^(k) = X_k s_m^(parent k). Row id rho (d, or maxd for gravity) belongs to
 // lane rho mod T, which therefore only reads rows it wrote itself.
-template <class S, int T>
-__device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E, S* carry) {
+template <class S, int T, class Tp>
+__device__ __forceinline__ void subspace_step(const Ctx<S, Tp>& c, int k, const S* E, S* carry) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   S* SK = W + L.SK;
   S* GR = W + L.UNION + L.GR;
-  const int dk = M.depth[k];
-  const int p = M.parent[k];
-  const bool carry_ok = T > M.maxd;        // one row id per lane: reuse the previous body's row
-  for (int rho = c.l; rho <= M.maxd; rho += T) {
+  const int dk = tp.depth(k);
+  const int p = tp.parent(k);
+  const bool carry_ok = T > tp.maxd();        // one row id per lane: reuse the previous body's row
+  for (int rho = c.l; rho <= tp.maxd(); rho += T) {
     if (rho == dk) {
       S row[8] = {M.axis[k][0], M.axis[k][1], M.axis[k][2], S(0), S(0), S(0),
-                  W[L.QD + M.perm[k]], S(k)};
-      S* dst = SK + 8 * (M.skoff[k] + dk);
+                  W[L.QD + tp.perm(k)], S(k)};
+      S* dst = SK + 8 * (tp.skoff(k) + dk);
       st4(dst, row);
       st4(dst + 4, row + 4);
 #pragma unroll
       for (int e = 0; e < 8; ++e) carry[e] = row[e];
-    } else if (rho < dk || rho == M.maxd) {
-      const bool grav = rho == M.maxd;
+    } else if (rho < dk || rho == tp.maxd()) {
+      const bool grav = rho == tp.maxd();
       S src[8];
       if (p < 0) {
 #pragma unroll
@@ -113,7 +161,7 @@ __device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E
 #pragma unroll
         for (int e = 0; e < 8; ++e) src[e] = carry[e];
       } else {
-        const S* sp = grav ? GR + 8 * p : SK + 8 * (M.skoff[p] + rho);
+        const S* sp = grav ? GR + 8 * p : SK + 8 * (tp.skoff(p) + rho);
         ld4(sp, src);
         ld4(sp + 4, src + 4);
       }
@@ -121,7 +169,7 @@ __device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E
       x_mul(E, E + 9, src, out);
       out[6] = src[6];
       out[7] = src[7];
-      S* dst = grav ? GR + 8 * k : SK + 8 * (M.skoff[k] + rho);
+      S* dst = grav ? GR + 8 * k : SK + 8 * (tp.skoff(k) + rho);
       st4(dst, out);
       st4(dst + 4, out + 4);
 #pragma unroll
@@ -130,13 +178,14 @@ __device__ __forceinline__ void subspace_step(const Ctx<S>& c, int k, const S* E
   }
 }
 
-template <class S, int T>
-__device__ void ph_subspaces(const Ctx<S>& c) {
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
+template <class S, int T, class Tp>
+__device__ void ph_subspaces(const Ctx<S, Tp>& c) {
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   S carry[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) carry[e] = S(0);
-  for (int k = 0; k < c.M.n; ++k) {
+#pragma unroll (Tp::kUnroll)
+  for (int k = 0; k < c.tp.n(); ++k) {
     S E[12];
     ld12(c.W + L.X + 12 * k, E);
     subspace_step<S, T>(c, k, E, carry);
@@ -159,13 +208,14 @@ __device__ void ph_subspaces(const Ctx<S>& c) {
 // next body processed (the first child is i + 1), and through per-branch-body
 // slots otherwise. With P = double (mixed precision) the pivots D_i, D_i^-1
 // and every update divided by them are evaluated in FP64.
-template <class S, class P, int T, int CPL, bool WITH_SK>
-__device__ void ph_minv(const Ctx<S>& c) {
+template <class S, class P, int T, int CPL, bool WITH_SK, class Tp>
+__device__ void ph_minv(const Ctx<S, Tp>& c) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   const int l = c.l;
-  const int n = M.n;
+  const int n = tp.n();
   const int U = L.UNION;
   const int MS = L.MS;
   const int base = c.lane32 - l;
@@ -175,7 +225,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
   S* BIA = W + U + L.BIA;
   S* BP = W + U + L.BP;
   for (int e = l; e < n * MS; e += T) MI[e] = S(0);
-  for (int e = l; e < 36 * M.nbranch; e += T) BIA[e] = S(0);
+  for (int e = l; e < 36 * tp.nbranch(); e += T) BIA[e] = S(0);
   SYNC();
   S carry[6], fb[CPL][6];
 #pragma unroll
@@ -184,9 +234,10 @@ __device__ void ph_minv(const Ctx<S>& c) {
   for (int cc = 0; cc < CPL; ++cc)
 #pragma unroll
     for (int e = 0; e < 6; ++e) fb[cc][e] = S(0);
+#pragma unroll (Tp::kUnroll)
   for (int i = n - 1; i >= 0; --i) {
-    const int p = M.parent[i];
-    const int br = M.branch[i];
+    const int p = tp.parent(i);
+    const int br = tp.branch(i);
     S E[12];
     ld12(W + L.X + 12 * i, E);
     const S* r = E + 9;
@@ -195,7 +246,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
     S ul = S(0);
     if (l < 6) {                              // column l of I^A_i
       ld6(c.gM->Icol[i][l], ia);
-      if (i + 1 < n && M.parent[i + 1] == i) {
+      if (i + 1 < n && tp.parent(i + 1) == i) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) ia[e] += carry[e];
       }
@@ -216,7 +267,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
 #pragma unroll
     for (int cc = 0; cc < CPL; ++cc) {
       const int k = l + cc * T;
-      if (k >= i && k < M.sub_end[i]) {
+      if (k >= i && k < tp.sub_end(i)) {
         S mik;
         if (k == i) mik = S(Dinv);
         else mik = S(-Dinv * (P(a[0]) * P(fb[cc][0]) + P(a[1]) * P(fb[cc][1]) + P(a[2]) * P(fb[cc][2])));
@@ -249,7 +300,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) carry[e] = it[e];
       } else {
-        S* slot = BIA + 36 * M.branch[p] + 6 * l;
+        S* slot = BIA + 36 * tp.branch(p) + 6 * l;
 #pragma unroll
         for (int e = 0; e < 6; ++e) slot[e] += it[e];
       }
@@ -264,9 +315,10 @@ __device__ void ph_minv(const Ctx<S>& c) {
     for (int e = 0; e < 6; ++e) pc[cc][e] = S(0);
 #pragma unroll
   for (int e = 0; e < 8; ++e) skc[e] = S(0);
+#pragma unroll (Tp::kUnroll)
   for (int i = 0; i < n; ++i) {
-    const int p = M.parent[i];
-    const int br = M.branch[i];
+    const int p = tp.parent(i);
+    const int br = tp.branch(i);
     S E[12];
     ld12(W + L.X + 12 * i, E);
     const S* r = E + 9;
@@ -277,7 +329,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
 #pragma unroll
     for (int cc = 0; cc < CPL; ++cc) {
       const int k = l + cc * T;
-      if (k >= i && k < M.comp_hi[i]) {
+      if (k >= i && k < tp.comp_hi(i)) {
         S t[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
         S mk = MI[i * MS + k];
         if (p >= 0) {
@@ -287,7 +339,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
             for (int e = 0; e < 6; ++e) pp[e] = pc[cc][e];
           } else {
 #pragma unroll
-            for (int e = 0; e < 6; ++e) pp[e] = BP[(6 * M.branch[p] + e) * n + k];
+            for (int e = 0; e < 6; ++e) pp[e] = BP[(6 * tp.branch(p) + e) * n + k];
           }
           x_mul(E, r, pp, t);
           P ut = P(Ui[0]) * P(t[0]);
@@ -311,7 +363,7 @@ __device__ void ph_minv(const Ctx<S>& c) {
   for (int cc = 0; cc < CPL; ++cc) {
     const int k = l + cc * T;
     if (k < n)
-      for (int i = M.comp_lo[k]; i < k; ++i) MI[k * MS + i] = MI[i * MS + k];
+      for (int i = tp.comp_lo(k); i < k; ++i) MI[k * MS + i] = MI[i * MS + k];
   }
   SYNC();
 }
@@ -323,15 +375,16 @@ __device__ void ph_minv(const Ctx<S>& c) {
 //   gamma_k = I_k v_k,  f_k = I_k a_k + v_k x* gamma_k
 // (the forward recursion v_i = X v_p + S qd_i, a_i = X a_p + S qdd_i + v_i x S qd_i
 // unrolled over the path). qdd_off < 0 means qdd = 0.
-template <class S, int T>
-__device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
+template <class S, int T, class Tp>
+__device__ void ph_rnea_bodies(const Ctx<S, Tp>& c, int qdd_off) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   const int U = L.UNION;
-  for (int k = c.l; k < M.n; k += T) {
-    const int dk = M.depth[k];
-    const S* rows = W + L.SK + 8 * M.skoff[k];
+  for (int k = c.l; k < tp.n(); k += T) {
+    const int dk = tp.depth(k);
+    const S* rows = W + L.SK + 8 * tp.skoff(k);
     S v[6], a[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) v[e] = S(0);
@@ -346,7 +399,7 @@ __device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
       for (int e = 0; e < 6; ++e) { sq[e] = s[e] * qd; v[e] += sq[e]; }
       crm_mul(v, sq, t);
       S qdd = S(0);
-      if (qdd_off >= 0) qdd = W[qdd_off + M.perm[(int)s[7]]];
+      if (qdd_off >= 0) qdd = W[qdd_off + tp.perm((int)s[7])];
 #pragma unroll
       for (int e = 0; e < 6; ++e) a[e] += t[e] + s[e] * qdd;
     }
@@ -367,17 +420,18 @@ __device__ void ph_rnea_bodies(const Ctx<S>& c, int qdd_off) {
 // ---------------------------------------------------------------- B5
 // Joint forces from body forces: c_i = S_i^T F_i = sum_{k in subtree(i)} s_i^(k) . f_k
 // (the RNEA backward sweep F_p += X^T F_i, tau_i = S_i^T F_i, unrolled).
-template <class S, int T>
-__device__ void ph_joint_forces(const Ctx<S>& c, int f_off, int out_off) {
+template <class S, int T, class Tp>
+__device__ void ph_joint_forces(const Ctx<S, Tp>& c, int f_off, int out_off) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
-  for (int i = c.l; i < M.n; i += T) {
-    const int di = M.depth[i];
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
+  for (int i = c.l; i < tp.n(); i += T) {
+    const int di = tp.depth(i);
     S acc = S(0);
-    for (int k = i; k < M.sub_end[i]; ++k) {
+    for (int k = i; k < tp.sub_end(i); ++k) {
       S s[6], f[6];
-      ld6(W + L.SK + 8 * (M.skoff[k] + di), s);
+      ld6(W + L.SK + 8 * (tp.skoff(k) + di), s);
       ld6(W + f_off + 8 * k, f);
       acc += s[0] * f[0] + s[1] * f[1] + s[2] * f[2] + s[3] * f[3] + s[4] * f[4] + s[5] * f[5];
     }
@@ -387,16 +441,18 @@ __device__ void ph_joint_forces(const Ctx<S>& c, int f_off, int out_off) {
 }
 
 // ---------------------------------------------------------------- B6
-template <class S, int T>
-__device__ void ph_fd(const Ctx<S>& c) {
+template <class S, int T, class Tp>
+__device__ void ph_fd(const Ctx<S, Tp>& c) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
-  const int n = M.n;
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
+  const int n = tp.n();
   for (int i = c.l; i < n; i += T) {
     S acc = S(0);
-    for (int j = M.comp_lo[i]; j < M.comp_hi[i]; ++j)
-      acc += W[L.MINV + i * L.MS + j] * (W[L.TAU + M.perm[j]] - W[L.CB + j]);
+#pragma unroll (Tp::kUnroll)
+    for (int j = tp.comp_lo(i); j < tp.comp_hi(i); ++j)
+      acc += W[L.MINV + i * L.MS + j] * (W[L.TAU + tp.perm(j)] - W[L.CB + j]);
     W[L.QDD + i] = acc;
   }
   SYNC();
@@ -408,19 +464,20 @@ __device__ void ph_fd(const Ctx<S>& c) {
 // (so beta_k = (a_k - qd_k v_k x S_k) x S_k, as S x S = 0). Then the
 // accumulated forces F_i = f_i + sum_children X_c^T F_c (lanes over
 // components) and phi_i = S_i x* F_i.
-template <class S, int T, bool ADD_QDD>
-__device__ void ph_update_and_forces(const Ctx<S>& c) {
+template <class S, int T, bool ADD_QDD, class Tp>
+__device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   const int U = L.UNION;
   const int l = c.l;
   S* FA = W + U + L.F;                     // own forces, made accumulated in place
   S* FSL = W + U + L.FSL;
-  for (int e = l; e < 8 * M.nbranch; e += T) FSL[e] = S(0);
-  for (int k = l; k < M.n; k += T) {
-    const int dk = M.depth[k];
-    const S* rows = W + L.SK + 8 * M.skoff[k];
+  for (int e = l; e < 8 * tp.nbranch(); e += T) FSL[e] = S(0);
+  for (int k = l; k < tp.n(); k += T) {
+    const int dk = tp.depth(k);
+    const S* rows = W + L.SK + 8 * tp.skoff(k);
     S da[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
     if (ADD_QDD) {                          // accelerations so far exclude qdd
       for (int d = 0; d <= dk; ++d) {
@@ -437,7 +494,7 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
     ld6(W + L.VG + 12 * k, v);
     ld6(W + U + L.A + 8 * k, a);
     ld6(FA + 8 * k, fo);
-    const S qdk = W[L.QD + M.perm[k]];
+    const S qdk = W[L.QD + tp.perm(k)];
     S idt[6], vxs[6], w[6];
     i_mul(M.inert[k], da, idt);
     cross3(v, ax, vxs);
@@ -459,13 +516,14 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
   // parent when the parent is the next body (k - 1), else through a slot.
   const int base = c.lane32 - l;
   S carry = S(0);
-  for (int k = M.n - 1; k >= 0; --k) {
-    const int p = M.parent[k];
-    const int br = M.branch[k];
+#pragma unroll (Tp::kUnroll)
+  for (int k = tp.n() - 1; k >= 0; --k) {
+    const int p = tp.parent(k);
+    const int br = tp.branch(k);
     S fk = S(0);
     if (l < 6) {
       fk = FA[8 * k + l];
-      if (k + 1 < M.n && M.parent[k + 1] == k) fk += carry;
+      if (k + 1 < tp.n() && tp.parent(k + 1) == k) fk += carry;
       if (br >= 0) fk += FSL[8 * br + l];
     }
     S F[6];
@@ -478,12 +536,12 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
         ld12(W + L.X + 12 * k, E);
         const S cl = xt_mul_c(E, E + 9, F, l);
         if (p == k - 1) carry = cl;
-        else FSL[8 * M.branch[p] + l] += cl;
+        else FSL[8 * tp.branch(p) + l] += cl;
       }
     }
   }
   SYNC();
-  for (int k = l; k < M.n; k += T) {
+  for (int k = l; k < tp.n(); k += T) {
     S F[6];
     ld6(FA + 8 * k, F);
     const S* ax = M.axis[k];
@@ -507,12 +565,13 @@ __device__ void ph_update_and_forces(const Ctx<S>& c) {
 // plus s_i^(j) . phi_j for the strict ancestors i of j when u = q. Each lane
 // accumulates these dot products per depth along its path in registers and
 // adds them to dc at the path's end.
-template <class S, int T, int MAXD>
-__device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, int nsteps) {
+template <class S, int T, int MAXD, class Tp>
+__device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sched, int nsteps) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
-  const int n = M.n;
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
+  const int n = tp.n();
   const int U = L.UNION;
   S* DC = W + U + L.DC;
   for (int e = c.l; e < 2 * n * n; e += T) DC[e] = S(0);
@@ -603,7 +662,7 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
         if (d <= dk) {
           GRID_ATOMIC_ADD(DC + b * 2 * n + col, acc[d]);
           acc[d] = S(0);
-          b = M.parent[b];
+          b = tp.parent(b);
         }
       }
     }
@@ -615,12 +674,13 @@ __device__ void ph_columns(const Ctx<S>& c, const uint32_t* __restrict__ sched, 
 
 // ---------------------------------------------------------------- D
 // J = -M^-1 dc, restricted to base-branch blocks, written in caller order.
-template <class S, int T, int CPL>
-__device__ void ph_product(const Ctx<S>& c, S* __restrict__ J) {
+template <class S, int T, int CPL, class Tp>
+__device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
-  const int n = M.n, n2 = 2 * n, MS = L.MS;
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
+  const int n = tp.n(), n2 = 2 * n, MS = L.MS;
   const int U = L.UNION;
   const S* DC = W + U + L.DC;
   const S* MI = W + L.MINV;
@@ -631,15 +691,16 @@ __device__ void ph_product(const Ctx<S>& c, S* __restrict__ J) {
   // written directly: the group's lanes cover consecutive columns of a row.
   for (int col = c.l; col < n2; col += T) {
     const int j = col < n ? col : col - n;
-    const int lo = M.comp_lo[j], hi = M.comp_hi[j];
+    const int lo = tp.comp_lo(j), hi = tp.comp_hi(j);
     S dcr[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) dcr[m] = (m >= lo && m < hi) ? DC[m * n2 + col] : S(0);
-    const int ucol = (col < n ? 0 : n) + M.perm[j];
+    const int ucol = (col < n ? 0 : n) + tp.perm(j);
     if (J) {
-      for (int i = 0; i < lo; ++i) J[M.perm[i] * n2 + ucol] = S(0);     // other base branches
-      for (int i = hi; i < n; ++i) J[M.perm[i] * n2 + ucol] = S(0);
+      for (int i = 0; i < lo; ++i) J[tp.perm(i) * n2 + ucol] = S(0);     // other base branches
+      for (int i = hi; i < n; ++i) J[tp.perm(i) * n2 + ucol] = S(0);
     }
+#pragma unroll (Tp::kUnroll)
     for (int i = lo; i < hi; ++i) {
       const S* mrow = MI + i * MS;
       S acc = S(0);
@@ -651,7 +712,7 @@ __device__ void ph_product(const Ctx<S>& c, S* __restrict__ J) {
           acc += mm[0] * dcr[m] + mm[1] * dcr[m + 1] + mm[2] * dcr[m + 2] + mm[3] * dcr[m + 3];
         }
       }
-      if (J) J[M.perm[i] * n2 + ucol] = -acc;
+      if (J) J[tp.perm(i) * n2 + ucol] = -acc;
     }
   }
   SYNC();
@@ -670,22 +731,24 @@ __device__ void ph_product(const Ctx<S>& c, S* __restrict__ J) {
 // and for joint k
 //   (dID/dqd)^T lambda |_k = S_k^T Vbar_k + Abar_k . (v_k x S_k)
 //   (dID/dq)^T lambda  |_k = Vbar_k . (v_k x S_k) + Abar_k . beta_k + F_k . (psi_k x S_k).
-template <class S, int T>
-__device__ void ph_vjp_seeds(const Ctx<S>& c) {
+template <class S, int T, class Tp>
+__device__ void ph_vjp_seeds(const Ctx<S, Tp>& c) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   const int U = L.UNION;
-  const int n = M.n;
+  const int n = tp.n();
   for (int i = c.l; i < n; i += T) {
     S acc = S(0);
-    for (int j = M.comp_lo[i]; j < M.comp_hi[i]; ++j) acc += W[L.MINV + i * L.MS + j] * W[U + L.GB + M.perm[j]];
+#pragma unroll (Tp::kUnroll)
+    for (int j = tp.comp_lo(i); j < tp.comp_hi(i); ++j) acc += W[L.MINV + i * L.MS + j] * W[U + L.GB + tp.perm(j)];
     W[U + L.LAM + i] = acc;
   }
   SYNC();
   for (int k = c.l; k < n; k += T) {
-    const int dk = M.depth[k];
-    const S* rows = W + L.SK + 8 * M.skoff[k];
+    const int dk = tp.depth(k);
+    const S* rows = W + L.SK + 8 * tp.skoff(k);
     S psi[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
     for (int d = 0; d <= dk; ++d) {
       S s[8];
@@ -709,27 +772,29 @@ __device__ void ph_vjp_seeds(const Ctx<S>& c) {
     st6(W + U + L.VB + 8 * k, t1);
     st6(W + U + L.PSI + 8 * k, psi);
   }
-  for (int e = c.l; e < 8 * M.nbranch; e += T) { W[U + L.SA + e] = S(0); W[U + L.SV + e] = S(0); }
+  for (int e = c.l; e < 8 * tp.nbranch(); e += T) { W[U + L.SA + e] = S(0); W[U + L.SV + e] = S(0); }
   SYNC();
 }
 
-template <class S, int T>
-__device__ void ph_vjp_sweep(const Ctx<S>& c) {
+template <class S, int T, class Tp>
+__device__ void ph_vjp_sweep(const Ctx<S, Tp>& c) {
   const ModelDev<S>& M = c.M;
+  const Tp& tp = c.tp;
   S* W = c.W;
-  const KnotLayout L = c.L;   // by value: offsets stay in registers
+  const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   const int U = L.UNION;
   const int l = c.l;
   const int base = c.lane32 - l;
   S* SA = W + U + L.SA;
   S* SV = W + U + L.SV;
   S ca = S(0), cv = S(0);
-  for (int k = M.n - 1; k >= 0; --k) {
-    const int p = M.parent[k];
-    const int br = M.branch[k];
-    const bool from_next = k + 1 < M.n && M.parent[k + 1] == k;
+#pragma unroll (Tp::kUnroll)
+  for (int k = tp.n() - 1; k >= 0; --k) {
+    const int p = tp.parent(k);
+    const int br = tp.branch(k);
+    const bool from_next = k + 1 < tp.n() && tp.parent(k + 1) == k;
     const S* ax = M.axis[k];
-    const S qdk = W[L.QD + M.perm[k]];
+    const S qdk = W[L.QD + tp.perm(k)];
     S ab = S(0), vb = S(0);
     if (l < 6) {
       ab = W[U + L.AB + 8 * k + l] + (from_next ? ca : S(0)) + (br >= 0 ? SA[8 * br + l] : S(0));
@@ -777,7 +842,7 @@ __device__ void ph_vjp_sweep(const Ctx<S>& c) {
       const S xa = xt_mul_c(E, E + 9, A, l);
       const S xv = xt_mul_c(E, E + 9, V, l);
       if (p == k - 1) { ca = xa; cv = xv; }
-      else { SA[8 * M.branch[p] + l] += xa; SV[8 * M.branch[p] + l] += xv; }
+      else { SA[8 * tp.branch(p) + l] += xa; SV[8 * tp.branch(p) + l] += xv; }
     }
   }
   SYNC();
@@ -785,19 +850,21 @@ __device__ void ph_vjp_sweep(const Ctx<S>& c) {
 
 // One warp processes knot points k0 .. k0 + 32/T - 1 (those < N). M is the
 // shared-memory copy of the model, gM the same model in device memory.
-template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED>
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N = 0>
 __device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const uint32_t* __restrict__ sched,
                              int nsteps, S* Wwarp, int lane32, int k0, int N, const S* __restrict__ q,
                              const S* __restrict__ qd, const S* __restrict__ x3,
                              const S* __restrict__ x4, S* __restrict__ out, S* __restrict__ out2,
                              S* __restrict__ out3) {
   using P = typename std::conditional<MIXED, double, S>::type;
-  const KnotLayout& L = layout_of<MODE>(M);
-  const int n = M.n;
+  using Tp = typename std::conditional<CHAIN_N == 0, RtTopo<S, MODE>, ChainTopo<S, MODE, CHAIN_N>>::type;
+  const Tp tp(M);
+  const auto& L = tp.layout();     // the staged layout (runtime topology) or a compile-time constant
+  const int n = tp.n();
   constexpr int G = 32 / T;
   const int g = lane32 / T;
   S* W = Wwarp + g * L.stride;
-  const Ctx<S> c{M, gM, L, W, lane32 % T, lane32};
+  const Ctx<S, Tp> c{M, gM, tp, W, lane32 % T, lane32};
   const int nvalid = min(G, N - k0);
   // stage inputs (coalesced across the warp)
   for (int e = lane32; e < G * n; e += 32) {
@@ -840,7 +907,7 @@ __device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const 
   }
   if constexpr (MODE == MODE_GRAD) {
     if (out2) {                                     // qdd in caller order
-      for (int i = c.l; i < n; i += T) W[L.CB + M.perm[i]] = W[L.QDD + i];
+      for (int i = c.l; i < n; i += T) W[L.CB + tp.perm(i)] = W[L.QDD + i];
       SYNC();
       for (int e = lane32; e < nvalid * n; e += 32) {
         const int kk = e / n, r = e % n;
@@ -851,9 +918,9 @@ __device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const 
   } else if constexpr (MODE == MODE_VJP) {
     S* OS = W + L.UNION + L.JS;
     for (int i = c.l; i < n; i += T) {
-      OS[M.perm[i]] = W[L.UNION + L.DQ + i];
-      OS[n + M.perm[i]] = W[L.UNION + L.DQD + i];
-      OS[2 * n + M.perm[i]] = W[L.UNION + L.LAM + i];
+      OS[tp.perm(i)] = W[L.UNION + L.DQ + i];
+      OS[n + tp.perm(i)] = W[L.UNION + L.DQD + i];
+      OS[2 * n + tp.perm(i)] = W[L.UNION + L.LAM + i];
     }
     SYNC();
     for (int e = lane32; e < nvalid * n; e += 32) {
@@ -869,16 +936,16 @@ __device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const 
     const int out_per = MODE == MODE_MINV ? n * n : (MODE == MODE_GRAD_ID ? 2 * n * n : n);
     S* OS = W + L.UNION + L.JS;
     if (MODE == MODE_RNEA) {
-      for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.CB + i];
+      for (int i = c.l; i < n; i += T) OS[tp.perm(i)] = W[L.CB + i];
     } else if (MODE == MODE_FD) {
-      for (int i = c.l; i < n; i += T) OS[M.perm[i]] = W[L.QDD + i];
+      for (int i = c.l; i < n; i += T) OS[tp.perm(i)] = W[L.QDD + i];
     } else if (MODE == MODE_MINV) {
-      for (int e = c.l; e < n * n; e += T) OS[M.perm[e / n] * n + M.perm[e % n]] = W[L.MINV + (e / n) * L.MS + e % n];
+      for (int e = c.l; e < n * n; e += T) OS[tp.perm(e / n) * n + tp.perm(e % n)] = W[L.MINV + (e / n) * L.MS + e % n];
     } else {
       const S* DC = W + L.UNION + L.DC;
       for (int e = c.l; e < 2 * n * n; e += T) {    // dc is [i][u n + j]
         const int i = e / (2 * n), col = e % (2 * n), j = col < n ? col : col - n;
-        OS[M.perm[i] * 2 * n + (col < n ? 0 : n) + M.perm[j]] = DC[e];
+        OS[tp.perm(i) * 2 * n + (col < n ? 0 : n) + tp.perm(j)] = DC[e];
       }
     }
     SYNC();

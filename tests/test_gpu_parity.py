@@ -110,6 +110,30 @@ def test_lane_counts_agree(grid, key, lanes):
     assert col_rel_err(J, oracle.grad_fd(r, q64, qd64, tau64)) <= TOL32
 
 
+CHAINS = [(n, s, g) for n in range(2, 10) for s, g in ((1, True), (2, False))]
+
+
+@pytest.mark.parametrize("n,seed,general", CHAINS, ids=lambda x: str(x))
+def test_chain_specialised_kernel(grid, n, seed, general):
+    """Serial chains (parent[i] = i - 1): the kernel compiled for the chain's
+    length against the oracle and against the run-time-topology kernel, on a
+    ragged batch; n = 9 has no specialised kernel and takes the general one."""
+    r = gi.random_tree(n, seed, general=general, max_children=1)
+    assert all(int(r.parent[i]) == i - 1 for i in range(n))
+    spec = grid.Model.from_robot(r)
+    gen = grid.Model.from_robot(r)
+    gen.set_option("specialize", 0)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, 77, 11, torch.float32)
+    Js, qdds = spec.grad_fd(q, qd, tau, return_qdd=True)
+    Jg, qddg = gen.grad_fd(q, qd, tau, return_qdd=True)
+    Js, qdds, Jg, qddg = (x.cpu().numpy() for x in (Js, qdds, Jg, qddg))
+    ref = oracle.grad_fd(r, q64, qd64, tau64)
+    assert col_rel_err(Js, ref, floor=1e-4) <= TOL32
+    assert vec_rel_err(qdds, oracle.fd(r, q64, qd64, tau64)) <= TOL32
+    assert col_rel_err(Js, Jg, floor=1e-4) <= 1e-5
+    assert vec_rel_err(qdds, qddg) <= 1e-5
+
+
 @pytest.mark.parametrize("key", WORKLOAD)
 def test_grad_fd_workload_sizes(grid, key):
     """The workload batch sizes (N = 16 .. 1024) in one call each."""
