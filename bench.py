@@ -171,6 +171,47 @@ def time_steps(fn, steps, warmup, stream, dist=None):
     return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
 
 
+def latency_table(grid, reps=200, warmup=20):
+    """Single-computation latency (one knot point, compute only, inputs resident)
+    of each entry point for the three workload robots: median over `reps` calls,
+    each bracketed by CUDA events on the launching stream."""
+    import numpy as np
+    import torch
+    import grid_inputs as gi
+    stream = torch.cuda.current_stream()
+    table = {}
+    for name in ("chain7", "tree12", "tree30"):
+        r = gi.robot(name)
+        m = grid.Model.from_robot(r, precision="mixed" if name == "tree30" else "fp32")
+        q, qd, tau = (torch.from_numpy(x.astype(np.float32)).cuda() for x in gi.states(r.n, 1, 77))
+        outs = {"rnea": torch.empty((1, r.n), device="cuda"),
+                "minv": torch.empty((1, r.n, r.n), device="cuda"),
+                "fd": torch.empty((1, r.n), device="cuda"),
+                "grad_id": torch.empty((1, r.n, 2 * r.n), device="cuda"),
+                "grad_fd": torch.empty((1, r.n, 2 * r.n), device="cuda")}
+        calls = {"rnea": lambda: m.rnea(q, qd, tau, out=outs["rnea"]),
+                 "minv": lambda: m.minv(q, out=outs["minv"]),
+                 "fd": lambda: m.fd(q, qd, tau, out=outs["fd"]),
+                 "grad_id": lambda: m.grad_rnea(q, qd, tau, out=outs["grad_id"]),
+                 "grad_fd": lambda: m.grad_fd(q, qd, tau, out=outs["grad_fd"])}
+        row = {}
+        for alg, fn in calls.items():
+            for _ in range(warmup):
+                fn()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(reps)]
+            torch.cuda.synchronize()
+            for e0, e1 in ev:
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            row[alg] = float(np.median([e0.elapsed_time(e1) * 1e3 for e0, e1 in ev]))
+        table[name] = row
+        m.close()
+    return table
+
+
 def cpu_oracle_rate(robot, seconds_min=10.0, seconds_max=30.0, threads=None):
     """The FP64 oracle as it stands on the host cores, on a bounded sample of the
     workload: repeated batches of 128-knot trajectories until >= seconds_min."""
@@ -346,6 +387,8 @@ def run_ours(args):
     J1 = J[:KNOTS]
     sec1 = time_steps(lambda: model.grad_fd(q1, qd1, tau1, out=J1), 200, 20, stream, None)
 
+    lat_table = latency_table(grid) if rank == 0 else None
+
     serve = None
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         serve = serve_leg(grid, args.serve_seconds)
@@ -387,6 +430,9 @@ def run_ours(args):
             "fp64_plain": {"value": fp64_value, "unit": UNIT, "knot_points_per_launch": Nd},
             "tree12": {"value": t12_value, "unit": UNIT, "knot_points_per_launch": Nk // 2},
             "latency_n128_us": sec1 / 200 * 1e6,
+            "latency_n1_us": lat_table,
+            "latency_n1_note": "one knot point per call, compute only, median of 200 event-timed calls "
+                               "(RNEA at qdd = tau's values; tree30 in mixed precision)",
             "serve": serve,
             "cpu_baseline": cpu,
             "clocks": clocks,

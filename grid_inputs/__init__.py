@@ -5,7 +5,10 @@ draws numbers; it holds none of the dynamics arithmetic (no spatial algebra, no
 inertia assembly, no transforms). Both sides consume the raw arrays it returns:
 
   parent  int32 [n]       parent body index, -1 = fixed base, parent[i] < i
-  axis    float64 [n,3]   unit revolute axis in the joint (child) frame
+  jtype   int32 [n]       joint type: 0 revolute, 1 prismatic, 2 fixed (optional;
+                          absent means all revolute)
+  axis    float64 [n,3]   unit joint axis in the joint (child) frame (ignored
+                          for a fixed joint)
   xtree   float64 [n,12]  E (3x3 row-major, maps parent coordinates to child
                           coordinates) then r (child origin in parent coords)
   inertia float64 [n,10]  m, c[3] (COM in link frame), Ixx Iyy Izz Ixy Ixz Iyz
@@ -80,6 +83,9 @@ class Stream:
         return (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)).reshape(size)
 
 
+REVOLUTE, PRISMATIC, FIXED = 0, 1, 2
+
+
 @dataclasses.dataclass
 class Robot:
     name: str
@@ -88,10 +94,21 @@ class Robot:
     xtree: np.ndarray
     inertia: np.ndarray
     gravity: np.ndarray
+    jtype: np.ndarray | None = None   # per body: REVOLUTE, PRISMATIC or FIXED (None: all revolute)
 
     @property
     def n(self) -> int:
+        """Bodies (equal to the degrees of freedom when no joint is fixed)."""
         return int(self.parent.shape[0])
+
+    @property
+    def nd(self) -> int:
+        """Degrees of freedom: the moving (non-fixed) joints."""
+        return self.n if self.jtype is None else int(np.count_nonzero(self.jtype != FIXED))
+
+    def jtypes(self) -> np.ndarray:
+        jt = np.zeros(self.n, dtype=np.int32) if self.jtype is None else self.jtype
+        return np.ascontiguousarray(jt, dtype=np.int32)
 
     def arrays(self):
         return (np.ascontiguousarray(self.parent, dtype=np.int32),
@@ -109,7 +126,8 @@ class Robot:
         par = np.array([-1 if self.parent[p] < 0 else inv[self.parent[p]] for p in perm],
                        dtype=np.int32)
         return Robot(self.name + "-perm", par, self.axis[perm].copy(), self.xtree[perm].copy(),
-                     self.inertia[perm].copy(), self.gravity.copy())
+                     self.inertia[perm].copy(), self.gravity.copy(),
+                     None if self.jtype is None else self.jtype[perm].copy())
 
 
 _AX = {"x": (1.0, 0.0, 0.0), "y": (0.0, 1.0, 0.0), "z": (0.0, 0.0, 1.0)}
@@ -249,6 +267,70 @@ def random_tree(n: int, seed: int, general: bool = True, max_children: int = 3) 
         E = None
     offsets = [tuple(s.uniform(-0.3, 0.3, 3)) for _ in range(n)]
     return _assemble(f"rand{n}-{seed}", parent, axes, offsets, s, 1.0, 4.0, E=E)
+
+
+def random_mixed(n: int, seed: int, p_prismatic: float = 0.3, p_fixed: float = 0.2,
+                 max_children: int = 3) -> Robot:
+    """random_tree(n, seed) with a joint type drawn per body: fixed with
+    probability p_fixed, prismatic with p_prismatic, else revolute (at least
+    one joint moves)."""
+    r = random_tree(n, seed, general=True, max_children=max_children)
+    u = Stream(stream_seed(20_000 + n, f"random_mixed/{seed}")).unit(n)
+    jt = np.where(u < p_fixed, FIXED, np.where(u < p_fixed + p_prismatic, PRISMATIC, REVOLUTE))
+    jt = jt.astype(np.int32)
+    if np.all(jt == FIXED):
+        jt[-1] = REVOLUTE
+    return dataclasses.replace(r, name=f"mixed{n}-{seed}", jtype=jt)
+
+
+def chain7_tool(workload: int = 1) -> Robot:
+    """The 7-DoF chain with a fixed tool body after joint 7 (offset (0,0,0.1),
+    rotated by rpy (0.3,-0.2,0.5)) and a fixed sensor body between joints 3 and 4
+    (joint 4 then hangs from the sensor): 9 bodies, 7 degrees of freedom."""
+    base = chain7(workload)
+    s_in = Stream(stream_seed(workload, "chain7_tool/inertia"))
+    body = list(range(7))
+    parent, axis, xtree, inertia, jt = [], [], [], [], []
+    for i in body:
+        if i == 3:                                  # sensor: fixed, hangs from body 2
+            parent.append(2)
+            axis.append((0.0, 0.0, 1.0))
+            xtree.append(_xtree(np.eye(3), (0.0, 0.0, 0.05)))
+            inertia.append(_link_inertia(s_in, 0.2, 0.5))
+            jt.append(FIXED)
+        parent.append(-1 if i == 0 else (len(parent) - 1))
+        axis.append(tuple(base.axis[i]))
+        xtree.append(base.xtree[i])
+        inertia.append(base.inertia[i])
+        jt.append(REVOLUTE)
+    parent.append(len(parent) - 1)                  # tool
+    axis.append((0.0, 0.0, 1.0))
+    xtree.append(_xtree(_rpy_E(0.3, -0.2, 0.5), (0.0, 0.0, 0.1)))
+    inertia.append(_link_inertia(s_in, 0.3, 1.0))
+    jt.append(FIXED)
+    return Robot("chain7_tool", np.asarray(parent, dtype=np.int32), np.asarray(axis, dtype=np.float64),
+                 np.stack(xtree), np.stack(inertia), base.gravity.copy(), np.asarray(jt, dtype=np.int32))
+
+
+def slider(m: float = 1.7, axis=(0.0, 0.0, 1.0), com=(0.05, -0.02, 0.1)) -> Robot:
+    """Single prismatic joint at the base with unit axis `axis`, mass m with its
+    COM at `com` and a small rotational inertia; gravity -z."""
+    a = np.asarray(axis, dtype=np.float64)
+    return Robot("slider", np.array([-1], dtype=np.int32), (a / np.linalg.norm(a))[None, :],
+                 _xtree(np.eye(3), (0.1, 0.2, 0.3))[None, :],
+                 np.array([[m, *com, 0.02, 0.03, 0.04, 0.001, 0.002, 0.003]]),
+                 np.array([0.0, 0.0, -G_STD]), np.array([PRISMATIC], dtype=np.int32))
+
+
+def cartpole(mc: float = 1.3, mp: float = 0.4, l: float = 0.6) -> Robot:
+    """Cart on a prismatic joint along x (mass mc at its origin, no rotational
+    inertia) carrying a pole on a revolute joint about y: a point mass mp at
+    (0, 0, l) in the pole frame. Gravity -z."""
+    return Robot("cartpole", np.array([-1, 0], dtype=np.int32),
+                 np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]),
+                 np.stack([_xtree(np.eye(3), (0.0, 0.0, 0.0))] * 2),
+                 np.array([[mc, 0, 0, 0, 0, 0, 0, 0, 0, 0], [mp, 0, 0, l, 0, 0, 0, 0, 0, 0]], dtype=np.float64),
+                 np.array([0.0, 0.0, -G_STD]), np.array([PRISMATIC, REVOLUTE], dtype=np.int32))
 
 
 def pendulum(m: float = 2.0, l: float = 0.5) -> Robot:

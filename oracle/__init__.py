@@ -14,7 +14,14 @@ itself: the closed-form single pendulum and acrobot, a Lagrangian (energy /
 Jacobian) formulation of M, G and C written independently with homogeneous
 transforms, invariants (M = M^T > 0, M M^-1 = I, RNEA(FD) = tau, qd-linearity and
 Euler homogeneity of dID/dqd), complex-step and central finite differences, and
-sibling-permutation equivariance. No function is left unpinned.
+sibling-permutation equivariance. Prismatic and fixed joints (in
+tests/test_oracle_joint_types.py) are pinned by the closed-form slider and
+cart-pole, the Lagrangian formulation on random trees of mixed joint types,
+complex-step derivatives, and fixed bodies lumped into their parents by hand.
+No function is left unpinned.
+
+Joint arrays (q, qd, qdd, tau and the rows and columns of M, M^-1 and the
+Jacobians) hold the moving joints only (``robot.nd`` of them), in body order.
 """
 from __future__ import annotations
 
@@ -54,7 +61,7 @@ def _load():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
-            model = [_I, _P, _P, _P, _P, _P]
+            model = [_I, _P, _P, _P, _P, _P, _P]
             sig = {
                 "oracle_rnea": model + [_I, _P, _P, _P, _P, _I],
                 "oracle_rnea_bodies": model + [_I, _P, _P, _P, _P, _P, _P, _P],
@@ -91,13 +98,14 @@ def _ptr(a):
 
 def _model_args(robot):
     parent, axis, xtree, inertia, gravity = robot.arrays()
-    keep = (parent, axis, xtree, inertia, gravity)
+    keep = (parent, robot.jtypes(), axis, xtree, inertia, gravity)
     return keep, [robot.n] + [_ptr(a) for a in keep]
 
 
 def _check(code, what):
     if code == 1:
-        raise OracleError(f"{what}: invalid model (parent[i] must satisfy -1 <= parent[i] < i)")
+        raise OracleError(f"{what}: invalid model (parent[i] must satisfy -1 <= parent[i] < i, "
+                          "joint types 0..2, at least one moving joint)")
     if code == 2:
         raise OracleError(f"{what}: mass matrix not positive definite")
     if code != 0:
@@ -105,7 +113,7 @@ def _check(code, what):
 
 
 def _states(robot, *xs):
-    n = robot.n
+    n = robot.nd
     out = [_f64(x).reshape(-1, n) for x in xs]
     N = out[0].shape[0]
     for x in out:
@@ -124,7 +132,7 @@ def rnea(robot, q, qd, qdd, nthreads=1):
 
 
 def rnea_bodies(robot, q, qd, qdd):
-    """Per-body v, a, f (own), F (accumulated), each [N, n, 6]."""
+    """Per-body v, a, f (own), F (accumulated), each [N, bodies, 6]."""
     N, (q, qd, qdd) = _states(robot, q, qd, qdd)
     outs = [np.empty((N, robot.n, 6)) for _ in range(4)]
     keep, margs = _model_args(robot)
@@ -136,7 +144,7 @@ def rnea_bodies(robot, q, qd, qdd):
 def mass_matrix(robot, q, nthreads=1):
     """M(q) by CRBA, [N, n, n]."""
     N, (q,) = _states(robot, q)
-    M = np.empty((N, robot.n, robot.n))
+    M = np.empty((N, robot.nd, robot.nd))
     keep, margs = _model_args(robot)
     _check(_load().oracle_mass_matrix(*margs, N, _ptr(q), _ptr(M), nthreads), "mass_matrix")
     return M
@@ -145,7 +153,7 @@ def mass_matrix(robot, q, nthreads=1):
 def minv(robot, q, nthreads=1):
     """M(q)^-1 by CRBA + Cholesky, full symmetric [N, n, n]."""
     N, (q,) = _states(robot, q)
-    Mi = np.empty((N, robot.n, robot.n))
+    Mi = np.empty((N, robot.nd, robot.nd))
     keep, margs = _model_args(robot)
     _check(_load().oracle_minv(*margs, N, _ptr(q), _ptr(Mi), nthreads), "minv")
     return Mi
@@ -163,7 +171,7 @@ def fd(robot, q, qd, tau, nthreads=1):
 def grad_rnea(robot, q, qd, qdd, nthreads=1):
     """(dtau/dq, dtau/dqd), each [N, n, n] (row = tau_i, column = joint j)."""
     N, (q, qd, qdd) = _states(robot, q, qd, qdd)
-    dq = np.empty((N, robot.n, robot.n))
+    dq = np.empty((N, robot.nd, robot.nd))
     dqd = np.empty_like(dq)
     keep, margs = _model_args(robot)
     _check(_load().oracle_grad_rnea(*margs, N, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(dq), _ptr(dqd),
@@ -174,7 +182,7 @@ def grad_rnea(robot, q, qd, qdd, nthreads=1):
 def grad_fd(robot, q, qd, tau, nthreads=1, with_qdd=False):
     """J = [dqdd/dq | dqdd/dqd], [N, n, 2n]; optionally also qdd [N, n]."""
     N, (q, qd, tau) = _states(robot, q, qd, tau)
-    J = np.empty((N, robot.n, 2 * robot.n))
+    J = np.empty((N, robot.nd, 2 * robot.nd))
     qdd = np.empty_like(q)
     keep, margs = _model_args(robot)
     _check(_load().oracle_grad_fd(*margs, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(J), _ptr(qdd),
@@ -185,7 +193,7 @@ def grad_fd(robot, q, qd, tau, nthreads=1, with_qdd=False):
 def fd_complex_step(robot, q, qd, tau, h=1e-30, nthreads=1):
     """[dFD/dq | dFD/dqd] by complex-step differentiation, [N, n, 2n]."""
     N, (q, qd, tau) = _states(robot, q, qd, tau)
-    J = np.empty((N, robot.n, 2 * robot.n))
+    J = np.empty((N, robot.nd, 2 * robot.nd))
     keep, margs = _model_args(robot)
     _check(_load().oracle_fd_complex_step(*margs, N, _ptr(q), _ptr(qd), _ptr(tau), h, _ptr(J),
                                           nthreads), "fd_complex_step")
@@ -195,7 +203,7 @@ def fd_complex_step(robot, q, qd, tau, h=1e-30, nthreads=1):
 def rnea_complex_step(robot, q, qd, qdd, h=1e-30, nthreads=1):
     """(dID/dq, dID/dqd) by complex-step differentiation, each [N, n, n]."""
     N, (q, qd, qdd) = _states(robot, q, qd, qdd)
-    dq = np.empty((N, robot.n, robot.n))
+    dq = np.empty((N, robot.nd, robot.nd))
     dqd = np.empty_like(dq)
     keep, margs = _model_args(robot)
     _check(_load().oracle_rnea_complex_step(*margs, N, _ptr(q), _ptr(qd), _ptr(qdd), h, _ptr(dq),
@@ -209,8 +217,8 @@ def fd_vjp(robot, q, qd, tau, gbar, nthreads=1):
     grad_fd (dqdd/dtau = M^-1, symmetric)."""
     J = grad_fd(robot, q, qd, tau, nthreads)
     Mi = minv(robot, q, nthreads)
-    g = _f64(gbar).reshape(-1, robot.n)
-    n = robot.n
+    g = _f64(gbar).reshape(-1, robot.nd)
+    n = robot.nd
     dq = np.einsum("kij,ki->kj", J[:, :, :n], g)
     dqd = np.einsum("kij,ki->kj", J[:, :, n:], g)
     dtau = np.einsum("kij,ki->kj", Mi, g)

@@ -27,8 +27,12 @@
 //  * The backward-pass term X^T (S_i x* f_i) uses the accumulated force f_i
 //    (own plus children) and applies only for u = q_i.
 //  * Gravity enters as a fictitious base acceleration a_0 = -g.
-//  * iX_lambda = X_J(q_i) X_T,i with X_J a coordinate rotation by q_i about
-//    the unit axis a_i, S_i = [a_i; 0].
+//  * iX_lambda = X_J(q_i) X_T,i. Joint types (Sec. IV-A lists revolute,
+//    prismatic and fixed joints among the supported URDF joints): revolute X_J
+//    is a coordinate rotation by q_i about the unit axis a_i, S_i = [a_i; 0];
+//    prismatic X_J is a translation of the child origin by q_i a_i,
+//    S_i = [0; a_i]; a fixed joint has X_J = 1 and no degree of freedom. Joint
+//    arrays (q, qd, qdd, tau) hold the moving joints only, in body order.
 #include <array>
 #include <cmath>
 #include <complex>
@@ -149,23 +153,36 @@ M6<double> spatial_inertia(const double* p) {
   return I;
 }
 
+enum { REVOLUTE = 0, PRISMATIC = 1, FIXED = 2 };
+
 struct Model {
-  int n = 0;
+  int n = 0;                    // bodies
+  int nd = 0;                   // degrees of freedom (moving joints)
   std::vector<int> parent;
+  std::vector<int> jtype;       // REVOLUTE, PRISMATIC or FIXED
+  std::vector<int> dof;         // body -> joint index, -1 for a fixed joint
   std::vector<V3<double>> axis;
   std::vector<M6<double>> XT;   // fixed transforms X_T,i
   std::vector<M6<double>> I;    // spatial inertias
   V6<double> a0;                // base acceleration -g
 };
 
-bool build_model(int n, const int* parent, const double* axis, const double* xtree,
+bool build_model(int n, const int* parent, const int* jtype, const double* axis, const double* xtree,
                  const double* inertia, const double* gravity, Model& m) {
   if (n <= 0) return false;
   m.n = n;
   m.parent.assign(parent, parent + n);
+  m.jtype.assign(n, REVOLUTE);
+  m.dof.assign(n, -1);
+  m.nd = 0;
   m.axis.resize(n); m.XT.resize(n); m.I.resize(n);
   for (int i = 0; i < n; ++i) {
     if (parent[i] < -1 || parent[i] >= i) return false;   // Sec. III-B: lambda_i < i
+    if (jtype) {
+      if (jtype[i] < REVOLUTE || jtype[i] > FIXED) return false;
+      m.jtype[i] = jtype[i];
+    }
+    if (m.jtype[i] != FIXED) m.dof[i] = m.nd++;
     m.axis[i] = {axis[3 * i], axis[3 * i + 1], axis[3 * i + 2]};
     M3<double> E; V3<double> r;
     for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) E[a][b] = xtree[12 * i + 3 * a + b];
@@ -174,7 +191,7 @@ bool build_model(int n, const int* parent, const double* axis, const double* xtr
     m.I[i] = spatial_inertia(inertia + 10 * i);
   }
   m.a0 = {0, 0, 0, -gravity[0], -gravity[1], -gravity[2]};
-  return true;
+  return m.nd > 0;
 }
 
 template <class T> M6<T> cast66(const M6<double>& A) {
@@ -183,15 +200,28 @@ template <class T> M6<T> cast66(const M6<double>& A) {
 template <class T> V6<T> cast6(const V6<double>& a) {
   V6<T> b; for (int i = 0; i < 6; ++i) b[i] = T(a[i]); return b;
 }
+// S_i: [a; 0] for a revolute joint, [0; a] for a prismatic one (unused for a
+// fixed joint, which has no degree of freedom).
 template <class T> V6<T> motion_subspace(const Model& m, int i) {
-  return {T(m.axis[i][0]), T(m.axis[i][1]), T(m.axis[i][2]), T(0), T(0), T(0)};
+  const T a0 = T(m.axis[i][0]), a1 = T(m.axis[i][1]), a2 = T(m.axis[i][2]);
+  if (m.jtype[i] == PRISMATIC) return {T(0), T(0), T(0), a0, a1, a2};
+  return {a0, a1, a2, T(0), T(0), T(0)};
 }
 
 // iX_lambda_i = X_J(q_i) X_T,i  (Sec. III-B).
 template <class T> std::vector<M6<T>> transforms(const Model& m, const T* q) {
   std::vector<M6<T>> X(m.n);
+  const M3<T> I3 = {{{T(1), T(0), T(0)}, {T(0), T(1), T(0)}, {T(0), T(0), T(1)}}};
   for (int i = 0; i < m.n; ++i) {
-    M6<T> XJ = plucker(joint_E<T>(m.axis[i], q[i]), V3<T>{T(0), T(0), T(0)});
+    M6<T> XJ;
+    if (m.jtype[i] == REVOLUTE) {
+      XJ = plucker(joint_E<T>(m.axis[i], q[m.dof[i]]), V3<T>{T(0), T(0), T(0)});
+    } else if (m.jtype[i] == PRISMATIC) {
+      const T d = q[m.dof[i]];
+      XJ = plucker(I3, V3<T>{d * T(m.axis[i][0]), d * T(m.axis[i][1]), d * T(m.axis[i][2])});
+    } else {
+      XJ = plucker(I3, V3<T>{T(0), T(0), T(0)});
+    }
     X[i] = mul(XJ, cast66<T>(m.XT[i]));
   }
   return X;
@@ -208,23 +238,29 @@ template <class T> struct RneaOut {
 //          a_i = X a_lambda + S qdd_i + v_i x S qd_i,  (a_base = -g, v_base = 0)
 //          f_i = I a_i + v_i x* I v_i;
 // backward tau_i = S^T F_i,  F_lambda += X^T F_i.
+// (A fixed joint contributes no S terms and no tau entry.)
 template <class T> RneaOut<T> rnea(const Model& m, const T* q, const T* qd, const T* qdd) {
   RneaOut<T> o;
   o.X = transforms<T>(m, q);
-  o.v.resize(m.n); o.a.resize(m.n); o.f.resize(m.n); o.F.resize(m.n); o.tau.resize(m.n);
+  o.v.resize(m.n); o.a.resize(m.n); o.f.resize(m.n); o.F.resize(m.n); o.tau.resize(m.nd);
   for (int i = 0; i < m.n; ++i) {
     int p = m.parent[i];
-    V6<T> S = motion_subspace<T>(m, i);
     V6<T> vp = p < 0 ? zero6<T>() : o.v[p];
     V6<T> ap = p < 0 ? cast6<T>(m.a0) : o.a[p];
-    o.v[i] = add(mul(o.X[i], vp), scale(S, qd[i]));
-    o.a[i] = add(add(mul(o.X[i], ap), scale(S, qdd[i])), mul(crm(o.v[i]), scale(S, qd[i])));
+    o.v[i] = mul(o.X[i], vp);
+    o.a[i] = mul(o.X[i], ap);
+    if (m.dof[i] >= 0) {
+      V6<T> S = motion_subspace<T>(m, i);
+      const int d = m.dof[i];
+      o.v[i] = add(o.v[i], scale(S, qd[d]));
+      o.a[i] = add(add(o.a[i], scale(S, qdd[d])), mul(crm(o.v[i]), scale(S, qd[d])));
+    }
     M6<T> I = cast66<T>(m.I[i]);
     o.f[i] = add(mul(I, o.a[i]), mul(crf(o.v[i]), mul(I, o.v[i])));
     o.F[i] = o.f[i];
   }
   for (int i = m.n - 1; i >= 0; --i) {
-    o.tau[i] = dot(motion_subspace<T>(m, i), o.F[i]);
+    if (m.dof[i] >= 0) o.tau[m.dof[i]] = dot(motion_subspace<T>(m, i), o.F[i]);
     int p = m.parent[i];
     if (p >= 0) o.F[p] = add(o.F[p], mulT(o.X[i], o.F[i]));
   }
@@ -242,17 +278,22 @@ template <class T> std::vector<T> crba(const Model& m, const T* q) {
     int p = m.parent[i];
     if (p >= 0) Ic[p] = add(Ic[p], mul(transpose(X[i]), mul(Ic[i], X[i])));
   }
-  std::vector<T> M(m.n * m.n, T(0));
+  const int nd = m.nd;
+  std::vector<T> M(nd * nd, T(0));
   for (int i = 0; i < m.n; ++i) {
+    if (m.dof[i] < 0) continue;
+    const int di = m.dof[i];
     V6<T> F = mul(Ic[i], motion_subspace<T>(m, i));
-    M[i * m.n + i] = dot(motion_subspace<T>(m, i), F);
+    M[di * nd + di] = dot(motion_subspace<T>(m, i), F);
     int j = i;
     while (m.parent[j] >= 0) {
       F = mulT(X[j], F);
       j = m.parent[j];
+      if (m.dof[j] < 0) continue;
+      const int dj = m.dof[j];
       T Mij = dot(motion_subspace<T>(m, j), F);
-      M[i * m.n + j] = Mij;
-      M[j * m.n + i] = Mij;
+      M[di * nd + dj] = Mij;
+      M[dj * nd + di] = Mij;
     }
   }
   return M;
@@ -295,64 +336,71 @@ template <class T> void chol_solve(int n, const std::vector<T>& L, T* x) {
 
 // M^-1 = L^-T L^-1, computed column by column as the solution of M x = e_j.
 template <class T> bool minv(const Model& m, const T* q, std::vector<T>& Mi) {
+  const int nd = m.nd;
   std::vector<T> M = crba<T>(m, q), L;
-  if (!cholesky<T>(m.n, M, L)) return false;
-  Mi.assign(m.n * m.n, T(0));
-  std::vector<T> x(m.n);
-  for (int j = 0; j < m.n; ++j) {
-    for (int i = 0; i < m.n; ++i) x[i] = T(i == j ? 1 : 0);
-    chol_solve<T>(m.n, L, x.data());
-    for (int i = 0; i < m.n; ++i) Mi[i * m.n + j] = x[i];
+  if (!cholesky<T>(nd, M, L)) return false;
+  Mi.assign(nd * nd, T(0));
+  std::vector<T> x(nd);
+  for (int j = 0; j < nd; ++j) {
+    for (int i = 0; i < nd; ++i) x[i] = T(i == j ? 1 : 0);
+    chol_solve<T>(nd, L, x.data());
+    for (int i = 0; i < nd; ++i) Mi[i * nd + j] = x[i];
   }
   return true;
 }
 
 // FD: qdd = M^-1 (tau - RNEA(q, qd, 0)) (Sec. IV-B), by a Cholesky solve.
 template <class T> bool fd(const Model& m, const T* q, const T* qd, const T* tau, T* qdd) {
-  std::vector<T> zero(m.n, T(0));
+  std::vector<T> zero(m.nd, T(0));
   RneaOut<T> r = rnea<T>(m, q, qd, zero.data());
   std::vector<T> M = crba<T>(m, q), L;
-  if (!cholesky<T>(m.n, M, L)) return false;
-  for (int i = 0; i < m.n; ++i) qdd[i] = tau[i] - r.tau[i];
-  chol_solve<T>(m.n, L, qdd);
+  if (!cholesky<T>(m.nd, M, L)) return false;
+  for (int i = 0; i < m.nd; ++i) qdd[i] = tau[i] - r.tau[i];
+  chol_solve<T>(m.nd, L, qdd);
   return true;
 }
 
 // Analytical RNEA derivatives, one column per joint (Alg. 1 forward pass and
-// its backward pass), at (q, qd, qdd). Outputs row-major n x n:
-// dtau_dq[i*n + j] = d tau_i / d q_j, likewise for qd.
+// its backward pass), at (q, qd, qdd). Outputs row-major nd x nd:
+// dtau_dq[i*nd + j] = d tau_i / d q_j, likewise for qd. Column j belongs to the
+// body bj whose joint is j; a fixed joint passes derivatives through its
+// transform and has no case terms, row or column.
 template <class T> void grad_rnea(const Model& m, const T* q, const T* qd, const T* qdd,
                                   T* dtau_dq, T* dtau_dqd) {
-  const int n = m.n;
+  const int n = m.n, nd = m.nd;
   RneaOut<T> r = rnea<T>(m, q, qd, qdd);
   std::vector<V6<T>> dv(n), da(n), df(n);
   for (int u = 0; u < 2; ++u) {                 // u = 0: d/dq, u = 1: d/dqd
     T* out = u == 0 ? dtau_dq : dtau_dqd;
-    for (int j = 0; j < n; ++j) {
+    for (int bj = 0; bj < n; ++bj) {
+      if (m.dof[bj] < 0) continue;
+      const int j = m.dof[bj];
       // forward pass over frames i = 1..n
       for (int i = 0; i < n; ++i) {
         int p = m.parent[i];
-        V6<T> S = motion_subspace<T>(m, i);
         V6<T> dvp = p < 0 ? zero6<T>() : dv[p];
         V6<T> dap = p < 0 ? zero6<T>() : da[p];
         V6<T> vp = p < 0 ? zero6<T>() : r.v[p];
         V6<T> ap = p < 0 ? cast6<T>(m.a0) : r.a[p];
         dv[i] = mul(r.X[i], dvp);
-        if (i == j) dv[i] = add(dv[i], u == 0 ? mul(crm(mul(r.X[i], vp)), S) : S);
-        da[i] = add(mul(r.X[i], dap), mul(crm(dv[i]), scale(S, qd[i])));
-        if (i == j) da[i] = add(da[i], u == 0 ? mul(crm(mul(r.X[i], ap)), S) : mul(crm(r.v[i]), S));
+        da[i] = mul(r.X[i], dap);
+        if (m.dof[i] >= 0) {
+          V6<T> S = motion_subspace<T>(m, i);
+          if (i == bj) dv[i] = add(dv[i], u == 0 ? mul(crm(mul(r.X[i], vp)), S) : S);
+          da[i] = add(da[i], mul(crm(dv[i]), scale(S, qd[m.dof[i]])));
+          if (i == bj) da[i] = add(da[i], u == 0 ? mul(crm(mul(r.X[i], ap)), S) : mul(crm(r.v[i]), S));
+        }
         M6<T> I = cast66<T>(m.I[i]);
         df[i] = add(add(mul(I, da[i]), mul(crf(dv[i]), mul(I, r.v[i]))),
                     mul(crf(r.v[i]), mul(I, dv[i])));
       }
       // backward pass over frames i = n..1
       for (int i = n - 1; i >= 0; --i) {
-        V6<T> S = motion_subspace<T>(m, i);
-        out[i * n + j] = dot(S, df[i]);
+        if (m.dof[i] >= 0) out[m.dof[i] * nd + j] = dot(motion_subspace<T>(m, i), df[i]);
         int p = m.parent[i];
         if (p >= 0) {
           V6<T> up = mulT(r.X[i], df[i]);
-          if (u == 0 && i == j) up = add(up, mulT(r.X[i], mul(crf(S), r.F[i])));
+          if (u == 0 && i == bj) up = add(up, mulT(r.X[i], mul(crf(motion_subspace<T>(m, i)), r.F[i])));
           df[p] = add(df[p], up);
         }
       }
@@ -363,7 +411,7 @@ template <class T> void grad_rnea(const Model& m, const T* q, const T* qd, const
 // dFD: [dqdd/dq | dqdd/dqd] = -M^-1 [dID/dq | dID/dqd] at qdd = FD(q, qd, tau)
 // (Sec. IV-B). J is row-major n x 2n.
 template <class T> bool grad_fd(const Model& m, const T* q, const T* qd, const T* tau, T* J, T* qdd_out) {
-  const int n = m.n;
+  const int n = m.nd;
   std::vector<T> qdd(n);
   if (!fd<T>(m, q, qd, tau, qdd.data())) return false;
   std::vector<T> dq(n * n), dqd(n * n), Mi;
@@ -399,9 +447,12 @@ using C = std::complex<double>;
 
 }  // namespace
 
-#define ORACLE_MODEL_ARGS int n, const int* parent, const double* axis, const double* xtree, \
-                          const double* inertia, const double* gravity
-#define ORACLE_BUILD Model m; if (!build_model(n, parent, axis, xtree, inertia, gravity, m)) return 1;
+// n is the number of bodies; jtype may be NULL (all revolute). Joint arrays
+// have nd = (number of non-fixed joints) entries per knot point.
+#define ORACLE_MODEL_ARGS int nb, const int* parent, const int* jtype, const double* axis, \
+                          const double* xtree, const double* inertia, const double* gravity
+#define ORACLE_BUILD Model m; if (!build_model(nb, parent, jtype, axis, xtree, inertia, gravity, m)) return 1; \
+                     const int n = m.nd;
 
 extern "C" {
 
@@ -417,15 +468,15 @@ int oracle_rnea(ORACLE_MODEL_ARGS, int N, const double* q, const double* qd, con
   });
 }
 
-// Per-body RNEA intermediates v, a, f (own) and F (accumulated), [N][n][6] each.
+// Per-body RNEA intermediates v, a, f (own) and F (accumulated), [N][nb][6].
 int oracle_rnea_bodies(ORACLE_MODEL_ARGS, int N, const double* q, const double* qd, const double* qdd,
                        double* v, double* a, double* f, double* F) {
   ORACLE_BUILD
   for (int k = 0; k < N; ++k) {
     RneaOut<double> r = rnea<double>(m, q + k * n, qd + k * n, qdd + k * n);
-    for (int i = 0; i < n; ++i) for (int c = 0; c < 6; ++c) {
-      v[(k * n + i) * 6 + c] = r.v[i][c]; a[(k * n + i) * 6 + c] = r.a[i][c];
-      f[(k * n + i) * 6 + c] = r.f[i][c]; F[(k * n + i) * 6 + c] = r.F[i][c];
+    for (int i = 0; i < nb; ++i) for (int c = 0; c < 6; ++c) {
+      v[(k * nb + i) * 6 + c] = r.v[i][c]; a[(k * nb + i) * 6 + c] = r.a[i][c];
+      f[(k * nb + i) * 6 + c] = r.f[i][c]; F[(k * nb + i) * 6 + c] = r.F[i][c];
     }
   }
   return 0;

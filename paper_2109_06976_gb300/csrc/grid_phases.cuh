@@ -532,9 +532,7 @@ __device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
     if (l < 6) {
       FA[8 * k + l] = fk;
       if (p >= 0) {
-        S E[12];
-        ld12(W + L.X + 12 * k, E);
-        const S cl = xt_mul_c(E, E + 9, F, l);
+        const S cl = xt_mul_c(W + L.X + 12 * k, F, l);
         if (p == k - 1) carry = cl;
         else FSL[8 * tp.branch(p) + l] += cl;
       }
@@ -837,10 +835,8 @@ __device__ void ph_vjp_sweep(const Ctx<S, Tp>& c) {
       W[U + L.DQD + k] = -gqd;
     }
     if (p >= 0 && l < 6) {
-      S E[12];
-      ld12(W + L.X + 12 * k, E);
-      const S xa = xt_mul_c(E, E + 9, A, l);
-      const S xv = xt_mul_c(E, E + 9, V, l);
+      const S xa = xt_mul_c(W + L.X + 12 * k, A, l);
+      const S xv = xt_mul_c(W + L.X + 12 * k, V, l);
       if (p == k - 1) { ca = xa; cv = xv; }
       else { SA[8 * tp.branch(p) + l] += xa; SV[8 * tp.branch(p) + l] += xv; }
     }

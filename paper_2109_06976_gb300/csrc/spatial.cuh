@@ -86,17 +86,20 @@ __device__ __forceinline__ S x_mul_c(const S* E, const S* r, const S* m, int c) 
   return E[3 * k] * t0 + E[3 * k + 1] * t1 + E[3 * k + 2] * t2;
 }
 
-// Component c of X^T f.
+// Component c of X^T f = [E^T f_ang + r x E^T f_lin; E^T f_lin], with the
+// transform record Er = E(9) r(3) read from memory: a lane-dependent c then
+// indexes shared memory instead of forcing a local-memory copy of E.
 template <class S>
-__device__ __forceinline__ S xt_mul_c(const S* E, const S* r, const S* f, int c) {
-  S g0 = E[0] * f[3] + E[3] * f[4] + E[6] * f[5];
-  S g1 = E[1] * f[3] + E[4] * f[4] + E[7] * f[5];
-  S g2 = E[2] * f[3] + E[5] * f[4] + E[8] * f[5];
-  if (c >= 3) return c == 3 ? g0 : (c == 4 ? g1 : g2);
-  S n = E[c] * f[0] + E[3 + c] * f[1] + E[6 + c] * f[2];
+__device__ __forceinline__ S xt_mul_c(const S* Er, const S* f, int c) {
+  if (c >= 3) {
+    const int k = c - 3;
+    return Er[k] * f[3] + Er[3 + k] * f[4] + Er[6 + k] * f[5];
+  }
   const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
-  const S g[3] = {g0, g1, g2};
-  return n + (r[c1] * g[c2] - r[c2] * g[c1]);
+  const S g1 = Er[c1] * f[3] + Er[3 + c1] * f[4] + Er[6 + c1] * f[5];
+  const S g2 = Er[c2] * f[3] + Er[3 + c2] * f[4] + Er[6 + c2] * f[5];
+  const S nc = Er[c] * f[0] + Er[3 + c] * f[1] + Er[6 + c] * f[2];
+  return nc + (Er[9 + c1] * g2 - Er[9 + c2] * g1);
 }
 
 // Component c of I m.

@@ -4,15 +4,35 @@ Written with world-frame homogeneous kinematics and geometric Jacobians
 (textbook manipulator dynamics), sharing nothing with the spatial-algebra
 oracle: no Plucker transforms, no cross-product operators, no recursions.
 
-  R_i = R_parent E_T,i^T Rot(a_i, q_i),   p_i = p_parent + R_parent r_i
+  revolute:  R_i = R_parent E_T,i^T Rot(a_i, q_i),  p_i = p_parent + R_parent r_i
+  prismatic: R_i = R_parent E_T,i^T,  p_i = p_parent + R_parent r_i + R_i a_i q_i
+  fixed:     R_i = R_parent E_T,i^T,  p_i = p_parent + R_parent r_i   (no joint variable)
   x_i = p_i + R_i c_i                     (COM of link i)
-  Jv_i[:, j] = z_j x (x_i - p_j),  Jw_i[:, j] = z_j  for j on the path to i
+  for the moving joint j of a body on the path to i, with z_j = R_j a_j:
+    revolute  Jv_i[:, j] = z_j x (x_i - p_j),  Jw_i[:, j] = z_j
+    prismatic Jv_i[:, j] = z_j,                Jw_i[:, j] = 0
   M = sum_i m_i Jv_i^T Jv_i + Jw_i^T R_i Ic_i R_i^T Jw_i
   G = -sum_i m_i Jv_i^T g
   C(q, qd) qd = Mdot qd - 1/2 d/dq (qd^T M qd)   (central differences in q)
   tau = M qdd + C qd + G                  (Eq. (1) with B = I, F = 0)
 """
 import numpy as np
+
+REVOLUTE, PRISMATIC, FIXED = 0, 1, 2
+
+
+def _jt(robot):
+    return np.zeros(robot.n, dtype=int) if robot.jtype is None else np.asarray(robot.jtype)
+
+
+def _dofs(robot):
+    """body -> joint-variable index (-1 for a fixed joint)."""
+    jt = _jt(robot)
+    out, d = [], 0
+    for i in range(robot.n):
+        out.append(-1 if jt[i] == FIXED else d)
+        d += jt[i] != FIXED
+    return out
 
 
 def _rot(a, q):
@@ -23,6 +43,7 @@ def _rot(a, q):
 
 def kinematics(robot, q):
     n = robot.n
+    jt, dof = _jt(robot), _dofs(robot)
     R = [None] * n
     p = [None] * n
     for i in range(n):
@@ -32,8 +53,29 @@ def kinematics(robot, q):
         E = robot.xtree[i, :9].reshape(3, 3)
         r = robot.xtree[i, 9:]
         p[i] = pp + Rp @ r
-        R[i] = Rp @ E.T @ _rot(robot.axis[i], q[i])
+        R[i] = Rp @ E.T
+        if jt[i] == REVOLUTE:
+            R[i] = R[i] @ _rot(robot.axis[i], q[dof[i]])
+        elif jt[i] == PRISMATIC:
+            p[i] = p[i] + R[i] @ (np.asarray(robot.axis[i]) * q[dof[i]])
     return R, p
+
+
+def _jacobians(robot, R, p, i, x):
+    """Linear and angular Jacobians of the point x on body i, [3, nd] each."""
+    jt, dof = _jt(robot), _dofs(robot)
+    Jv = np.zeros((3, robot.nd))
+    Jw = np.zeros((3, robot.nd))
+    for j in _path(robot, i):
+        if jt[j] == FIXED:
+            continue
+        z = R[j] @ robot.axis[j]
+        if jt[j] == REVOLUTE:
+            Jv[:, dof[j]] = np.cross(z, x - p[j])
+            Jw[:, dof[j]] = z
+        else:
+            Jv[:, dof[j]] = z
+    return Jv, Jw
 
 
 def _path(robot, i):
@@ -45,41 +87,34 @@ def _path(robot, i):
 
 
 def mass_matrix(robot, q):
-    n = robot.n
+    nd = robot.nd
     R, p = kinematics(robot, q)
-    M = np.zeros((n, n))
-    for i in range(n):
+    M = np.zeros((nd, nd))
+    for i in range(robot.n):
         m = robot.inertia[i, 0]
         c = robot.inertia[i, 1:4]
         Ixx, Iyy, Izz, Ixy, Ixz, Iyz = robot.inertia[i, 4:]
         Ic = np.array([[Ixx, Ixy, Ixz], [Ixy, Iyy, Iyz], [Ixz, Iyz, Izz]])
         x = p[i] + R[i] @ c
-        Jv = np.zeros((3, n))
-        Jw = np.zeros((3, n))
-        for j in _path(robot, i):
-            z = R[j] @ robot.axis[j]
-            Jv[:, j] = np.cross(z, x - p[j])
-            Jw[:, j] = z
+        Jv, Jw = _jacobians(robot, R, p, i, x)
         M += m * Jv.T @ Jv + Jw.T @ (R[i] @ Ic @ R[i].T) @ Jw
     return M
 
 
 def gravity_torque(robot, q):
-    n = robot.n
     R, p = kinematics(robot, q)
-    G = np.zeros(n)
+    G = np.zeros(robot.nd)
     g = robot.gravity
-    for i in range(n):
+    for i in range(robot.n):
         m = robot.inertia[i, 0]
         x = p[i] + R[i] @ robot.inertia[i, 1:4]
-        for j in _path(robot, i):
-            z = R[j] @ robot.axis[j]
-            G[j] -= m * np.cross(z, x - p[j]) @ g
+        Jv, _ = _jacobians(robot, R, p, i, x)
+        G -= m * Jv.T @ g
     return G
 
 
 def inverse_dynamics(robot, q, qd, qdd, h=1e-6):
-    n = robot.n
+    n = robot.nd
     M = mass_matrix(robot, q)
     dM = []
     for k in range(n):
