@@ -56,8 +56,15 @@ typedef enum {
   GRID_FP64 = 2   /* the whole path in FP64 (the _f64 calls) */
 } grid_precision;
 
-/* Largest supported number of joints. */
+/* Largest supported number of moving joints (degrees of freedom). */
 #define GRID_MAX_DOF 32
+
+/* Joint types (Sec. IV-A lists revolute, prismatic and fixed joints). */
+typedef enum {
+  GRID_JOINT_REVOLUTE = 0,  /* rotation by q about the unit axis a: S = [a; 0] */
+  GRID_JOINT_PRISMATIC = 1, /* translation of the child origin by q a: S = [0; a] */
+  GRID_JOINT_FIXED = 2      /* no degree of freedom: merged into the parent at creation */
+} grid_joint_type;
 
 /*
  * grid_create -- build a device-resident robot model (Sec. III-B).
@@ -82,10 +89,32 @@ grid_status grid_create(int n, const int* parent, const double* axis, const doub
                         const double* inertia, const double* gravity, grid_precision prec,
                         grid_model** out);
 
+/*
+ * grid_create_ex -- grid_create with a joint type per body (Sec. IV-A: the
+ * library supports revolute, prismatic and fixed joints).
+ *   nb      number of bodies, 1 <= nb <= 256, at most GRID_MAX_DOF of them moving
+ *   jtype   [nb] grid_joint_type per body, or NULL for all revolute
+ *   parent, axis, X_tree, inertia, gravity, prec, out: as for grid_create, per
+ *           body (axis is ignored for a fixed joint; a fixed body may have zero mass)
+ * A prismatic joint translates the child origin by q a (X_J = X(1, q a),
+ * S = [0; a]). A fixed body is merged into its nearest moving ancestor: its
+ * spatial inertia is added to the ancestor's in the ancestor's frame and the
+ * bodies hanging from it take the composed fixed transform (a fixed body on the
+ * base contributes nothing). Every joint array of the compute calls (q, qd,
+ * qdd, tau, and the rows and columns of M^-1 and the Jacobians) then holds the
+ * moving joints only, in body order: grid_model_dof() of them.
+ * Errors: GRID_E_ARG for a joint type outside 0..2, GRID_E_TOPOLOGY when no
+ * joint moves or the limits are exceeded, GRID_E_NUMERIC for a non-unit axis of
+ * a moving joint or a non-positive mass after merging.
+ */
+grid_status grid_create_ex(int nb, const int* parent, const int* jtype, const double* axis,
+                           const double* X_tree, const double* inertia, const double* gravity,
+                           grid_precision prec, grid_model** out);
+
 /* grid_destroy -- free the model (synchronises the device first). NULL is a no-op. */
 grid_status grid_destroy(grid_model* model);
 
-/* grid_model_dof -- number of joints n of a model (0 for NULL). */
+/* grid_model_dof -- number of moving joints n of a model (0 for NULL). */
 int grid_model_dof(const grid_model* model);
 
 /*

@@ -42,26 +42,33 @@ def _np(a, dtype):
 class Model:
     """A robot model resident on the current CUDA device.
 
-    parent [n] (int, -1 = fixed base, parent[i] < i), axis [n, 3] unit joint
-    axes, xtree [n, 12] (E row-major then r), inertia [n, 10] (m, COM, Ic about
-    the COM: xx yy zz xy xz yz), gravity [3]. See include/grid.h.
+    Per body: parent [nb] (int, -1 = fixed base, parent[i] < i), axis [nb, 3]
+    unit joint axes, xtree [nb, 12] (E row-major then r), inertia [nb, 10] (m,
+    COM, Ic about the COM: xx yy zz xy xz yz), optional jtype [nb] (0 revolute,
+    1 prismatic, 2 fixed; None = all revolute); gravity [3]. Fixed bodies are
+    merged into their parents, so every state array has ``n`` = the number of
+    moving joints per knot point. See include/grid.h.
     """
 
-    def __init__(self, parent, axis, xtree, inertia, gravity=(0.0, 0.0, -9.81), precision="fp32"):
+    def __init__(self, parent, axis, xtree, inertia, gravity=(0.0, 0.0, -9.81), precision="fp32",
+                 jtype=None):
         lib = _native.load()
-        self._keep = (_np(parent, np.int32), _np(axis, np.float64), _np(xtree, np.float64),
-                      _np(inertia, np.float64), _np(gravity, np.float64))
-        self.n = int(self._keep[0].shape[0])
+        self._keep = (_np(parent, np.int32), None if jtype is None else _np(jtype, np.int32),
+                      _np(axis, np.float64), _np(xtree, np.float64), _np(inertia, np.float64),
+                      _np(gravity, np.float64))
+        nb = int(self._keep[0].shape[0])
         h = ctypes.c_void_p()
-        _native.check("grid_create", lib.grid_create(
-            self.n, *[a.ctypes.data_as(ctypes.c_void_p) for a in self._keep],
+        _native.check("grid_create_ex", lib.grid_create_ex(
+            nb, *[None if a is None else a.ctypes.data_as(ctypes.c_void_p) for a in self._keep],
             _PREC[precision], ctypes.byref(h)))
         self._h = h
+        self.n = int(lib.grid_model_dof(h))
         self.device = torch.cuda.current_device()
 
     @classmethod
     def from_robot(cls, robot, precision="fp32"):
-        return cls(robot.parent, robot.axis, robot.xtree, robot.inertia, robot.gravity, precision)
+        return cls(robot.parent, robot.axis, robot.xtree, robot.inertia, robot.gravity, precision,
+                   jtype=robot.jtype)
 
     @property
     def handle(self):

@@ -21,6 +21,7 @@ _P = ctypes.c_void_p
 # name -> argument types (every function returns grid_status)
 SIGNATURES = {
     "grid_create": [_I, _P, _P, _P, _P, _P, _I, ctypes.POINTER(_P)],
+    "grid_create_ex": [_I, _P, _P, _P, _P, _P, _P, _I, ctypes.POINTER(_P)],
     "grid_destroy": [_P],
     "grid_set_option": [_P, ctypes.c_char_p, _I],
     "grid_rnea": [_P, _I, _P, _P, _P, _P, _P],

@@ -72,6 +72,12 @@ extern "C" {
 grid_status grid_create(int n, const int* parent, const double* axis, const double* X_tree,
                         const double* inertia, const double* gravity, grid_precision prec,
                         grid_model** out) {
+  return grid_create_ex(n, parent, nullptr, axis, X_tree, inertia, gravity, prec, out);
+}
+
+grid_status grid_create_ex(int n, const int* parent, const int* jtype, const double* axis,
+                           const double* X_tree, const double* inertia, const double* gravity,
+                           grid_precision prec, grid_model** out) {
   if (!out) { grid_set_error("grid_create: null output handle"); return GRID_E_ARG; }
   *out = nullptr;
   if (prec != GRID_FP32 && prec != GRID_MIXED && prec != GRID_FP64) {
@@ -84,12 +90,16 @@ grid_status grid_create(int n, const int* parent, const double* axis, const doub
   m->lanes_opt = 0;
   m->ctas_opt = 0;
   m->specialize_opt = 1;
-  m->chain = n >= 1 && parent != nullptr;
-  for (int i = 0; m->chain && i < n; ++i) m->chain = parent[i] == i - 1;
   m->host_f = new ModelDev<float>();
   m->host_d = new ModelDev<double>();
-  grid_status s = grid_build_model(n, parent, axis, X_tree, inertia, gravity, m->host_f, m->host_d);
+  grid_status s = grid_build_model(n, parent, jtype, axis, X_tree, inertia, gravity, m->host_f, m->host_d);
   if (s != GRID_OK) { delete m->host_f; delete m->host_d; delete m; return s; }
+  m->n = m->host_d->n;                       // moving joints
+  // A serial chain of revolute joints in caller order (the depth-first
+  // numbering is then the identity) can use the chain-specialised kernels.
+  m->chain = !m->host_d->any_prism;
+  for (int i = 0; m->chain && i < m->n; ++i)
+    m->chain = m->host_d->parent[i] == i - 1 && m->host_d->perm[i] == i;
   cudaGetDevice(&m->device);
   cudaError_t e1 = cudaMalloc(&m->dev_f, sizeof(ModelDev<float>));
   cudaError_t e2 = cudaMalloc(&m->dev_d, sizeof(ModelDev<double>));

@@ -1,6 +1,7 @@
 // Host-side model construction: validation, depth-first renumbering, device
 // constants and the per-lane schedules of the derivative-column phase.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -26,18 +27,185 @@ struct Unit {            // one root-to-leaf path of one derivative column
   std::vector<uint32_t> steps;
 };
 
+// ---- fixed-joint merging (host, FP64)
+// Compact transform records Er = E (3x3 row-major) then r (3): X = [E 0; -E r~ E].
+// X(A) X(B) = X(E_A E_B, r_B + E_B^T r_A) (B applied first).
+void compose(const double* A, const double* B, double* out) {
+  double o[12];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+      o[3 * i + j] = s;
+    }
+  for (int i = 0; i < 3; ++i) {
+    double s = B[9 + i];
+    for (int k = 0; k < 3; ++k) s += B[3 * k + i] * A[9 + k];
+    o[9 + i] = s;
+  }
+  std::memcpy(out, o, sizeof(o));
+}
+
+void plucker6(const double* Er, double X[6][6]) {
+  const double* r = Er + 9;
+  const double rx[3][3] = {{0, -r[2], r[1]}, {r[2], 0, -r[0]}, {-r[1], r[0], 0}};
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) X[i][j] = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      X[i][j] = X[i + 3][j + 3] = Er[3 * i + j];
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += Er[3 * i + k] * rx[k][j];
+      X[i + 3][j] = -s;
+    }
+}
+
+// (m, c, Ic) -> 6x6 spatial inertia about the body origin, and back.
+void spatial_from_params(const double* p, double I[6][6]) {
+  const double m = p[0], c[3] = {p[1], p[2], p[3]};
+  const double Ic[3][3] = {{p[4], p[7], p[8]}, {p[7], p[5], p[9]}, {p[8], p[9], p[6]}};
+  const double cx[3][3] = {{0, -c[2], c[1]}, {c[2], 0, -c[0]}, {-c[1], c[0], 0}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double cct = 0;
+      for (int k = 0; k < 3; ++k) cct += cx[i][k] * cx[j][k];
+      I[i][j] = Ic[i][j] + m * cct;
+      I[i][j + 3] = m * cx[i][j];
+      I[i + 3][j] = m * cx[j][i];
+      I[i + 3][j + 3] = i == j ? m : 0.0;
+    }
+}
+
+void params_from_spatial(const double I[6][6], double* p) {
+  const double m = I[3][3];
+  const double c[3] = {I[2][4] / m, I[0][5] / m, I[1][3] / m};   // m c~ is the upper-right block
+  const double cx[3][3] = {{0, -c[2], c[1]}, {c[2], 0, -c[0]}, {-c[1], c[0], 0}};
+  double Ic[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double cct = 0;
+      for (int k = 0; k < 3; ++k) cct += cx[i][k] * cx[j][k];
+      Ic[i][j] = I[i][j] - m * cct;
+    }
+  p[0] = m; p[1] = c[0]; p[2] = c[1]; p[3] = c[2];
+  p[4] = Ic[0][0]; p[5] = Ic[1][1]; p[6] = Ic[2][2];
+  p[7] = 0.5 * (Ic[0][1] + Ic[1][0]); p[8] = 0.5 * (Ic[0][2] + Ic[2][0]); p[9] = 0.5 * (Ic[1][2] + Ic[2][1]);
+}
+
+struct Reduced {
+  int n = 0;
+  std::vector<int> parent, jt;
+  std::vector<double> axis, X_tree, inertia;
+};
+
+// Every fixed joint is merged into its nearest moving ancestor (or the base):
+// the fixed body's spatial inertia, expressed in the ancestor's frame (X^T I X),
+// is added to the ancestor's, and bodies hanging from it take the composed
+// fixed transform. What remains has one degree of freedom per body; joint
+// arrays index the moving joints in body order.
+grid_status merge_fixed(int nb, const int* parent, const int* jtype, const double* axis,
+                        const double* X_tree, const double* inertia, Reduced& R) {
+  std::vector<int> anchor(nb, -1), newidx(nb, -1);
+  std::vector<std::array<double, 12>> toanchor(nb);        // X from the anchor's frame to body f's
+  std::vector<std::array<double, 36>> I6(nb);
+  for (int i = 0; i < nb; ++i) {
+    double I[6][6];
+    spatial_from_params(inertia + 10 * i, I);
+    std::memcpy(I6[i].data(), I, sizeof(I));
+  }
+  for (int i = 0; i < nb; ++i) {
+    const int p = parent[i];
+    const bool pfixed = p >= 0 && jtype && jtype[p] == GRID_JOINT_FIXED;
+    const int host = pfixed ? anchor[p] : p;                // moving body (or -1) this one hangs from
+    double Xt[12];
+    std::memcpy(Xt, X_tree + 12 * i, sizeof(Xt));
+    if (pfixed) compose(X_tree + 12 * i, toanchor[p].data(), Xt);
+    if (jtype && jtype[i] == GRID_JOINT_FIXED) {
+      anchor[i] = host;
+      std::memcpy(toanchor[i].data(), Xt, sizeof(Xt));
+      if (host >= 0) {                                      // I_host += X^T I_i X
+        double X[6][6], I[6][6], T[6][6];
+        plucker6(Xt, X);
+        std::memcpy(I, I6[i].data(), sizeof(I));
+        for (int a = 0; a < 6; ++a)
+          for (int b = 0; b < 6; ++b) {
+            double s = 0;
+            for (int k = 0; k < 6; ++k) s += I[a][k] * X[k][b];
+            T[a][b] = s;
+          }
+        for (int a = 0; a < 6; ++a)
+          for (int b = 0; b < 6; ++b) {
+            double s = 0;
+            for (int k = 0; k < 6; ++k) s += X[k][a] * T[k][b];
+            I6[host][6 * a + b] += s;
+          }
+      }
+      continue;
+    }
+    newidx[i] = R.n++;
+    R.parent.push_back(host < 0 ? -1 : newidx[host]);
+    R.jt.push_back(jtype ? jtype[i] : GRID_JOINT_REVOLUTE);
+    for (int a = 0; a < 3; ++a) R.axis.push_back(axis[3 * i + a]);
+    for (int a = 0; a < 12; ++a) R.X_tree.push_back(Xt[a]);
+  }
+  R.inertia.resize(10 * R.n);
+  for (int i = 0; i < nb; ++i)
+    if (newidx[i] >= 0) {
+      double I[6][6];
+      std::memcpy(I, I6[i].data(), sizeof(I));
+      params_from_spatial(I, R.inertia.data() + 10 * newidx[i]);
+    }
+  return GRID_OK;
+}
+
 }  // namespace
 
-grid_status grid_build_model(int n, const int* parent, const double* axis, const double* X_tree,
-                             const double* inertia, const double* gravity,
+static grid_status build_moving(int n, const int* parent, const int* jt, const double* axis,
+                                const double* X_tree, const double* inertia, const double* gravity,
+                                ModelDev<float>* mf, ModelDev<double>* md);
+
+grid_status grid_build_model(int nb, const int* parent, const int* jtype, const double* axis,
+                             const double* X_tree, const double* inertia, const double* gravity,
                              ModelDev<float>* mf, ModelDev<double>* md) {
-  if (n < 1 || n > GRID_MAX_DOF) {
-    grid_set_error("grid_create: n = %d outside [1, %d]", n, GRID_MAX_DOF);
+  if (nb < 1 || nb > GRID_MAX_BODIES) {
+    grid_set_error("grid_create: %d bodies outside [1, %d]", nb, GRID_MAX_BODIES);
     return GRID_E_TOPOLOGY;
   }
   if (!parent || !axis || !X_tree || !inertia || !gravity) {
     grid_set_error("grid_create: null model array");
     return GRID_E_ARG;
+  }
+  for (int i = 0; i < nb; ++i) {
+    if (parent[i] < -1 || parent[i] >= i) {
+      grid_set_error("grid_create: parent[%d] = %d violates -1 <= parent[i] < i", i, parent[i]);
+      return GRID_E_TOPOLOGY;
+    }
+    if (jtype && (jtype[i] < GRID_JOINT_REVOLUTE || jtype[i] > GRID_JOINT_FIXED)) {
+      grid_set_error("grid_create: joint type %d of body %d is not 0, 1 or 2", jtype[i], i);
+      return GRID_E_ARG;
+    }
+    if (jtype && jtype[i] == GRID_JOINT_FIXED && !(inertia[10 * i] >= 0.0)) {
+      grid_set_error("grid_create: fixed body %d has mass %g (must be >= 0)", i, inertia[10 * i]);
+      return GRID_E_NUMERIC;
+    }
+  }
+  Reduced R;
+  grid_status st = merge_fixed(nb, parent, jtype, axis, X_tree, inertia, R);
+  if (st != GRID_OK) return st;
+  if (R.n == 0) {
+    grid_set_error("grid_create: every joint is fixed (no degree of freedom)");
+    return GRID_E_TOPOLOGY;
+  }
+  return build_moving(R.n, R.parent.data(), R.jt.data(), R.axis.data(), R.X_tree.data(), R.inertia.data(),
+                      gravity, mf, md);
+}
+
+static grid_status build_moving(int n, const int* parent, const int* jt, const double* axis,
+                                const double* X_tree, const double* inertia, const double* gravity,
+                                ModelDev<float>* mf, ModelDev<double>* md) {
+  if (n < 1 || n > GRID_MAX_DOF) {
+    grid_set_error("grid_create: %d degrees of freedom outside [1, %d]", n, GRID_MAX_DOF);
+    return GRID_E_TOPOLOGY;
   }
   for (int i = 0; i < n; ++i) {
     if (parent[i] < -1 || parent[i] >= i) {
@@ -114,6 +282,8 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
       if (X_tree[12 * c + a] != e) ident = false;
     }
     D.et_ident[k] = ident ? 1 : 0;
+    D.jt[k] = jt[c];
+    if (jt[c] == GRID_JOINT_PRISMATIC) D.any_prism = 1;
     for (int a = 0; a < 3; ++a) D.rT[k][a] = X_tree[12 * c + 9 + a];
     // Spatial inertia about the body origin in compact form: mass m,
     // first moment h = m c, rotational inertia Ibar = Ic + m (c.c 1 - c c^T).
@@ -210,6 +380,8 @@ grid_status grid_build_model(int n, const int* parent, const double* axis, const
   ModelDev<float>& F = *mf;
   std::memset(&F, 0, sizeof(F));
   F.n = D.n; F.maxd = D.maxd; F.nsk = D.nsk; F.ncomp = D.ncomp; F.nbranch = D.nbranch;
+  F.any_prism = D.any_prism;
+  std::memcpy(F.jt, D.jt, sizeof(D.jt));
   std::memcpy(F.steps, D.steps, sizeof(D.steps));
   std::memcpy(F.sched_off, D.sched_off, sizeof(D.sched_off));
   std::memcpy(F.parent, D.parent, sizeof(D.parent));

@@ -118,9 +118,12 @@ GRID_HD constexpr KnotLayout make_layout(int n, int nsk, int nbranch, int ssize,
 
 GRID_HD constexpr int layout_kind(int mode) { return mode == MODE_GRAD ? 0 : (mode == MODE_VJP ? 2 : 1); }
 
+#define GRID_MAX_BODIES 256       // bodies before fixed joints are merged
+
 template <class S>
 struct ModelDev {
   int n, maxd, nsk, ncomp, nbranch;
+  int any_prism;                 // some joint is prismatic
   int steps[GRID_NUM_LANE_CFG];      // steps per lane for 8, 16, 32 lanes
   int sched_off[GRID_NUM_LANE_CFG];  // offsets into sched
   KnotLayout L;                  // workspace of the gradient-of-FD kernel (J is stored directly)
@@ -135,6 +138,7 @@ struct ModelDev {
   int skoff[GRID_MAX_DOF];       // first subspace row of body k
   int branch[GRID_MAX_DOF];      // slot of a body with >= 2 children, else -1
   int et_ident[GRID_MAX_DOF];
+  int jt[GRID_MAX_DOF];          // GRID_JOINT_REVOLUTE or GRID_JOINT_PRISMATIC
   alignas(16) S axis[GRID_MAX_DOF][4];   // unit axis, padded
   S ET[GRID_MAX_DOF][9];
   S rT[GRID_MAX_DOF][3];
@@ -172,6 +176,6 @@ struct grid_model {
 
 // Host helpers (grid_host.cpp)
 void grid_set_error(const char* fmt, ...);
-grid_status grid_build_model(int n, const int* parent, const double* axis, const double* X_tree,
-                             const double* inertia, const double* gravity,
+grid_status grid_build_model(int nb, const int* parent, const int* jtype, const double* axis,
+                             const double* X_tree, const double* inertia, const double* gravity,
                              ModelDev<float>* mf, ModelDev<double>* md);

@@ -44,6 +44,7 @@ struct RtTopo {
   __device__ int perm(int i) const { return M.perm[i]; }
   __device__ int skoff(int i) const { return M.skoff[i]; }
   __device__ int branch(int i) const { return M.branch[i]; }
+  __device__ bool prism(int i) const { return M.jt[i] != 0; }
 };
 
 template <class S, int MODE, int N>
@@ -64,6 +65,7 @@ struct ChainTopo {
   GRID_HD static constexpr int perm(int i) { return i; }
   GRID_HD static constexpr int skoff(int i) { return i * (i + 1) / 2; }
   GRID_HD static constexpr int branch(int) { return -1; }
+  GRID_HD static constexpr bool prism(int) { return false; }   // revolute chains only
 };
 
 template <class S, class Tp>
@@ -96,16 +98,26 @@ __device__ void ph_transforms(const Ctx<S, Tp>& c) {
   const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
   for (int k = c.l; k < tp.n(); k += T) {
     S qk = W[L.Q + tp.perm(k)];
+    const S* a = M.axis[k];
+    S* X = W + L.X + 12 * k;
+    if (tp.prism(k)) {
+      // X_J = X(1, q a): X = X(E_T, r_T + E_T^T q a)
+      const S* ET = M.ET[k];
+      const S d[3] = {qk * a[0], qk * a[1], qk * a[2]};
+#pragma unroll
+      for (int e = 0; e < 9; ++e) X[e] = ET[e];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) X[9 + j] = M.rT[k][j] + ET[j] * d[0] + ET[3 + j] * d[1] + ET[6 + j] * d[2];
+      continue;
+    }
     S s, co;
     if constexpr (std::is_same<S, float>::value) sincosf(qk, &s, &co); else sincos(qk, &s, &co);
-    const S* a = M.axis[k];
     // E_J = R(a, q)^T = cos q 1 + (1 - cos q) a a^T - sin q a~
     S EJ[9];
     const S omc = S(1) - co;
     EJ[0] = co + omc * a[0] * a[0];      EJ[1] = omc * a[0] * a[1] + s * a[2]; EJ[2] = omc * a[0] * a[2] - s * a[1];
     EJ[3] = omc * a[1] * a[0] - s * a[2]; EJ[4] = co + omc * a[1] * a[1];     EJ[5] = omc * a[1] * a[2] + s * a[0];
     EJ[6] = omc * a[2] * a[0] + s * a[1]; EJ[7] = omc * a[2] * a[1] - s * a[0]; EJ[8] = co + omc * a[2] * a[2];
-    S* X = W + L.X + 12 * k;
     if (M.et_ident[k]) {
 #pragma unroll
       for (int e = 0; e < 9; ++e) X[e] = EJ[e];
@@ -143,8 +155,10 @@ __device__ __forceinline__ void subspace_step(const Ctx<S, Tp>& c, int k, const 
   const bool carry_ok = T > tp.maxd();        // one row id per lane: reuse the previous body's row
   for (int rho = c.l; rho <= tp.maxd(); rho += T) {
     if (rho == dk) {
-      S row[8] = {M.axis[k][0], M.axis[k][1], M.axis[k][2], S(0), S(0), S(0),
-                  W[L.QD + tp.perm(k)], S(k)};
+      S row[8];
+      joint_s(M.axis[k], tp.prism(k), row);
+      row[6] = W[L.QD + tp.perm(k)];
+      row[7] = S(k);
       S* dst = SK + 8 * (tp.skoff(k) + dk);
       st4(dst, row);
       st4(dst + 4, row + 4);
@@ -242,6 +256,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     ld12(W + L.X + 12 * i, E);
     const S* r = E + 9;
     const S a[3] = {M.axis[i][0], M.axis[i][1], M.axis[i][2]};
+    const bool pr = tp.prism(i);              // S_i = [0; a] instead of [a; 0]
     S ia[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
     S ul = S(0);
     if (l < 6) {                              // column l of I^A_i
@@ -255,13 +270,14 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) ia[e] += sl[e];
       }
-      ul = ia[0] * a[0] + ia[1] * a[1] + ia[2] * a[2];   // U_l (I^A symmetric)
+      ul = dot_s(a, pr, ia);                  // U_l = (I^A S)_l (I^A symmetric)
       UB[8 * i + l] = ul;
     }
     S u[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) u[e] = GRID_SHFL(ul, base + e);
-    const P Dk = P(a[0]) * P(u[0]) + P(a[1]) * P(u[1]) + P(a[2]) * P(u[2]);
+    const S us0 = pr ? u[3] : u[0], us1 = pr ? u[4] : u[1], us2 = pr ? u[5] : u[2];   // S^T U
+    const P Dk = P(a[0]) * P(us0) + P(a[1]) * P(us1) + P(a[2]) * P(us2);
     const P Dinv = P(1) / Dk;
     if (l == 0) DINV[i] = Dinv;
 #pragma unroll
@@ -270,7 +286,11 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
       if (k >= i && k < tp.sub_end(i)) {
         S mik;
         if (k == i) mik = S(Dinv);
-        else mik = S(-Dinv * (P(a[0]) * P(fb[cc][0]) + P(a[1]) * P(fb[cc][1]) + P(a[2]) * P(fb[cc][2])));
+        else {
+          const S f0 = pr ? fb[cc][3] : fb[cc][0], f1 = pr ? fb[cc][4] : fb[cc][1],
+                  f2 = pr ? fb[cc][5] : fb[cc][2];
+          mik = S(-Dinv * (P(a[0]) * P(f0) + P(a[1]) * P(f1) + P(a[2]) * P(f2)));
+        }
         MI[i * MS + k] = mik;
         if (p >= 0) {
           S w[6];
@@ -323,6 +343,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     ld12(W + L.X + 12 * i, E);
     const S* r = E + 9;
     const S* a = M.axis[i];
+    const bool pr = tp.prism(i);
     S Ui[6];
     ld6(UB + 8 * i, Ui);
     const P Dinv = DINV[i];
@@ -349,7 +370,8 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
           MI[i * MS + k] = mk;
         }
 #pragma unroll
-        for (int e = 0; e < 6; ++e) pc[cc][e] = (e < 3 ? a[e] * mk : S(0)) + t[e];
+        for (int e = 0; e < 6; ++e)
+          pc[cc][e] = (pr ? (e >= 3 ? a[e - 3] * mk : S(0)) : (e < 3 ? a[e] * mk : S(0))) + t[e];
         if (br >= 0) {
 #pragma unroll
           for (int e = 0; e < 6; ++e) BP[(6 * br + e) * n + k] = pc[cc][e];
@@ -495,10 +517,10 @@ __device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
     ld6(W + U + L.A + 8 * k, a);
     ld6(FA + 8 * k, fo);
     const S qdk = W[L.QD + tp.perm(k)];
+    const bool pr = tp.prism(k);
     S idt[6], vxs[6], w[6];
     i_mul(M.inert[k], da, idt);
-    cross3(v, ax, vxs);
-    cross3(v + 3, ax, vxs + 3);
+    cross_s(v, ax, pr, vxs);
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
       w[e] = a[e] + da[e] - qdk * vxs[e];
@@ -506,8 +528,7 @@ __device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
     }
     st6(FA + 8 * k, fo);
     S B[6];
-    cross3(w, ax, B);
-    cross3(w + 3, ax, B + 3);
+    cross_s(w, ax, pr, B);
     st6(W + L.BPH + 12 * k, B);
   }
   SYNC();
@@ -543,9 +564,8 @@ __device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
     S F[6];
     ld6(FA + 8 * k, F);
     const S* ax = M.axis[k];
-    S Ph[6];                                   // [a; 0] x* F = [a x F_ang; a x F_lin]
-    cross3(ax, F, Ph);
-    cross3(ax, F + 3, Ph + 3);
+    S Ph[6];                                   // S x* F
+    crf_s(ax, tp.prism(k), F, Ph);
     st6u(W + L.BPH + 12 * k + 6, Ph);
   }
   SYNC();
@@ -607,8 +627,8 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
     S ndv[6], nda[6], vxs[6];
     x_mul(E, r, dv, ndv);
     x_mul(E, r, da, nda);
-    cross3(v, ax, vxs);          // v x [a; 0] = [w x a; v x a]
-    cross3(v + 3, ax, vxs + 3);
+    const bool pr = tp.prism(k);
+    cross_s(v, ax, pr, vxs);     // v x S
     if (root) {
       if (uq) {
         S B[6];
@@ -616,16 +636,16 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
 #pragma unroll
         for (int e = 0; e < 6; ++e) { ndv[e] += vxs[e]; nda[e] += B[e]; }
       } else {
-        ndv[0] += ax[0]; ndv[1] += ax[1]; ndv[2] += ax[2];
+        S s6[6];
+        joint_s(ax, pr, s6);
 #pragma unroll
-        for (int e = 0; e < 6; ++e) nda[e] += vxs[e];
+        for (int e = 0; e < 6; ++e) { ndv[e] += s6[e]; nda[e] += vxs[e]; }
       }
     }
     {
       const S sq[3] = {ax[0] * qdk, ax[1] * qdk, ax[2] * qdk};
       S t[6];
-      cross3(ndv, sq, t);        // dv x [a qd; 0]
-      cross3(ndv + 3, sq, t + 3);
+      cross_s(ndv, sq, pr, t);   // dv x S qd
 #pragma unroll
       for (int e = 0; e < 6; ++e) nda[e] += t[e];
     }
@@ -792,6 +812,7 @@ __device__ void ph_vjp_sweep(const Ctx<S, Tp>& c) {
     const int br = tp.branch(k);
     const bool from_next = k + 1 < tp.n() && tp.parent(k + 1) == k;
     const S* ax = M.axis[k];
+    const bool pr = tp.prism(k);
     const S qdk = W[L.QD + tp.perm(k)];
     S ab = S(0), vb = S(0);
     if (l < 6) {
@@ -802,11 +823,10 @@ __device__ void ph_vjp_sweep(const Ctx<S, Tp>& c) {
 #pragma unroll
     for (int e = 0; e < 6; ++e) A[e] = GRID_SHFL(ab, base + e);
     {
-      // (S qd) x* Abar = [a qd x Abar_ang; a qd x Abar_lin]
+      // (S qd) x* Abar
       const S sq[3] = {ax[0] * qdk, ax[1] * qdk, ax[2] * qdk};
       S t[6];
-      cross3(sq, A, t);
-      cross3(sq, A + 3, t + 3);
+      crf_s(sq, pr, A, t);
       S add = t[0];
 #pragma unroll
       for (int e = 1; e < 6; ++e) add = (l == e) ? t[e] : add;
@@ -820,11 +840,9 @@ __device__ void ph_vjp_sweep(const Ctx<S, Tp>& c) {
       ld6(W + L.BPH + 12 * k, B);
       ld6(W + U + L.F + 8 * k, F);
       ld6(W + U + L.PSI + 8 * k, psi);
-      cross3(v, ax, vxs);
-      cross3(v + 3, ax, vxs + 3);
-      cross3(psi, ax, pxs);
-      cross3(psi + 3, ax, pxs + 3);
-      S gqd = ax[0] * V[0] + ax[1] * V[1] + ax[2] * V[2];
+      cross_s(v, ax, pr, vxs);
+      cross_s(psi, ax, pr, pxs);
+      S gqd = dot_s(ax, pr, V);
       S gq = S(0);
 #pragma unroll
       for (int e = 0; e < 6; ++e) {

@@ -86,6 +86,41 @@ __device__ __forceinline__ S x_mul_c(const S* E, const S* r, const S* m, int c) 
   return E[3 * k] * t0 + E[3 * k + 1] * t1 + E[3 * k + 2] * t2;
 }
 
+// ---- joint motion subspaces: S = [a; 0] (revolute) or [0; a] (prismatic, pr)
+template <class S>
+__device__ __forceinline__ void joint_s(const S* a, bool pr, S* s) {
+  s[0] = pr ? S(0) : a[0]; s[1] = pr ? S(0) : a[1]; s[2] = pr ? S(0) : a[2];
+  s[3] = pr ? a[0] : S(0); s[4] = pr ? a[1] : S(0); s[5] = pr ? a[2] : S(0);
+}
+// v x S = [w x a; v x a] (revolute) or [0; w x a] (prismatic)
+template <class S>
+__device__ __forceinline__ void cross_s(const S* v, const S* a, bool pr, S* out) {
+  if (pr) {
+    out[0] = out[1] = out[2] = S(0);
+    cross3(v, a, out + 3);
+  } else {
+    cross3(v, a, out);
+    cross3(v + 3, a, out + 3);
+  }
+}
+// S x* f = [a x n; a x f] (revolute) or [a x f; 0] (prismatic), f = [n; f]
+template <class S>
+__device__ __forceinline__ void crf_s(const S* a, bool pr, const S* f, S* out) {
+  if (pr) {
+    cross3(a, f + 3, out);
+    out[3] = out[4] = out[5] = S(0);
+  } else {
+    cross3(a, f, out);
+    cross3(a, f + 3, out + 3);
+  }
+}
+// S^T f
+template <class S>
+__device__ __forceinline__ S dot_s(const S* a, bool pr, const S* f) {
+  const S f0 = pr ? f[3] : f[0], f1 = pr ? f[4] : f[1], f2 = pr ? f[5] : f[2];
+  return a[0] * f0 + a[1] * f1 + a[2] * f2;
+}
+
 // Component c of X^T f = [E^T f_ang + r x E^T f_lin; E^T f_lin], with the
 // transform record Er = E(9) r(3) read from memory: a lane-dependent c then
 // indexes shared memory instead of forcing a local-memory copy of E.

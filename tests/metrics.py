@@ -35,3 +35,25 @@ def col_rel_err_stats(x, y, floor=1e-6):
 def vec_rel_err(x, y, floor=1e-6):
     """Vector outputs [N, n] as one column each."""
     return col_rel_err(np.asarray(x)[:, :, None], np.asarray(y)[:, :, None], floor)
+
+
+def col_err_split(x, y, zero=1e-12, floor=1e-6):
+    """Errors for outputs with structurally zero columns (their oracle norm is at
+    rounding level, e.g. d/dq of a prismatic base joint, or a column that is zero
+    by cancellation of O(1) terms, where FP32 leaves noise of ~1e-7 of the
+    largest column). Per knot point, with m = the largest column norm:
+      e_nz = the metric above (with `floor`) over columns with norm > zero * m,
+      e_z  = max |x - y| / m over the structurally zero columns.
+    Returns (max e_nz, max e_z) over knot points."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    assert x.shape == y.shape, (x.shape, y.shape)
+    if x.size == 0:
+        return 0.0, 0.0
+    nrm = np.linalg.norm(y, axis=-2)                                   # [N, cols]
+    m = np.maximum(nrm.max(axis=-1, keepdims=True), 1e-30)
+    diff = np.abs(x - y).max(axis=-2)
+    zmask = nrm <= zero * m
+    e_nz = np.where(zmask, 0.0, diff / np.maximum(nrm, floor * m))
+    e_z = np.where(zmask, diff / m, 0.0)
+    return float(e_nz.max()), float(e_z.max())
