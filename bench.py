@@ -171,14 +171,34 @@ def time_steps(fn, steps, warmup, stream, dist=None):
     return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
 
 
+def device_latency_us(fn, reps=200, warmup=20):
+    """Median device time of one call: each call is queued behind a ~50 us
+    device-side spin, so the CUDA events around it (on the launching stream)
+    bracket the GPU's execution of the call and not the host's time to issue it."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(100_000)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e3)
+    return float(np.median(ts))
+
+
 def latency_table(grid, reps=200, warmup=20):
     """Single-computation latency (one knot point, compute only, inputs resident)
-    of each entry point for the three workload robots: median over `reps` calls,
-    each bracketed by CUDA events on the launching stream."""
+    of each entry point for the three workload robots (device_latency_us)."""
     import numpy as np
     import torch
     import grid_inputs as gi
-    stream = torch.cuda.current_stream()
     table = {}
     for name in ("chain7", "tree12", "tree30"):
         r = gi.robot(name)
@@ -194,20 +214,7 @@ def latency_table(grid, reps=200, warmup=20):
                  "fd": lambda: m.fd(q, qd, tau, out=outs["fd"]),
                  "grad_id": lambda: m.grad_rnea(q, qd, tau, out=outs["grad_id"]),
                  "grad_fd": lambda: m.grad_fd(q, qd, tau, out=outs["grad_fd"])}
-        row = {}
-        for alg, fn in calls.items():
-            for _ in range(warmup):
-                fn()
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(reps)]
-            torch.cuda.synchronize()
-            for e0, e1 in ev:
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-            torch.cuda.synchronize()
-            row[alg] = float(np.median([e0.elapsed_time(e1) * 1e3 for e0, e1 in ev]))
-        table[name] = row
+        table[name] = {alg: device_latency_us(fn, reps, warmup) for alg, fn in calls.items()}
         m.close()
     return table
 
@@ -385,7 +392,7 @@ def run_ours(args):
     # single-trajectory latency at N = 128 (compute only)
     q1, qd1, tau1 = q[:KNOTS], qd[:KNOTS], tau[:KNOTS]
     J1 = J[:KNOTS]
-    sec1 = time_steps(lambda: model.grad_fd(q1, qd1, tau1, out=J1), 200, 20, stream, None)
+    lat128 = device_latency_us(lambda: model.grad_fd(q1, qd1, tau1, out=J1))
 
     lat_table = latency_table(grid) if rank == 0 else None
 
@@ -429,9 +436,10 @@ def run_ours(args):
                                  "compiled for its length)"},
             "fp64_plain": {"value": fp64_value, "unit": UNIT, "knot_points_per_launch": Nd},
             "tree12": {"value": t12_value, "unit": UNIT, "knot_points_per_launch": Nk // 2},
-            "latency_n128_us": sec1 / 200 * 1e6,
+            "latency_n128_us": lat128,
             "latency_n1_us": lat_table,
-            "latency_n1_note": "one knot point per call, compute only, median of 200 event-timed calls "
+            "latency_n1_note": "one knot point per call, compute only: median over 200 calls of the "
+                               "device time between CUDA events, each call queued behind a device spin "
                                "(RNEA at qdd = tau's values; tree30 in mixed precision)",
             "serve": serve,
             "cpu_baseline": cpu,

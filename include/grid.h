@@ -59,7 +59,7 @@ typedef enum {
 /* Largest supported number of moving joints (degrees of freedom). */
 #define GRID_MAX_DOF 32
 
-/* Joint types (Sec. IV-A lists revolute, prismatic and fixed joints). */
+/* Joint types (Sec. IV-B lists revolute, prismatic and fixed joints). */
 typedef enum {
   GRID_JOINT_REVOLUTE = 0,  /* rotation by q about the unit axis a: S = [a; 0] */
   GRID_JOINT_PRISMATIC = 1, /* translation of the child origin by q a: S = [0; a] */
@@ -90,7 +90,7 @@ grid_status grid_create(int n, const int* parent, const double* axis, const doub
                         grid_model** out);
 
 /*
- * grid_create_ex -- grid_create with a joint type per body (Sec. IV-A: the
+ * grid_create_ex -- grid_create with a joint type per body (Sec. IV-B: the
  * library supports revolute, prismatic and fixed joints).
  *   nb      number of bodies, 1 <= nb <= 256, at most GRID_MAX_DOF of them moving
  *   jtype   [nb] grid_joint_type per body, or NULL for all revolute

@@ -27,7 +27,7 @@
 //  * The backward-pass term X^T (S_i x* f_i) uses the accumulated force f_i
 //    (own plus children) and applies only for u = q_i.
 //  * Gravity enters as a fictitious base acceleration a_0 = -g.
-//  * iX_lambda = X_J(q_i) X_T,i. Joint types (Sec. IV-A lists revolute,
+//  * iX_lambda = X_J(q_i) X_T,i. Joint types (Sec. IV-B lists revolute,
 //    prismatic and fixed joints among the supported URDF joints): revolute X_J
 //    is a coordinate rotation by q_i about the unit axis a_i, S_i = [a_i; 0];
 //    prismatic X_J is a translation of the child origin by q_i a_i,

@@ -30,6 +30,7 @@
 template <class S, int MODE>
 struct RtTopo {
   static constexpr int kUnroll = 1;
+  static constexpr int kChainN = 0;       // not a compile-time chain
   const ModelDev<S>& M;
   __device__ explicit RtTopo(const ModelDev<S>& m) : M(m) {}
   __device__ const KnotLayout& layout() const { return layout_of<MODE>(M); }
@@ -50,6 +51,7 @@ struct RtTopo {
 template <class S, int MODE, int N>
 struct ChainTopo {
   static constexpr int kUnroll = N;
+  static constexpr int kChainN = N;
   __device__ explicit ChainTopo(const ModelDev<S>&) {}
   GRID_HD static constexpr KnotLayout layout() {
     return make_layout(N, N * (N + 1) / 2, 0, (int)sizeof(S), layout_kind(MODE));
@@ -248,6 +250,9 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
   for (int cc = 0; cc < CPL; ++cc)
 #pragma unroll
     for (int e = 0; e < 6; ++e) fb[cc][e] = S(0);
+  // column l of the next body's inertia, fetched one body ahead (device memory)
+  S icn[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+  if (l < 6) ldg6(c.gM->Icol[n - 1][l], icn);
 #pragma unroll (Tp::kUnroll)
   for (int i = n - 1; i >= 0; --i) {
     const int p = tp.parent(i);
@@ -260,7 +265,9 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     S ia[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
     S ul = S(0);
     if (l < 6) {                              // column l of I^A_i
-      ld6(c.gM->Icol[i][l], ia);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ia[e] = icn[e];
+      if (i > 0) ldg6(c.gM->Icol[i - 1][l], icn);
       if (i + 1 < n && tp.parent(i + 1) == i) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) ia[e] += carry[e];
@@ -363,9 +370,8 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
             for (int e = 0; e < 6; ++e) pp[e] = BP[(6 * tp.branch(p) + e) * n + k];
           }
           x_mul(E, r, pp, t);
-          P ut = P(Ui[0]) * P(t[0]);
-#pragma unroll
-          for (int e = 1; e < 6; ++e) ut += P(Ui[e]) * P(t[e]);
+          const P ut = (P(Ui[0]) * P(t[0]) + P(Ui[1]) * P(t[1])) + (P(Ui[2]) * P(t[2]) + P(Ui[3]) * P(t[3])) +
+                       (P(Ui[4]) * P(t[4]) + P(Ui[5]) * P(t[5]));
           mk = S(P(mk) - Dinv * ut);
           MI[i * MS + k] = mk;
         }
@@ -455,7 +461,7 @@ __device__ void ph_joint_forces(const Ctx<S, Tp>& c, int f_off, int out_off) {
       S s[6], f[6];
       ld6(W + L.SK + 8 * (tp.skoff(k) + di), s);
       ld6(W + f_off + 8 * k, f);
-      acc += s[0] * f[0] + s[1] * f[1] + s[2] * f[2] + s[3] * f[3] + s[4] * f[4] + s[5] * f[5];
+      acc += dot6(s, f);
     }
     W[out_off + i] = acc;
   }
@@ -592,15 +598,21 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
   const int n = tp.n();
   const int U = L.UNION;
   S* DC = W + U + L.DC;
-  for (int e = c.l; e < 2 * n * n; e += T) DC[e] = S(0);
+  // In a chain every column has one path (j .. n-1), which writes its whole
+  // column of dc at the end; elsewhere several paths add into it.
+  if constexpr (Tp::kChainN == 0) {
+    for (int e = c.l; e < 2 * n * n; e += T) DC[e] = S(0);
+  }
   SYNC();
   S dv[6], da[6], acc[MAXD];
 #pragma unroll
   for (int e = 0; e < 6; ++e) { dv[e] = S(0); da[e] = S(0); }
 #pragma unroll
   for (int d = 0; d < MAXD; ++d) acc[d] = S(0);
+  uint32_t st_next = nsteps > 0 ? sched[c.l] : 0u;   // descriptors are fetched one step ahead
   for (int s = 0; s < nsteps; ++s) {
-    const uint32_t st = sched[s * T + c.l];
+    const uint32_t st = st_next;
+    if (s + 1 < nsteps) st_next = sched[(s + 1) * T + c.l];
     if (!(st & STEP_VALID)) continue;
     const int k = STEP_BODY(st);
     const int col = STEP_COL(st);
@@ -662,25 +674,45 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
 #pragma unroll
       for (int e = 0; e < 6; ++e) df[e] += Ph[e];
     }
-    if (st & STEP_OWNED) {
+    if constexpr (Tp::kChainN > 0) {
+      // chain: body d is the ancestor at depth d; every step owns its body.
+      // Rows past depth dk are not needed: their loads repeat row dk and the
+      // result is discarded, which keeps the loop free of branches.
+      static_assert(Tp::kChainN <= MAXD, "accumulators");
 #pragma unroll
-      for (int d = 0; d < MAXD; ++d) {
-        if (d <= dk) {
-          S sr[6];
-          ld6(rows + 8 * d, sr);
-          acc[d] += sr[0] * df[0] + sr[1] * df[1] + sr[2] * df[2] + sr[3] * df[3] + sr[4] * df[4] +
-                    sr[5] * df[5];
+      for (int d = 0; d < Tp::kChainN; ++d) {
+        S sr[6];
+        ld6(rows + 8 * min(d, dk), sr);
+        const S t = dot6(sr, df);
+        acc[d] += d <= dk ? t : S(0);
+      }
+      if (st & STEP_FLUSH) {                  // the path ends at body n - 1: all depths
+#pragma unroll
+        for (int d = 0; d < Tp::kChainN; ++d) {
+          DC[d * 2 * n + col] = acc[d];
+          acc[d] = S(0);
         }
       }
-    }
-    if (st & STEP_FLUSH) {
-      int b = k;
+    } else {
+      if (st & STEP_OWNED) {
 #pragma unroll
-      for (int d = MAXD - 1; d >= 0; --d) {
-        if (d <= dk) {
-          GRID_ATOMIC_ADD(DC + b * 2 * n + col, acc[d]);
-          acc[d] = S(0);
-          b = tp.parent(b);
+        for (int d = 0; d < MAXD; ++d) {
+          if (d <= dk) {
+            S sr[6];
+            ld6(rows + 8 * d, sr);
+            acc[d] += dot6(sr, df);
+          }
+        }
+      }
+      if (st & STEP_FLUSH) {
+        int b = k;
+#pragma unroll
+        for (int d = MAXD - 1; d >= 0; --d) {
+          if (d <= dk) {
+            GRID_ATOMIC_ADD(DC + b * 2 * n + col, acc[d]);
+            acc[d] = S(0);
+            b = tp.parent(b);
+          }
         }
       }
     }

@@ -86,6 +86,30 @@ __device__ __forceinline__ S x_mul_c(const S* E, const S* r, const S* m, int c) 
   return E[3 * k] * t0 + E[3 * k + 1] * t1 + E[3 * k + 2] * t2;
 }
 
+// a . b for 6-vectors as a balanced sum (dependency depth 4 instead of 7)
+template <class S>
+__device__ __forceinline__ S dot6(const S* a, const S* b) {
+  return (a[0] * b[0] + a[1] * b[1]) + (a[2] * b[2] + a[3] * b[3]) + (a[4] * b[4] + a[5] * b[5]);
+}
+// 6-vector stored in an 8-scalar record of read-only device memory (not shared)
+template <class S>
+__device__ __forceinline__ void ldg6(const S* p, S* o) {
+#ifdef __CUDACC__
+  if constexpr (sizeof(S) == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    const float2 u = __ldg(reinterpret_cast<const float2*>(p + 4));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w; o[4] = u.x; o[5] = u.y;
+  } else {
+    for (int e = 0; e < 6; e += 2) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(p + e));
+      o[e] = t.x; o[e + 1] = t.y;
+    }
+  }
+#else
+  for (int e = 0; e < 6; ++e) o[e] = p[e];
+#endif
+}
+
 // ---- joint motion subspaces: S = [a; 0] (revolute) or [0; a] (prismatic, pr)
 template <class S>
 __device__ __forceinline__ void joint_s(const S* a, bool pr, S* s) {

@@ -1,4 +1,4 @@
-"""Pins of the FP64 oracle for prismatic and fixed joints (Sec. IV-A names
+"""Pins of the FP64 oracle for prismatic and fixed joints (Sec. IV-B names
 revolute, prismatic and fixed among the supported joints): closed forms of a
 slider and a cart-pole, the independent Lagrangian formulation on random trees
 of mixed joint types, complex-step derivatives, invariants, and fixed joints
