@@ -123,7 +123,7 @@ int grid_model_dof(const grid_model* model);
  *   "precision"   GRID_FP32 or GRID_MIXED for the float entry points
  *   "ctas_per_sm" resident CTAs per SM the launcher sizes the grid for (0 = auto)
  *   "specialize"  1 (default): serial chains (parent[i] = i - 1) of 2 to 8 bodies
- *                 run the FP32 gradient of FD in a kernel compiled for their
+ *                 run the gradient of FD (FP32 and FP64) in a kernel compiled for their
  *                 length (the chain topology of Sec. IV-C fixed at compile time);
  *                 0: always the kernel that reads the topology at run time
  */

@@ -1,6 +1,6 @@
 // Kernel instantiations for serial chains (parent(i) = i - 1) of 2 .. 8
-// bodies, FP32 gradient of FD: the topology and the workspace layout are
-// compile-time constants (ChainTopo), 8 lanes per knot point.
+// bodies, gradient of FD in FP32 and FP64: the topology and the workspace
+// layout are compile-time constants (ChainTopo), 8 lanes per knot point.
 #include "grid_launch.cuh"
 
 template <class S, int MODE>
@@ -21,3 +21,7 @@ grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const Model
 template grid_status launch_chain<float, MODE_GRAD>(const grid_model*, const ModelDev<float>*, const ModelDev<float>*,
                                                     int, const float*, const float*, const float*, const float*,
                                                     float*, float*, float*, cudaStream_t);
+template grid_status launch_chain<double, MODE_GRAD>(const grid_model*, const ModelDev<double>*,
+                                                     const ModelDev<double>*, int, const double*, const double*,
+                                                     const double*, const double*, double*, double*, double*,
+                                                     cudaStream_t);

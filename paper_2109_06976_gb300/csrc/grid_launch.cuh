@@ -169,7 +169,7 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   else { hm = m->host_d; dm = m->dev_d; }
   int T = m->lanes_opt;
   const int n = hm->n;
-  if constexpr (std::is_same<S, float>::value && MODE == MODE_GRAD && !MIXED) {
+  if constexpr (MODE == MODE_GRAD && !MIXED) {
     if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
       return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   }

@@ -114,7 +114,8 @@ CHAINS = [(n, s, g) for n in range(2, 10) for s, g in ((1, True), (2, False))]
 
 
 @pytest.mark.parametrize("n,seed,general", CHAINS, ids=lambda x: str(x))
-def test_chain_specialised_kernel(grid, n, seed, general):
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_chain_specialised_kernel(grid, n, seed, general, dtype):
     """Serial chains (parent[i] = i - 1): the kernel compiled for the chain's
     length against the oracle and against the run-time-topology kernel, on a
     ragged batch; n = 9 has no specialised kernel and takes the general one."""
@@ -123,17 +124,18 @@ def test_chain_specialised_kernel(grid, n, seed, general):
     spec = grid.Model.from_robot(r)
     gen = grid.Model.from_robot(r)
     gen.set_option("specialize", 0)
-    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, 77, 11, torch.float32)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, 77, 11, dtype)
     Js, qdds = spec.grad_fd(q, qd, tau, return_qdd=True)
     Jg, qddg = gen.grad_fd(q, qd, tau, return_qdd=True)
     Js, qdds, Jg, qddg = (x.cpu().numpy() for x in (Js, qdds, Jg, qddg))
     ref = oracle.grad_fd(r, q64, qd64, tau64)
-    assert col_rel_err(Js, ref, floor=1e-4) <= TOL32
-    assert vec_rel_err(qdds, oracle.fd(r, q64, qd64, tau64)) <= TOL32
-    # both kernels meet the bar; they differ only in FP32 rounding order
-    assert col_rel_err(Jg, ref, floor=1e-4) <= TOL32
-    assert col_rel_err(Js, Jg, floor=1e-4) <= TOL32
-    assert vec_rel_err(qdds, qddg) <= 1e-5
+    tol, fl = (TOL32, 1e-4) if dtype == torch.float32 else (TOL64, 1e-6)
+    assert col_rel_err(Js, ref, floor=fl) <= tol
+    assert vec_rel_err(qdds, oracle.fd(r, q64, qd64, tau64)) <= tol
+    # both kernels meet the bar; they differ only in rounding order
+    assert col_rel_err(Jg, ref, floor=fl) <= tol
+    assert col_rel_err(Js, Jg, floor=fl) <= tol
+    assert vec_rel_err(qdds, qddg) <= tol
 
 
 @pytest.mark.parametrize("key", WORKLOAD)
