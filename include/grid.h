@@ -188,6 +188,69 @@ grid_status grid_fd_vjp(const grid_model* model, int N, const float* q, const fl
                         void* stream);
 
 /* FP64 twins: same operations and layouts, the whole path in double. */
+/*
+ * grid_grad_fd_ex -- grid_grad_fd that also writes M^-1 = dqdd/dtau (Sec. IV-B,
+ * fifth item), which the kernel forms on the way: Minv [N][n][n] full
+ * symmetric, or NULL (then identical to grid_grad_fd).
+ */
+grid_status grid_grad_fd_ex(const grid_model* model, int N, const float* q, const float* qd,
+                            const float* tau, float* J, float* qdd, float* Minv, void* stream);
+grid_status grid_grad_fd_ex_f64(const grid_model* model, int N, const double* q, const double* qd,
+                                const double* tau, double* J, double* qdd, double* Minv, void* stream);
+
+/*
+ * Trajectory-optimisation step (Sec. V-B: the all-GPU loop the library is built
+ * for). Knot arrays are [B][H+1][n] (trajectory, knot point, joint): the
+ * B (H+1) knot points of a batch are one contiguous set that grid_grad_fd_ex
+ * differentiates in one call. Device (or pinned host) pointers; asynchronous
+ * on `stream`; no allocation.
+ *
+ * grid_rollout -- semi-implicit Euler through forward dynamics:
+ *   qdd_k = FD(q_k, qd_k, u_k), qd_{k+1} = qd_k + dt qdd_k, q_{k+1} = q_k + dt qd_{k+1}
+ *   for k = 0 .. H-1 from q0, qd0 [B][n]. Without a policy (K = NULL) u_k = U_k;
+ *   with one, u_k = U_k + alpha kff_k + K_k (x_k - xnom_k), x = (q, qd), with
+ *   K [B][H+1][n][2n], kff [B][H+1][n] (from grid_riccati) and the nominal states
+ *   Qnom, QDnom [B][H+1][n]. Outputs Q, QD [B][H+1][n] (knot 0 = q0, qd0) and,
+ *   if Uout != NULL, the applied controls [B][H+1][n] (entry H set to 0).
+ *   U's entry H is not read.
+ *
+ * grid_riccati -- the iLQR backward pass (DDP without second-order dynamics
+ *   terms; Li and Todorov 2004, Tassa et al. 2012) for the tracking cost
+ *     sum_{k<H} 1/2 (x_k - r_k)^T diag(wq) (x_k - r_k) + 1/2 u_k^T diag(wr) u_k
+ *     + 1/2 (x_H - r_H)^T diag(wf) (x_H - r_H),   r = (Qref, QDref) [B][H+1][n]
+ *   about the nominal trajectory (Q, QD, U). The step Jacobians come from J and
+ *   Minv [B][H+1][n][2n], [B][H+1][n][n] (grid_grad_fd_ex at the nominal knots):
+ *     A = [[1 + dt^2 Jq, dt (1 + dt Jv)], [dt Jq, 1 + dt Jv]],  B = [[dt^2 Minv], [dt Minv]].
+ *   From V_x = diag(wf)(x_H - r_H), V_xx = diag(wf), for k = H-1 .. 0:
+ *     Q_x = l_x + A^T V_x, Q_u = l_u + B^T V_x, Q_xx = l_xx + A^T V_xx A,
+ *     Q_uu = l_uu + B^T V_xx B + mu 1, Q_ux = B^T V_xx A,
+ *     K_k = -Q_uu^-1 Q_ux, k_k = -Q_uu^-1 Q_u,
+ *     V_x = Q_x + K^T Q_uu k + K^T Q_u + Q_ux^T k,
+ *     V_xx = sym(Q_xx + K^T Q_uu K + K^T Q_ux + Q_ux^T K).
+ *   Outputs K [B][H+1][n][2n] and kff [B][H+1][n] (entry H set to 0) and
+ *   dV [B][2] = (sum k^T Q_u, sum 1/2 k^T Q_uu k): the predicted cost change of a
+ *   step alpha is alpha dV[0] + alpha^2 dV[1]. A trajectory whose Q_uu is not
+ *   positive definite at some step gets dV = NaN (raise mu). Weights wq, wf [2n]
+ *   and wr [n] in device memory. Requires n <= 16 (GRID_E_ARG otherwise).
+ */
+grid_status grid_rollout(const grid_model* model, int B, int H, float dt, const float* q0,
+                         const float* qd0, const float* U, const float* K, const float* kff,
+                         const float* Qnom, const float* QDnom, float alpha, float* Q, float* QD,
+                         float* Uout, void* stream);
+grid_status grid_rollout_f64(const grid_model* model, int B, int H, double dt, const double* q0,
+                             const double* qd0, const double* U, const double* K, const double* kff,
+                             const double* Qnom, const double* QDnom, double alpha, double* Q,
+                             double* QD, double* Uout, void* stream);
+grid_status grid_riccati(const grid_model* model, int B, int H, float dt, const float* Q,
+                         const float* QD, const float* U, const float* J, const float* Minv,
+                         const float* Qref, const float* QDref, const float* wq, const float* wr,
+                         const float* wf, float mu, float* K, float* kff, float* dV, void* stream);
+grid_status grid_riccati_f64(const grid_model* model, int B, int H, double dt, const double* Q,
+                             const double* QD, const double* U, const double* J, const double* Minv,
+                             const double* Qref, const double* QDref, const double* wq,
+                             const double* wr, const double* wf, double mu, double* K, double* kff,
+                             double* dV, void* stream);
+
 grid_status grid_rnea_f64(const grid_model* model, int N, const double* q, const double* qd,
                           const double* qdd, double* tau, void* stream);
 grid_status grid_minv_f64(const grid_model* model, int N, const double* q, double* Minv, void* stream);

@@ -173,6 +173,69 @@ class Model:
                      _ptr(qdd_out), self._stream())
         return (J, qdd_out) if return_qdd else J
 
+    def grad_fd_minv(self, q, qd, tau, out=None, minv_out=None):
+        """(J, M^-1): the gradient of FD [N, n, 2n] and M^-1 = dqdd/dtau [N, n, n]
+        from one kernel (grid_grad_fd_ex)."""
+        N, dt, (q, qd, tau) = self._state(q, qd, tau)
+        J = out if out is not None else self._empty((N, self.n, 2 * self.n), dt, q)
+        Mi = minv_out if minv_out is not None else self._empty((N, self.n, self.n), dt, q)
+        _native.call(self._fn("grid_grad_fd_ex", dt), self._h, N, _ptr(q), _ptr(qd), _ptr(tau), _ptr(J), None,
+                     _ptr(Mi), self._stream())
+        return J, Mi
+
+    # ------------------------------------------------------------ trajectories
+    def _traj(self, *ts):
+        """Trajectory tensors [B, H+1, n], contiguous, one dtype and device."""
+        B, K1 = ts[0].shape[0], ts[0].shape[1]
+        for t in ts:
+            if t is None:
+                continue
+            if t.shape != (B, K1, self.n) or t.dtype != ts[0].dtype or not t.is_contiguous():
+                raise ValueError(f"trajectory tensors must be contiguous [B, H+1, n={self.n}] of one dtype")
+        return B, K1 - 1, ts[0].dtype
+
+    def rollout(self, q0, qd0, U, dt, policy=None, out=None):
+        """Semi-implicit Euler rollout through FD (grid_rollout). q0, qd0 [B, n];
+        U [B, H+1, n] (entry H unused). policy = (K, kff, Qnom, QDnom, alpha) from
+        riccati() and the nominal trajectory, or None. Returns Q, QD and the
+        applied controls, each [B, H+1, n]."""
+        B, H, dtp = self._traj(U)
+        Q, QD, Ua = out if out is not None else tuple(torch.empty_like(U) for _ in range(3))
+        K = kff = Qn = QDn = None
+        alpha = 1.0
+        if policy is not None:
+            K, kff, Qn, QDn, alpha = policy
+        _native.call(self._fn("grid_rollout", dtp), self._h, B, H, float(dt), _ptr(q0.contiguous()),
+                     _ptr(qd0.contiguous()), _ptr(U), _ptr(K), _ptr(kff), _ptr(Qn), _ptr(QDn), float(alpha),
+                     _ptr(Q), _ptr(QD), _ptr(Ua), self._stream())
+        return Q, QD, Ua
+
+    def riccati(self, Q, QD, U, J, Minv, Qref, QDref, wq, wr, wf, dt, mu=0.0):
+        """iLQR backward pass about the nominal trajectory (grid_riccati). J, Minv
+        from grad_fd_minv at the nominal knot points ([B (H+1), n, 2n] and
+        [B (H+1), n, n]); weights wq, wf [2n], wr [n] on the device. Returns
+        K [B, H+1, n, 2n], kff [B, H+1, n] and dV [B, 2]."""
+        B, H, dtp = self._traj(Q, QD, U, Qref, QDref)
+        n = self.n
+        K = torch.empty((B, H + 1, n, 2 * n), dtype=dtp, device=Q.device)
+        kff = torch.empty((B, H + 1, n), dtype=dtp, device=Q.device)
+        dV = torch.empty((B, 2), dtype=dtp, device=Q.device)
+        _native.call(self._fn("grid_riccati", dtp), self._h, B, H, float(dt), _ptr(Q), _ptr(QD), _ptr(U),
+                     _ptr(J.contiguous()), _ptr(Minv.contiguous()), _ptr(Qref), _ptr(QDref), _ptr(wq), _ptr(wr),
+                     _ptr(wf), float(mu), _ptr(K), _ptr(kff), _ptr(dV), self._stream())
+        return K, kff, dV
+
+    def ilqr_iteration(self, q0, qd0, U, Qref, QDref, wq, wr, wf, dt, mu=0.0, alpha=1.0):
+        """One iLQR iteration on the device with no host transfer: rollout of the
+        nominal controls, the gradient of FD and M^-1 at every knot point, the
+        backward pass, and the forward pass under the new policy. Returns the new
+        (Q, QD, U) [B, H+1, n] and dV [B, 2] of the step taken."""
+        Q, QD, _ = self.rollout(q0, qd0, U, dt)
+        J, Mi = self.grad_fd_minv(Q, QD, U)
+        K, kff, dV = self.riccati(Q, QD, U, J, Mi, Qref, QDref, wq, wr, wf, dt, mu)
+        Qn, QDn, Un = self.rollout(q0, qd0, U, dt, policy=(K, kff, Q, QD, alpha))
+        return Qn, QDn, Un, dV
+
     def fd_vjp(self, q, qd, tau, gbar, out=None):
         """Vector-Jacobian product through FD for gbar = dL/dqdd:
         returns (dL/dq, dL/dqd, dL/dtau), each [N, n]. Forward intermediates are

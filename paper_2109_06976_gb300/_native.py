@@ -36,6 +36,12 @@ SIGNATURES = {
     "grid_grad_rnea": [_P, _I, _P, _P, _P, _P, _P],
     "grid_grad_rnea_f64": [_P, _I, _P, _P, _P, _P, _P],
     "grid_fd_vjp_f64": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
+    "grid_grad_fd_ex": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "grid_grad_fd_ex_f64": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "grid_rollout": [_P, _I, _I, ctypes.c_float] + [_P] * 7 + [ctypes.c_float] + [_P] * 4,
+    "grid_rollout_f64": [_P, _I, _I, ctypes.c_double] + [_P] * 7 + [ctypes.c_double] + [_P] * 4,
+    "grid_riccati": [_P, _I, _I, ctypes.c_float] + [_P] * 10 + [ctypes.c_float] + [_P] * 4,
+    "grid_riccati_f64": [_P, _I, _I, ctypes.c_double] + [_P] * 10 + [ctypes.c_double] + [_P] * 4,
     "grid_server_create": [_P, _I, _I, ctypes.c_size_t, ctypes.POINTER(_P)],
     "grid_server_set_idle_timeout": [_P, ctypes.c_double],
     "grid_server_start": [_P, _P],

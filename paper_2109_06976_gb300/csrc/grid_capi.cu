@@ -184,6 +184,18 @@ grid_status grid_grad_fd(const grid_model* m, int N, const float* q, const float
   if (s != GRID_OK) return s;
   return run<float, MODE_GRAD>(m, N, q, qd, tau, nullptr, J, qdd, nullptr, stream);
 }
+grid_status grid_grad_fd_ex(const grid_model* m, int N, const float* q, const float* qd, const float* tau,
+                            float* J, float* qdd, float* Minv, void* stream) {
+  grid_status s = check_args<float>(m, N, {q, qd, tau, J}, {qdd, Minv});
+  if (s != GRID_OK) return s;
+  return run<float, MODE_GRAD>(m, N, q, qd, tau, nullptr, J, qdd, Minv, stream);
+}
+grid_status grid_grad_fd_ex_f64(const grid_model* m, int N, const double* q, const double* qd,
+                                const double* tau, double* J, double* qdd, double* Minv, void* stream) {
+  grid_status s = check_args<double>(m, N, {q, qd, tau, J}, {qdd, Minv});
+  if (s != GRID_OK) return s;
+  return run<double, MODE_GRAD>(m, N, q, qd, tau, nullptr, J, qdd, Minv, stream);
+}
 grid_status grid_rnea_f64(const grid_model* m, int N, const double* q, const double* qd,
                           const double* qdd, double* tau, void* stream) {
   grid_status s = check_args<double>(m, N, {q, qd, tau}, {qdd});

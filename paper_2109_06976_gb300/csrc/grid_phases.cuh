@@ -960,6 +960,13 @@ __device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const 
         out2[(size_t)k0 * n + e] = Wwarp[kk * L.stride + L.CB + r];
       }
     }
+    if (out3 && g < nvalid) {                       // M^-1 in caller order (full symmetric)
+      S* Mo = out3 + (size_t)(k0 + g) * n * n;
+      for (int e = c.l; e < n * n; e += T) {
+        const int i = e / n, j = e % n;
+        Mo[tp.perm(i) * n + tp.perm(j)] = W[L.MINV + i * L.MS + j];
+      }
+    }
     SYNC();
   } else if constexpr (MODE == MODE_VJP) {
     S* OS = W + L.UNION + L.JS;

@@ -1,0 +1,476 @@
+// Trajectory-optimisation step on the device: a rollout through forward
+// dynamics (optionally under a feedback policy) and the iLQR backward pass,
+// whose step Jacobians come from the analytical gradient of FD and M^-1
+// (grid_grad_fd_ex). Sec. V-B names the all-GPU trajectory-optimisation loop
+// as the use GRiD targets; the recursions are the textbook forms (Li and
+// Todorov 2004; Tassa, Erez and Todorov 2012).
+//
+// Knot arrays are [B][H+1][n]: trajectory b, knot point k, joint i, so the
+// B (H+1) knot points of a batch are one contiguous set for grid_grad_fd_ex.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <initializer_list>
+#include <type_traits>
+
+#include "grid_launch.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- rollout
+// qdd_k = FD(q_k, qd_k, u_k), qd_{k+1} = qd_k + dt qdd_k, q_{k+1} = q_k + dt qd_{k+1};
+// with a policy u_k = U_k + alpha kff_k + K_k (x_k - xnom_k). One knot slot of
+// a warp per trajectory (T lanes), the H steps in sequence; the state stays in
+// the slot's workspace between steps.
+template <class S, int T, int CPL, bool MIXED>
+__global__ void __launch_bounds__(128) rollout_kernel(
+    const ModelDev<S>* __restrict__ gm, int B, int H, S dt, const S* __restrict__ q0,
+    const S* __restrict__ qd0, const S* __restrict__ U, const S* __restrict__ K, const S* __restrict__ kff,
+    const S* __restrict__ Qn, const S* __restrict__ QDn, S alpha, S* __restrict__ Q, S* __restrict__ QD,
+    S* __restrict__ Uout) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int head = align16(model_head_bytes<S>());
+  {
+    const int4* src = reinterpret_cast<const int4*>(gm);
+    int4* dst = reinterpret_cast<int4*>(smem);
+    for (int i = threadIdx.x; i < head / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  using P = typename std::conditional<MIXED, double, S>::type;
+  using Tp = RtTopo<S, MODE_FD>;
+  const ModelDev<S>& M = *reinterpret_cast<const ModelDev<S>*>(smem);
+  const Tp tp(M);
+  const KnotLayout& L = tp.layout();
+  const int n = tp.n();
+  constexpr int G = 32 / T;
+  const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int g = lane32 / T, l = lane32 % T;
+  S* W = reinterpret_cast<S*>(smem + head) + (warp * G + g) * L.stride;
+  const Ctx<S, Tp> c{M, gm, tp, W, l, lane32};
+  const size_t knots = (size_t)H + 1;
+  const int ntiles = (B + G - 1) / G;
+  for (int tile = blockIdx.x * wpb + warp; tile < ntiles; tile += gridDim.x * wpb) {
+    const int b = tile * G + g;
+    const bool ok = b < B;                     // padding slots compute on zeros and store nothing
+    const size_t k0 = (size_t)(ok ? b : 0) * knots;
+    for (int i = l; i < n; i += T) {
+      const S qv = ok ? q0[(size_t)b * n + i] : S(0);
+      const S qdv = ok ? qd0[(size_t)b * n + i] : S(0);
+      W[L.Q + i] = qv;
+      W[L.QD + i] = qdv;
+      if (ok) { Q[k0 * n + i] = qv; QD[k0 * n + i] = qdv; }
+    }
+    SYNC();
+    for (int k = 0; k < H; ++k) {
+      const size_t kb = k0 + k;
+      for (int i = l; i < n; i += T) {       // control of step k (caller order)
+        S u = ok ? U[kb * n + i] : S(0);
+        if (K && ok) {
+          const S* Kr = K + (kb * n + i) * 2 * n;
+          S acc = alpha * kff[kb * n + i];
+          for (int j = 0; j < n; ++j)
+            acc += Kr[j] * (W[L.Q + j] - Qn[kb * n + j]) + Kr[n + j] * (W[L.QD + j] - QDn[kb * n + j]);
+          u += acc;
+        }
+        W[L.TAU + i] = u;
+        if (ok && Uout) Uout[kb * n + i] = u;
+      }
+      SYNC();
+      ph_transforms<S, T>(c);
+      ph_minv<S, P, T, CPL, true>(c);
+      ph_rnea_bodies<S, T>(c, -1);
+      ph_joint_forces<S, T>(c, L.UNION + L.F, L.CB);
+      ph_fd<S, T>(c);
+      for (int i = l; i < n; i += T) {       // semi-implicit Euler; qdd is in internal order
+        const int ci = tp.perm(i);
+        const S qd1 = W[L.QD + ci] + dt * W[L.QDD + i];
+        const S q1 = W[L.Q + ci] + dt * qd1;
+        W[L.QD + ci] = qd1;
+        W[L.Q + ci] = q1;
+        if (ok) { Q[(kb + 1) * n + ci] = q1; QD[(kb + 1) * n + ci] = qd1; }
+      }
+      SYNC();
+    }
+    if (ok && Uout)
+      for (int i = l; i < n; i += T) Uout[(k0 + H) * n + i] = S(0);
+    SYNC();
+  }
+}
+
+// ---------------------------------------------------------------- iLQR backward pass
+// One warp per trajectory; m = 2n state components, n controls. Matrices live
+// in the warp's shared-memory slice, row-major; lanes run over entries.
+struct RicLayout {
+  int Vxx, Vn, A, VA, Qxx, Bm, VB, Quu, Lc, Qux, Kk, QK, Vx, Qx, Qu, kk, Qk, lx, lu, stride;
+};
+
+GRID_HD inline RicLayout ric_layout(int n, int ssize) {
+  RicLayout R{};
+  const int m = 2 * n;
+  int o = 0;
+  auto take = [&](int cnt) { int r = o; o += (cnt + 3) & ~3; return r; };
+  R.Vxx = take(m * m); R.Vn = take(m * m); R.A = take(m * m); R.VA = take(m * m); R.Qxx = take(m * m);
+  R.Bm = take(m * n); R.VB = take(m * n); R.Quu = take(n * n); R.Lc = take(n * n); R.Qux = take(n * m);
+  R.Kk = take(n * m); R.QK = take(n * m);
+  R.Vx = take(m); R.Qx = take(m); R.Qu = take(n); R.kk = take(n); R.Qk = take(n); R.lx = take(m); R.lu = take(n);
+  R.stride = o + (32 / ssize);
+  return R;
+}
+
+template <class S>
+__global__ void __launch_bounds__(128) riccati_kernel(
+    int n, int B, int H, S dt, const S* __restrict__ Q, const S* __restrict__ QD, const S* __restrict__ U,
+    const S* __restrict__ J, const S* __restrict__ Minv, const S* __restrict__ Qr, const S* __restrict__ QDr,
+    const S* __restrict__ wq, const S* __restrict__ wr, const S* __restrict__ wf, S mu, S* __restrict__ Ko,
+    S* __restrict__ kffo, S* __restrict__ dV) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const RicLayout R = ric_layout(n, (int)sizeof(S));
+  const int m = 2 * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  S* Wb = reinterpret_cast<S*>(smem) + warp * R.stride;
+  S* Vxx = Wb + R.Vxx; S* Vn = Wb + R.Vn; S* A = Wb + R.A; S* VA = Wb + R.VA; S* Qxx = Wb + R.Qxx;
+  S* Bm = Wb + R.Bm; S* VB = Wb + R.VB; S* Quu = Wb + R.Quu; S* Lc = Wb + R.Lc; S* Qux = Wb + R.Qux;
+  S* Kk = Wb + R.Kk; S* QK = Wb + R.QK; S* Vx = Wb + R.Vx; S* Qx = Wb + R.Qx; S* Qu = Wb + R.Qu;
+  S* kk = Wb + R.kk; S* Qk = Wb + R.Qk; S* lx = Wb + R.lx; S* lu = Wb + R.lu;
+  const size_t knots = (size_t)H + 1;
+  for (int b = blockIdx.x * wpb + warp; b < B; b += gridDim.x * wpb) {
+    const size_t kH = (size_t)b * knots + H;
+    // terminal cost: V_x = W_f (x_H - r_H), V_xx = W_f
+    for (int e = lane; e < m * m; e += 32) Vxx[e] = (e / m == e % m) ? wf[e % m] : S(0);
+    for (int i = lane; i < m; i += 32) {
+      const S x = i < n ? Q[kH * n + i] : QD[kH * n + i - n];
+      const S r = i < n ? Qr[kH * n + i] : QDr[kH * n + i - n];
+      Vx[i] = wf[i] * (x - r);
+    }
+    S dv0 = S(0), dv1 = S(0);
+    bool pd = true;
+    __syncwarp();
+    for (int k = H - 1; k >= 0; --k) {
+      const size_t kb = (size_t)b * knots + k;
+      // step Jacobians: rows n..2n-1 (qd'), then rows 0..n-1 (q' = q + dt qd')
+      const S* Jk = J + kb * n * m;
+      const S* Mk = Minv + kb * n * n;
+      for (int e = lane; e < n * m; e += 32) {
+        const int i = e / m, j = e % m;
+        A[(n + i) * m + j] = dt * Jk[i * m + j] + ((j == n + i) ? S(1) : S(0));
+      }
+      for (int e = lane; e < n * n; e += 32) {
+        const int i = e / n, j = e % n;
+        Bm[(n + i) * n + j] = dt * Mk[i * n + j];
+      }
+      for (int i = lane; i < m; i += 32) {
+        const S x = i < n ? Q[kb * n + i] : QD[kb * n + i - n];
+        const S r = i < n ? Qr[kb * n + i] : QDr[kb * n + i - n];
+        lx[i] = wq[i] * (x - r);
+      }
+      for (int i = lane; i < n; i += 32) lu[i] = wr[i] * U[kb * n + i];
+      __syncwarp();
+      for (int e = lane; e < n * m; e += 32) {
+        const int i = e / m, j = e % m;
+        A[i * m + j] = ((j == i) ? S(1) : S(0)) + dt * A[(n + i) * m + j];
+      }
+      for (int e = lane; e < n * n; e += 32) Bm[e] = dt * Bm[n * n + e];
+      __syncwarp();
+      // V_xx A and V_xx B
+      for (int e = lane; e < m * m; e += 32) {
+        const int r = e / m, cc = e % m;
+        S s = S(0);
+        for (int t = 0; t < m; ++t) s += Vxx[r * m + t] * A[t * m + cc];
+        VA[e] = s;
+      }
+      for (int e = lane; e < m * n; e += 32) {
+        const int r = e / n, cc = e % n;
+        S s = S(0);
+        for (int t = 0; t < m; ++t) s += Vxx[r * m + t] * Bm[t * n + cc];
+        VB[e] = s;
+      }
+      __syncwarp();
+      // Q terms
+      for (int e = lane; e < m * m; e += 32) {
+        const int r = e / m, cc = e % m;
+        S s = (r == cc) ? wq[r] : S(0);
+        for (int t = 0; t < m; ++t) s += A[t * m + r] * VA[t * m + cc];
+        Qxx[e] = s;
+      }
+      for (int e = lane; e < n * n; e += 32) {
+        const int r = e / n, cc = e % n;
+        S s = (r == cc) ? wr[r] + mu : S(0);
+        for (int t = 0; t < m; ++t) s += Bm[t * n + r] * VB[t * n + cc];
+        Quu[e] = s;
+      }
+      for (int e = lane; e < n * m; e += 32) {
+        const int r = e / m, cc = e % m;
+        S s = S(0);
+        for (int t = 0; t < m; ++t) s += Bm[t * n + r] * VA[t * m + cc];
+        Qux[e] = s;
+      }
+      for (int i = lane; i < m; i += 32) {
+        S s = lx[i];
+        for (int t = 0; t < m; ++t) s += A[t * m + i] * Vx[t];
+        Qx[i] = s;
+      }
+      for (int i = lane; i < n; i += 32) {
+        S s = lu[i];
+        for (int t = 0; t < m; ++t) s += Bm[t * n + i] * Vx[t];
+        Qu[i] = s;
+      }
+      __syncwarp();
+      // Cholesky Q_uu = L L^T (one lane; n <= 16)
+      if (lane == 0) {
+        for (int j = 0; j < n; ++j) {
+          S d = Quu[j * n + j];
+          for (int t = 0; t < j; ++t) d -= Lc[j * n + t] * Lc[j * n + t];
+          if (!(d > S(0))) { pd = false; d = S(1); }
+          const S ljj = sqrt(d);
+          Lc[j * n + j] = ljj;
+          for (int i = j + 1; i < n; ++i) {
+            S s = Quu[i * n + j];
+            for (int t = 0; t < j; ++t) s -= Lc[i * n + t] * Lc[j * n + t];
+            Lc[i * n + j] = s / ljj;
+          }
+        }
+      }
+      __syncwarp();
+      // K = -Q_uu^-1 Q_ux (columns 0..m-1), k = -Q_uu^-1 Q_u (column m): one lane per column
+      for (int cc = lane; cc <= m; cc += 32) {
+        S y[16];
+        for (int i = 0; i < n; ++i) {
+          S s = cc < m ? Qux[i * m + cc] : Qu[i];
+          for (int t = 0; t < i; ++t) s -= Lc[i * n + t] * y[t];
+          y[i] = s / Lc[i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+          S s = y[i];
+          for (int t = i + 1; t < n; ++t) s -= Lc[t * n + i] * y[t];
+          y[i] = s / Lc[i * n + i];
+        }
+        for (int i = 0; i < n; ++i) {
+          if (cc < m) Kk[i * m + cc] = -y[i];
+          else kk[i] = -y[i];
+        }
+      }
+      __syncwarp();
+      // Q_uu K and Q_uu k
+      for (int e = lane; e < n * m; e += 32) {
+        const int r = e / m, cc = e % m;
+        S s = S(0);
+        for (int t = 0; t < n; ++t) s += Quu[r * n + t] * Kk[t * m + cc];
+        QK[e] = s;
+      }
+      for (int i = lane; i < n; i += 32) {
+        S s = S(0);
+        for (int t = 0; t < n; ++t) s += Quu[i * n + t] * kk[t];
+        Qk[i] = s;
+      }
+      __syncwarp();
+      // V_x = Q_x + K^T Q_uu k + K^T Q_u + Q_ux^T k
+      for (int i = lane; i < m; i += 32) {
+        S s = Qx[i];
+        for (int t = 0; t < n; ++t) s += Kk[t * m + i] * Qk[t] + Kk[t * m + i] * Qu[t] + Qux[t * m + i] * kk[t];
+        Vx[i] = s;
+      }
+      // V_xx = Q_xx + K^T Q_uu K + K^T Q_ux + Q_ux^T K
+      for (int e = lane; e < m * m; e += 32) {
+        const int r = e / m, cc = e % m;
+        S s = Qxx[e];
+        for (int t = 0; t < n; ++t)
+          s += Kk[t * m + r] * QK[t * m + cc] + Kk[t * m + r] * Qux[t * m + cc] + Qux[t * m + r] * Kk[t * m + cc];
+        Vn[e] = s;
+      }
+      if (lane == 0) {
+        S a = S(0), q2 = S(0);
+        for (int t = 0; t < n; ++t) { a += kk[t] * Qu[t]; q2 += kk[t] * Qk[t]; }
+        dv0 += a;
+        dv1 += S(0.5) * q2;
+      }
+      for (int e = lane; e < n * m; e += 32) Ko[kb * n * m + e] = Kk[e];
+      for (int i = lane; i < n; i += 32) kffo[kb * n + i] = kk[i];
+      __syncwarp();
+      for (int e = lane; e < m * m; e += 32) {
+        const int r = e / m, cc = e % m;
+        Vxx[e] = S(0.5) * (Vn[r * m + cc] + Vn[cc * m + r]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const bool all_pd = pd;
+      dV[2 * (size_t)b] = all_pd ? dv0 : S(NAN);
+      dV[2 * (size_t)b + 1] = all_pd ? dv1 : S(NAN);
+    }
+    for (int e = lane; e < n * m; e += 32) Ko[((size_t)b * knots + H) * n * m + e] = S(0);
+    for (int i = lane; i < n; i += 32) kffo[((size_t)b * knots + H) * n + i] = S(0);
+    __syncwarp();
+  }
+}
+
+// Warps per CTA with the most resident warps (same rule as the dynamics kernels).
+template <class Kern>
+bool pick_launch(Kern kern, int dev_optin, size_t fixed, size_t per_warp, int& warps, int& per_sm) {
+  int best = 0;
+  warps = per_sm = 0;
+  for (int w = 4; w >= 1; --w) {
+    const size_t sm = fixed + w * per_warp;
+    if (sm > (size_t)dev_optin) continue;
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, 32 * w, sm);
+    if (blocks * w > best) { best = blocks * w; warps = w; per_sm = blocks; }
+  }
+  return warps > 0;
+}
+
+template <class S, int T, int CPL, bool MIXED>
+grid_status launch_rollout(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int B, int H, S dt,
+                           const S* q0, const S* qd0, const S* U, const S* K, const S* kff, const S* Qn,
+                           const S* QDn, S alpha, S* Q, S* QD, S* Uout, cudaStream_t st) {
+  auto kern = rollout_kernel<S, T, CPL, MIXED>;
+  const DevInfo di = dev_info(m->device);
+  static std::atomic<int> opted{0};
+  if (!opted.load()) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin) != cudaSuccess) {
+      grid_set_error("cudaFuncSetAttribute failed");
+      return GRID_E_CUDA;
+    }
+    opted.store(1);
+  }
+  constexpr int G = 32 / T;
+  const size_t fixed = align16(model_head_bytes<S>());
+  const size_t per_warp = (size_t)G * hm->LS.stride * sizeof(S);
+  int warps, per_sm;
+  if (!pick_launch(kern, di.smem_optin, fixed, per_warp, warps, per_sm)) {
+    grid_set_error("rollout workspace needs %zu B of shared memory per warp; use more lanes", fixed + per_warp);
+    return GRID_E_ARG;
+  }
+  const long tiles = (B + G - 1) / G;
+  const int grid = (int)std::min<long>((tiles + warps - 1) / warps, (long)di.nsm * per_sm);
+  kern<<<grid, 32 * warps, fixed + warps * per_warp, st>>>(dm, B, H, dt, q0, qd0, U, K, kff, Qn, QDn, alpha, Q, QD,
+                                                           Uout);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    grid_set_error("rollout launch: %s", cudaGetErrorString(err));
+    return GRID_E_CUDA;
+  }
+  return GRID_OK;
+}
+
+template <class S, bool MIXED>
+grid_status rollout_dispatch(const grid_model* m, int B, int H, S dt, const S* q0, const S* qd0, const S* U,
+                             const S* K, const S* kff, const S* Qn, const S* QDn, S alpha, S* Q, S* QD, S* Uout,
+                             cudaStream_t st) {
+  const ModelDev<S>* hm;
+  const ModelDev<S>* dm;
+  if constexpr (std::is_same<S, float>::value) { hm = m->host_f; dm = m->dev_f; }
+  else { hm = m->host_d; dm = m->dev_d; }
+  const int n = hm->n;
+  int T = m->lanes_opt;
+  if (T == 0) T = n <= 12 ? 8 : 16;
+  const int cpl = (n + T - 1) / T;
+#define GRID_RL(TT, CC) return launch_rollout<S, TT, CC, MIXED>(m, hm, dm, B, H, dt, q0, qd0, U, K, kff, Qn, QDn, \
+                                                                  alpha, Q, QD, Uout, st)
+  if (T == 8) { if (cpl <= 1) GRID_RL(8, 1); if (cpl <= 2) GRID_RL(8, 2); GRID_RL(8, 4); }
+  if (T == 16) { if (cpl <= 1) GRID_RL(16, 1); GRID_RL(16, 2); }
+  if (T == 32) GRID_RL(32, 1);
+#undef GRID_RL
+  grid_set_error("lanes option %d not in {0, 8, 16, 32}", T);
+  return GRID_E_ARG;
+}
+
+template <class S>
+grid_status check_traj(const grid_model* m, int B, int H, std::initializer_list<const void*> must,
+                       std::initializer_list<const void*> may) {
+  if (!m) { grid_set_error("null model"); return GRID_E_ARG; }
+  if (B < 0 || H < 1) { grid_set_error("B = %d, H = %d (need B >= 0, H >= 1)", B, H); return GRID_E_ARG; }
+  for (const void* p : must) {
+    if (!p && B > 0) { grid_set_error("null trajectory pointer"); return GRID_E_ARG; }
+    if (((uintptr_t)p) % sizeof(S)) { grid_set_error("pointer not %zu-byte aligned", sizeof(S)); return GRID_E_ALIGN; }
+  }
+  for (const void* p : may)
+    if (((uintptr_t)p) % sizeof(S)) { grid_set_error("pointer not %zu-byte aligned", sizeof(S)); return GRID_E_ALIGN; }
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != m->device) {
+    grid_set_error("current device %d differs from the model's device %d", dev, m->device);
+    return GRID_E_ARG;
+  }
+  return GRID_OK;
+}
+
+template <class S>
+grid_status rollout(const grid_model* m, int B, int H, S dt, const S* q0, const S* qd0, const S* U, const S* K,
+                    const S* kff, const S* Qn, const S* QDn, S alpha, S* Q, S* QD, S* Uout, void* stream) {
+  grid_status s = check_traj<S>(m, B, H, {q0, qd0, U, Q, QD}, {K, kff, Qn, QDn, Uout});
+  if (s != GRID_OK) return s;
+  if (K && (!kff || !Qn || !QDn)) { grid_set_error("a policy needs K, kff and the nominal states"); return GRID_E_ARG; }
+  if (B == 0) return GRID_OK;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (std::is_same<S, float>::value && m->prec == GRID_MIXED)
+    return rollout_dispatch<S, true>(m, B, H, dt, q0, qd0, U, K, kff, Qn, QDn, alpha, Q, QD, Uout, st);
+  return rollout_dispatch<S, false>(m, B, H, dt, q0, qd0, U, K, kff, Qn, QDn, alpha, Q, QD, Uout, st);
+}
+
+template <class S>
+grid_status riccati(const grid_model* m, int B, int H, S dt, const S* Q, const S* QD, const S* U, const S* J,
+                    const S* Minv, const S* Qr, const S* QDr, const S* wq, const S* wr, const S* wf, S mu, S* K,
+                    S* kff, S* dV, void* stream) {
+  grid_status s = check_traj<S>(m, B, H, {Q, QD, U, J, Minv, Qr, QDr, wq, wr, wf, K, kff, dV}, {});
+  if (s != GRID_OK) return s;
+  const int n = m->n;
+  if (n > 16) { grid_set_error("the Riccati pass supports n <= 16 (n = %d)", n); return GRID_E_ARG; }
+  if (B == 0) return GRID_OK;
+  auto kern = riccati_kernel<S>;
+  const DevInfo di = dev_info(m->device);
+  static std::atomic<int> opted{0};
+  if (!opted.load()) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin) != cudaSuccess) {
+      grid_set_error("cudaFuncSetAttribute failed");
+      return GRID_E_CUDA;
+    }
+    opted.store(1);
+  }
+  const size_t per_warp = (size_t)ric_layout(n, (int)sizeof(S)).stride * sizeof(S);
+  int warps, per_sm;
+  if (!pick_launch(kern, di.smem_optin, 0, per_warp, warps, per_sm)) {
+    grid_set_error("Riccati workspace of %zu B exceeds shared memory", per_warp);
+    return GRID_E_ARG;
+  }
+  const int grid = (int)std::min<long>(((long)B + warps - 1) / warps, (long)di.nsm * per_sm);
+  kern<<<grid, 32 * warps, warps * per_warp, reinterpret_cast<cudaStream_t>(stream)>>>(
+      n, B, H, dt, Q, QD, U, J, Minv, Qr, QDr, wq, wr, wf, mu, K, kff, dV);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    grid_set_error("Riccati launch: %s", cudaGetErrorString(err));
+    return GRID_E_CUDA;
+  }
+  return GRID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+grid_status grid_rollout(const grid_model* m, int B, int H, float dt, const float* q0, const float* qd0,
+                         const float* U, const float* K, const float* kff, const float* Qnom, const float* QDnom,
+                         float alpha, float* Q, float* QD, float* Uout, void* stream) {
+  return rollout<float>(m, B, H, dt, q0, qd0, U, K, kff, Qnom, QDnom, alpha, Q, QD, Uout, stream);
+}
+grid_status grid_rollout_f64(const grid_model* m, int B, int H, double dt, const double* q0, const double* qd0,
+                             const double* U, const double* K, const double* kff, const double* Qnom,
+                             const double* QDnom, double alpha, double* Q, double* QD, double* Uout, void* stream) {
+  return rollout<double>(m, B, H, dt, q0, qd0, U, K, kff, Qnom, QDnom, alpha, Q, QD, Uout, stream);
+}
+grid_status grid_riccati(const grid_model* m, int B, int H, float dt, const float* Q, const float* QD,
+                         const float* U, const float* J, const float* Minv, const float* Qref, const float* QDref,
+                         const float* wq, const float* wr, const float* wf, float mu, float* K, float* kff,
+                         float* dV, void* stream) {
+  return riccati<float>(m, B, H, dt, Q, QD, U, J, Minv, Qref, QDref, wq, wr, wf, mu, K, kff, dV, stream);
+}
+grid_status grid_riccati_f64(const grid_model* m, int B, int H, double dt, const double* Q, const double* QD,
+                             const double* U, const double* J, const double* Minv, const double* Qref,
+                             const double* QDref, const double* wq, const double* wr, const double* wf, double mu,
+                             double* K, double* kff, double* dV, void* stream) {
+  return riccati<double>(m, B, H, dt, Q, QD, U, J, Minv, Qref, QDref, wq, wr, wf, mu, K, kff, dV, stream);
+}
+
+}  // extern "C"
