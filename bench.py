@@ -172,6 +172,40 @@ def time_steps(fn, steps, warmup, stream, dist=None):
     return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
 
 
+def traj_leg(grid, model, stream, dist, B=2048, H=64, dt=0.01):
+    """One iLQR iteration on the device for B trajectories of H steps of the
+    7-DoF chain (rollout, gradient of FD and M^-1 at the B (H+1) knot points,
+    backward pass, policy rollout), FP32, inputs resident; and its parts."""
+    import numpy as np
+    import torch
+    import grid_inputs as gi
+    n = model.n
+    s = gi.Stream(4242)
+    q0, qd0, _ = (torch.from_numpy(x.astype(np.float32)).cuda() for x in gi.states(n, B, 4242))
+    U = torch.from_numpy((0.3 * s.normal((B, H + 1, n))).astype(np.float32)).cuda()
+    Qref = torch.zeros_like(U)
+    QDref = torch.zeros_like(U)
+    wq = torch.tensor([10.0] * n + [0.1] * n, device="cuda")
+    wr = torch.full((n,), 1e-3, device="cuda")
+    wf = 10.0 * wq
+    it = lambda: model.ilqr_iteration(q0, qd0, U, Qref, QDref, wq, wr, wf, dt, 1e-6, 1.0)
+    steps = 5
+    sec = time_steps(it, steps, 2, stream, dist)
+    Q, QD, _ = model.rollout(q0, qd0, U, dt)
+    J, Mi = model.grad_fd_minv(Q, QD, U)
+    parts = {
+        "rollout_ms": time_steps(lambda: model.rollout(q0, qd0, U, dt), steps, 2, stream, dist) / steps * 1e3,
+        "grad_fd_minv_ms": time_steps(lambda: model.grad_fd_minv(Q, QD, U, out=J, minv_out=Mi), steps, 2,
+                                      stream, dist) / steps * 1e3,
+        "riccati_ms": time_steps(lambda: model.riccati(Q, QD, U, J, Mi, Qref, QDref, wq, wr, wf, dt, 1e-6), steps,
+                                 2, stream, dist) / steps * 1e3,
+    }
+    return {"trajectories": B, "horizon": H, "ms_per_iteration": sec / steps * 1e3,
+            "knot_points_per_s": B * (H + 1) * steps / sec, **parts,
+            "note": "one iLQR iteration = rollout + gradient of FD and M^-1 at every knot point + "
+                    "backward pass + policy rollout, all on the device (7-DoF chain, FP32)"}
+
+
 def device_latency_us(fn, reps=200, warmup=20):
     """Median device time of one call: each call is queued behind a ~50 us
     device-side spin, so the CUDA events around it (on the launching stream)
@@ -396,6 +430,7 @@ def run_ours(args):
     lat128 = device_latency_us(lambda: model.grad_fd(q1, qd1, tau1, out=J1))
 
     lat_table = latency_table(grid) if rank == 0 else None
+    traj = traj_leg(grid, model, stream, dist) if rank == 0 and world == 1 else None
 
     serve = None
     if rank == 0 and world == 1 and args.serve_seconds > 0:
@@ -442,6 +477,7 @@ def run_ours(args):
             "latency_n1_note": "one knot point per call, compute only: median over 200 calls of the "
                                "device time between CUDA events, each call queued behind a device spin "
                                "(RNEA at qdd = tau's values; tree30 in mixed precision)",
+            "traj_step": traj,
             "serve": serve,
             "cpu_baseline": cpu,
             "clocks": clocks,
