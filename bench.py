@@ -235,9 +235,9 @@ def latency_table(grid, reps=200, warmup=20):
     import torch
     import grid_inputs as gi
     table = {}
-    for name in ("chain7", "tree12", "tree30"):
+    for name, prec in (("chain7", "fp32"), ("tree12", "fp32"), ("tree30", "fp32"), ("tree30", "mixed")):
         r = gi.robot(name)
-        m = grid.Model.from_robot(r, precision="mixed" if name == "tree30" else "fp32")
+        m = grid.Model.from_robot(r, precision=prec)
         q, qd, tau = (torch.from_numpy(x.astype(np.float32)).cuda() for x in gi.states(r.n, 1, 77))
         outs = {"rnea": torch.empty((1, r.n), device="cuda"),
                 "minv": torch.empty((1, r.n, r.n), device="cuda"),
@@ -249,7 +249,8 @@ def latency_table(grid, reps=200, warmup=20):
                  "fd": lambda: m.fd(q, qd, tau, out=outs["fd"]),
                  "grad_id": lambda: m.grad_rnea(q, qd, tau, out=outs["grad_id"]),
                  "grad_fd": lambda: m.grad_fd(q, qd, tau, out=outs["grad_fd"])}
-        table[name] = {alg: device_latency_us(fn, reps, warmup) for alg, fn in calls.items()}
+        table[name if prec == "fp32" else name + "_mixed"] = {alg: device_latency_us(fn, reps, warmup)
+                                                               for alg, fn in calls.items()}
         m.close()
     return table
 
@@ -476,7 +477,7 @@ def run_ours(args):
             "latency_n1_us": lat_table,
             "latency_n1_note": "one knot point per call, compute only: median over 200 calls of the "
                                "device time between CUDA events, each call queued behind a device spin "
-                               "(RNEA at qdd = tau's values; tree30 in mixed precision)",
+                               "(RNEA at qdd = tau's values; FP32, and the 30-DoF tree also in mixed precision)",
             "traj_step": traj,
             "serve": serve,
             "cpu_baseline": cpu,

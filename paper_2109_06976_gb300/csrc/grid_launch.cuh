@@ -173,7 +173,11 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
     if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
       return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   }
-  if (T == 0) T = n <= 12 ? 8 : 16;
+  // Default lanes: 8 up to 12 bodies, else 16 (throughput). A batch smaller
+  // than two knot points per SM is latency-bound: for more bodies than 8 lanes,
+  // one warp per knot point then shortens the parallel phases (measured for the
+  // 12- and 30-DoF trees; up to 8 bodies, 8 lanes stay faster).
+  if (T == 0) T = (n > 8 && N <= 2 * dev_info(m->device).nsm) ? 32 : (n <= 12 ? 8 : 16);
   const int cpl = (n + T - 1) / T;
   if (T == 8) {
     if (cpl <= 1) return launch_d<S, MODE, 8, 1, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);

@@ -262,59 +262,62 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     const S* r = E + 9;
     const S a[3] = {M.axis[i][0], M.axis[i][1], M.axis[i][2]};
     const bool pr = tp.prism(i);              // S_i = [0; a] instead of [a; 0]
-    S ia[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
-    S ul = S(0);
-    if (l < 6) {                              // column l of I^A_i
+    // Lanes 0..5 own column l of I^A_i; the other lanes carry zeros through the
+    // same instructions (no divergent branches, so the compiler can interleave
+    // the independent F-column and congruence work below).
+    const bool own = l < 6;
+    S ia[6];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) ia[e] = icn[e];
-      if (i > 0) ldg6(c.gM->Icol[i - 1][l], icn);
-      if (i + 1 < n && tp.parent(i + 1) == i) {
+    for (int e = 0; e < 6; ++e) ia[e] = icn[e];
+    if (i > 0) ldg6(c.gM->Icol[i - 1][own ? l : 0], icn);
+    if (i > 0 && !own) {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) ia[e] += carry[e];
-      }
-      if (br >= 0) {
-        const S* sl = BIA + 36 * br + 6 * l;  // 6-scalar rows: scalar loads
-#pragma unroll
-        for (int e = 0; e < 6; ++e) ia[e] += sl[e];
-      }
-      ul = dot_s(a, pr, ia);                  // U_l = (I^A S)_l (I^A symmetric)
-      UB[8 * i + l] = ul;
+      for (int e = 0; e < 6; ++e) icn[e] = S(0);
     }
+    if (i + 1 < n && tp.parent(i + 1) == i) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ia[e] += carry[e];
+    }
+    if (br >= 0) {
+      const S* sl = BIA + 36 * br + 6 * (own ? l : 0);   // 6-scalar rows: scalar loads
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ia[e] += own ? sl[e] : S(0);
+    }
+    const S ul = dot_s(a, pr, ia);            // U_l = (I^A S)_l (I^A symmetric)
+    if (own) UB[8 * i + l] = ul;
     S u[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) u[e] = GRID_SHFL(ul, base + e);
     const S us0 = pr ? u[3] : u[0], us1 = pr ? u[4] : u[1], us2 = pr ? u[5] : u[2];   // S^T U
     const P Dk = P(a[0]) * P(us0) + P(a[1]) * P(us1) + P(a[2]) * P(us2);
-    const P Dinv = P(1) / Dk;
+    P Dinv;
+    if constexpr (std::is_same<P, float>::value) Dinv = __frcp_rn(Dk);
+    else Dinv = __drcp_rn(Dk);
     if (l == 0) DINV[i] = Dinv;
 #pragma unroll
     for (int cc = 0; cc < CPL; ++cc) {
       const int k = l + cc * T;
-      if (k >= i && k < tp.sub_end(i)) {
-        S mik;
-        if (k == i) mik = S(Dinv);
-        else {
-          const S f0 = pr ? fb[cc][3] : fb[cc][0], f1 = pr ? fb[cc][4] : fb[cc][1],
-                  f2 = pr ? fb[cc][5] : fb[cc][2];
-          mik = S(-Dinv * (P(a[0]) * P(f0) + P(a[1]) * P(f1) + P(a[2]) * P(f2)));
-        }
-        MI[i * MS + k] = mik;
-        if (p >= 0) {
-          S w[6];
+      const bool act = k >= i && k < tp.sub_end(i);
+      const S f0 = pr ? fb[cc][3] : fb[cc][0], f1 = pr ? fb[cc][4] : fb[cc][1], f2 = pr ? fb[cc][5] : fb[cc][2];
+      const S mik = (k == i) ? S(Dinv) : S(-Dinv * (P(a[0]) * P(f0) + P(a[1]) * P(f1) + P(a[2]) * P(f2)));
+      if (act) MI[i * MS + k] = mik;
+      if (p >= 0) {
+        S w[6], fn[6];
 #pragma unroll
-          for (int e = 0; e < 6; ++e) w[e] = fb[cc][e] + u[e] * mik;
-          xt_mul(E, r, w, fb[cc]);
-        }
+        for (int e = 0; e < 6; ++e) w[e] = fb[cc][e] + u[e] * mik;
+        xt_mul(E, r, w, fn);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) fb[cc][e] = act ? fn[e] : fb[cc][e];
       }
     }
     S* CT = W + U + L.CT + 48 * (i & 1);     // alternate buffers: no second barrier needed
-    if (p >= 0 && l < 6) {
+    if (p >= 0) {
       S acol[6], cx[6];
       const P ulD = P(ul) * Dinv;
 #pragma unroll
       for (int e = 0; e < 6; ++e) acol[e] = S(P(ia[e]) - P(u[e]) * ulD);
       xt_mul(E, r, acol, cx);                 // column l of C = X^T A
-      st6(CT + 8 * l, cx);
+      if (own) st6(CT + 8 * l, cx);
     }
     SYNC();
     if (p >= 0 && l < 6) {
@@ -342,6 +345,56 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     for (int e = 0; e < 6; ++e) pc[cc][e] = S(0);
 #pragma unroll
   for (int e = 0; e < 8; ++e) skc[e] = S(0);
+  if constexpr (Tp::kChainN > 0 && Tp::kChainN < T && CPL == 1 && WITH_SK) {
+    // Serial chain with fewer bodies than lanes. At body i, lane l < i carries
+    // subspace row l (s_l^(i) = X_i s_l^(i-1)), lanes i..N-1 their P column and
+    // lane N the gravity row: one x_mul per lane, no divergent paths.
+    constexpr int NB = Tp::kChainN;
+    S* SK = W + L.SK;
+    S* GR = W + U + L.GR;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      S E[12];
+      ld12(W + L.X + 12 * i, E);
+      const S* r = E + 9;
+      const S* a = M.axis[i];
+      S Ui[6];
+      ld6(UB + 8 * i, Ui);
+      const P Dinv = DINV[i];
+      const bool row_lane = l < i || l == NB;
+      S in[6], t[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) in[e] = (i == 0 && l == NB) ? M.a0[e] : (row_lane ? skc[e] : pc[0][e]);
+      x_mul(E, r, in, t);
+      if (l >= i && l < NB) {                  // P column l
+        S mk = MI[i * MS + l];
+        if (i > 0) {
+          const P ut = (P(Ui[0]) * P(t[0]) + P(Ui[1]) * P(t[1])) + (P(Ui[2]) * P(t[2]) + P(Ui[3]) * P(t[3])) +
+                       (P(Ui[4]) * P(t[4]) + P(Ui[5]) * P(t[5]));
+          mk = S(P(mk) - Dinv * ut);
+          MI[i * MS + l] = mk;
+        }
+#pragma unroll
+        for (int e = 0; e < 6; ++e) pc[0][e] = (e < 3 ? a[e] * mk : S(0)) + (i > 0 ? t[e] : S(0));
+      }
+      if (row_lane) {                          // transported ancestor row, or the gravity row
+#pragma unroll
+        for (int e = 0; e < 6; ++e) skc[e] = t[e];
+        if (l == NB) skc[6] = skc[7] = S(0);
+        S* dst = l == NB ? GR + 8 * i : SK + 8 * (tp.skoff(i) + l);
+        st4(dst, skc);
+        st4(dst + 4, skc + 4);
+      } else if (l == i) {                     // own row s_i^(i) = S_i, with qd_i and i
+        skc[0] = a[0]; skc[1] = a[1]; skc[2] = a[2];
+        skc[3] = skc[4] = skc[5] = S(0);
+        skc[6] = W[L.QD + i];
+        skc[7] = S(i);
+        S* dst = SK + 8 * (tp.skoff(i) + i);
+        st4(dst, skc);
+        st4(dst + 4, skc + 4);
+      }
+    }
+  } else {
 #pragma unroll (Tp::kUnroll)
   for (int i = 0; i < n; ++i) {
     const int p = tp.parent(i);
@@ -385,6 +438,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
       }
     }
     if (WITH_SK) subspace_step<S, T>(c, i, E, skc);
+  }
   }
   // mirror the columns this lane owns into the lower triangle
 #pragma unroll
