@@ -592,30 +592,52 @@ __device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
     st6(W + L.BPH + 12 * k, B);
   }
   SYNC();
-  // Leaves to root: lane l < 6 holds component l of F_k; the full vector is
-  // gathered by warp shuffles. A child's X^T F passes in a register to its
-  // parent when the parent is the next body (k - 1), else through a slot.
-  const int base = c.lane32 - l;
-  S carry = S(0);
-#pragma unroll (Tp::kUnroll)
-  for (int k = tp.n() - 1; k >= 0; --k) {
-    const int p = tp.parent(k);
-    const int br = tp.branch(k);
-    S fk = S(0);
-    if (l < 6) {
-      fk = FA[8 * k + l];
-      if (k + 1 < tp.n() && tp.parent(k + 1) == k) fk += carry;
-      if (br >= 0) fk += FSL[8 * br + l];
-    }
-    S F[6];
+  if constexpr (Tp::kChainN > 0) {
+    // Chain: every lane carries the whole accumulated force, F_k = f_k + X_{k+1}^T F_{k+1}
+    // (no exchange between lanes; lane 0 stores it).
+    S F[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
 #pragma unroll
-    for (int e = 0; e < 6; ++e) F[e] = GRID_SHFL(fk, base + e);
-    if (l < 6) {
-      FA[8 * k + l] = fk;
-      if (p >= 0) {
-        const S cl = xt_mul_c(W + L.X + 12 * k, F, l);
-        if (p == k - 1) carry = cl;
-        else FSL[8 * tp.branch(p) + l] += cl;
+    for (int k = Tp::kChainN - 1; k >= 0; --k) {
+      S f[6];
+      ld6(FA + 8 * k, f);
+      if (k + 1 < Tp::kChainN) {
+        S E[12], x[6];
+        ld12(W + L.X + 12 * (k + 1), E);
+        xt_mul(E, E + 9, F, x);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) f[e] += x[e];
+      }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) F[e] = f[e];
+      SYNC();                                  // every lane has read f_k before it is overwritten
+      if (l == 0) st6(FA + 8 * k, F);
+    }
+  } else {
+    // Leaves to root: lane l < 6 holds component l of F_k; the full vector is
+    // gathered by warp shuffles. A child's X^T F passes in a register to its
+    // parent when the parent is the next body (k - 1), else through a slot.
+    const int base = c.lane32 - l;
+    S carry = S(0);
+#pragma unroll (Tp::kUnroll)
+    for (int k = tp.n() - 1; k >= 0; --k) {
+      const int p = tp.parent(k);
+      const int br = tp.branch(k);
+      S fk = S(0);
+      if (l < 6) {
+        fk = FA[8 * k + l];
+        if (k + 1 < tp.n() && tp.parent(k + 1) == k) fk += carry;
+        if (br >= 0) fk += FSL[8 * br + l];
+      }
+      S F[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) F[e] = GRID_SHFL(fk, base + e);
+      if (l < 6) {
+        FA[8 * k + l] = fk;
+        if (p >= 0) {
+          const S cl = xt_mul_c(W + L.X + 12 * k, F, l);
+          if (p == k - 1) carry = cl;
+          else FSL[8 * tp.branch(p) + l] += cl;
+        }
       }
     }
   }
@@ -671,10 +693,9 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
     const int k = STEP_BODY(st);
     const int col = STEP_COL(st);
     const bool root = st & STEP_ROOT, uq = st & STEP_UQ;
-    if (st & STEP_RESET) {
+    const bool rs = st & STEP_RESET;           // first step of a path: no parent derivatives
 #pragma unroll
-      for (int e = 0; e < 6; ++e) { dv[e] = S(0); da[e] = S(0); }
-    }
+    for (int e = 0; e < 6; ++e) { dv[e] = rs ? S(0) : dv[e]; da[e] = rs ? S(0) : da[e]; }
     const int dk = STEP_DEPTH(st);
     const S* rows = W + L.SK + 8 * STEP_SKOFF(st);
     S E[12];
@@ -695,7 +716,7 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
     x_mul(E, r, da, nda);
     const bool pr = tp.prism(k);
     cross_s(v, ax, pr, vxs);     // v x S
-    if (root) {
+    if (root) {                   // case terms at the column's own joint
       if (uq) {
         S B[6];
         ld6(W + L.BPH + 12 * k, B);
@@ -722,7 +743,7 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
     crf_mul(v, idv, t2);
 #pragma unroll
     for (int e = 0; e < 6; ++e) df[e] += t1[e] + t2[e];
-    if (root && uq) {
+    if (root && uq) {                          // backward-pass term S x* F of Alg. 1
       S Ph[6];
       ld6u(W + L.BPH + 12 * k + 6, Ph);
 #pragma unroll
