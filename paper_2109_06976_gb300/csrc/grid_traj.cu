@@ -18,6 +18,12 @@
 
 #include "grid_launch.cuh"
 
+// iLQR backward pass, compiled per state size (grid_riccati.cu)
+template <class S>
+grid_status launch_riccati(const grid_model* m, int B, int H, S dt, const S* Q, const S* QD, const S* U,
+                           const S* J, const S* Minv, const S* Qr, const S* QDr, const S* wq, const S* wr,
+                           const S* wf, S mu, S* K, S* kff, S* dV, cudaStream_t st);
+
 namespace {
 
 // ---------------------------------------------------------------- rollout
@@ -97,212 +103,6 @@ __global__ void __launch_bounds__(128) rollout_kernel(
     if (ok && Uout)
       for (int i = l; i < n; i += T) Uout[(k0 + H) * n + i] = S(0);
     SYNC();
-  }
-}
-
-// ---------------------------------------------------------------- iLQR backward pass
-// One warp per trajectory; m = 2n state components, n controls. Matrices live
-// in the warp's shared-memory slice, row-major; lanes run over entries.
-struct RicLayout {
-  int Vxx, Vn, A, VA, Qxx, Bm, VB, Quu, Lc, Qux, Kk, QK, Vx, Qx, Qu, kk, Qk, lx, lu, stride;
-};
-
-GRID_HD inline RicLayout ric_layout(int n, int ssize) {
-  RicLayout R{};
-  const int m = 2 * n;
-  int o = 0;
-  auto take = [&](int cnt) { int r = o; o += (cnt + 3) & ~3; return r; };
-  R.Vxx = take(m * m); R.Vn = take(m * m); R.A = take(m * m); R.VA = take(m * m); R.Qxx = take(m * m);
-  R.Bm = take(m * n); R.VB = take(m * n); R.Quu = take(n * n); R.Lc = take(n * n); R.Qux = take(n * m);
-  R.Kk = take(n * m); R.QK = take(n * m);
-  R.Vx = take(m); R.Qx = take(m); R.Qu = take(n); R.kk = take(n); R.Qk = take(n); R.lx = take(m); R.lu = take(n);
-  R.stride = o + (32 / ssize);
-  return R;
-}
-
-template <class S>
-__global__ void __launch_bounds__(128) riccati_kernel(
-    int n, int B, int H, S dt, const S* __restrict__ Q, const S* __restrict__ QD, const S* __restrict__ U,
-    const S* __restrict__ J, const S* __restrict__ Minv, const S* __restrict__ Qr, const S* __restrict__ QDr,
-    const S* __restrict__ wq, const S* __restrict__ wr, const S* __restrict__ wf, S mu, S* __restrict__ Ko,
-    S* __restrict__ kffo, S* __restrict__ dV) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const RicLayout R = ric_layout(n, (int)sizeof(S));
-  const int m = 2 * n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  S* Wb = reinterpret_cast<S*>(smem) + warp * R.stride;
-  S* Vxx = Wb + R.Vxx; S* Vn = Wb + R.Vn; S* A = Wb + R.A; S* VA = Wb + R.VA; S* Qxx = Wb + R.Qxx;
-  S* Bm = Wb + R.Bm; S* VB = Wb + R.VB; S* Quu = Wb + R.Quu; S* Lc = Wb + R.Lc; S* Qux = Wb + R.Qux;
-  S* Kk = Wb + R.Kk; S* QK = Wb + R.QK; S* Vx = Wb + R.Vx; S* Qx = Wb + R.Qx; S* Qu = Wb + R.Qu;
-  S* kk = Wb + R.kk; S* Qk = Wb + R.Qk; S* lx = Wb + R.lx; S* lu = Wb + R.lu;
-  const size_t knots = (size_t)H + 1;
-  for (int b = blockIdx.x * wpb + warp; b < B; b += gridDim.x * wpb) {
-    const size_t kH = (size_t)b * knots + H;
-    // terminal cost: V_x = W_f (x_H - r_H), V_xx = W_f
-    for (int e = lane; e < m * m; e += 32) Vxx[e] = (e / m == e % m) ? wf[e % m] : S(0);
-    for (int i = lane; i < m; i += 32) {
-      const S x = i < n ? Q[kH * n + i] : QD[kH * n + i - n];
-      const S r = i < n ? Qr[kH * n + i] : QDr[kH * n + i - n];
-      Vx[i] = wf[i] * (x - r);
-    }
-    S dv0 = S(0), dv1 = S(0);
-    bool pd = true;
-    __syncwarp();
-    for (int k = H - 1; k >= 0; --k) {
-      const size_t kb = (size_t)b * knots + k;
-      // step Jacobians: rows n..2n-1 (qd'), then rows 0..n-1 (q' = q + dt qd')
-      const S* Jk = J + kb * n * m;
-      const S* Mk = Minv + kb * n * n;
-      for (int e = lane; e < n * m; e += 32) {
-        const int i = e / m, j = e % m;
-        A[(n + i) * m + j] = dt * Jk[i * m + j] + ((j == n + i) ? S(1) : S(0));
-      }
-      for (int e = lane; e < n * n; e += 32) {
-        const int i = e / n, j = e % n;
-        Bm[(n + i) * n + j] = dt * Mk[i * n + j];
-      }
-      for (int i = lane; i < m; i += 32) {
-        const S x = i < n ? Q[kb * n + i] : QD[kb * n + i - n];
-        const S r = i < n ? Qr[kb * n + i] : QDr[kb * n + i - n];
-        lx[i] = wq[i] * (x - r);
-      }
-      for (int i = lane; i < n; i += 32) lu[i] = wr[i] * U[kb * n + i];
-      __syncwarp();
-      for (int e = lane; e < n * m; e += 32) {
-        const int i = e / m, j = e % m;
-        A[i * m + j] = ((j == i) ? S(1) : S(0)) + dt * A[(n + i) * m + j];
-      }
-      for (int e = lane; e < n * n; e += 32) Bm[e] = dt * Bm[n * n + e];
-      __syncwarp();
-      // V_xx A and V_xx B
-      for (int e = lane; e < m * m; e += 32) {
-        const int r = e / m, cc = e % m;
-        S s = S(0);
-        for (int t = 0; t < m; ++t) s += Vxx[r * m + t] * A[t * m + cc];
-        VA[e] = s;
-      }
-      for (int e = lane; e < m * n; e += 32) {
-        const int r = e / n, cc = e % n;
-        S s = S(0);
-        for (int t = 0; t < m; ++t) s += Vxx[r * m + t] * Bm[t * n + cc];
-        VB[e] = s;
-      }
-      __syncwarp();
-      // Q terms
-      for (int e = lane; e < m * m; e += 32) {
-        const int r = e / m, cc = e % m;
-        S s = (r == cc) ? wq[r] : S(0);
-        for (int t = 0; t < m; ++t) s += A[t * m + r] * VA[t * m + cc];
-        Qxx[e] = s;
-      }
-      for (int e = lane; e < n * n; e += 32) {
-        const int r = e / n, cc = e % n;
-        S s = (r == cc) ? wr[r] + mu : S(0);
-        for (int t = 0; t < m; ++t) s += Bm[t * n + r] * VB[t * n + cc];
-        Quu[e] = s;
-      }
-      for (int e = lane; e < n * m; e += 32) {
-        const int r = e / m, cc = e % m;
-        S s = S(0);
-        for (int t = 0; t < m; ++t) s += Bm[t * n + r] * VA[t * m + cc];
-        Qux[e] = s;
-      }
-      for (int i = lane; i < m; i += 32) {
-        S s = lx[i];
-        for (int t = 0; t < m; ++t) s += A[t * m + i] * Vx[t];
-        Qx[i] = s;
-      }
-      for (int i = lane; i < n; i += 32) {
-        S s = lu[i];
-        for (int t = 0; t < m; ++t) s += Bm[t * n + i] * Vx[t];
-        Qu[i] = s;
-      }
-      __syncwarp();
-      // Cholesky Q_uu = L L^T (one lane; n <= 16)
-      if (lane == 0) {
-        for (int j = 0; j < n; ++j) {
-          S d = Quu[j * n + j];
-          for (int t = 0; t < j; ++t) d -= Lc[j * n + t] * Lc[j * n + t];
-          if (!(d > S(0))) { pd = false; d = S(1); }
-          const S ljj = sqrt(d);
-          Lc[j * n + j] = ljj;
-          for (int i = j + 1; i < n; ++i) {
-            S s = Quu[i * n + j];
-            for (int t = 0; t < j; ++t) s -= Lc[i * n + t] * Lc[j * n + t];
-            Lc[i * n + j] = s / ljj;
-          }
-        }
-      }
-      __syncwarp();
-      // K = -Q_uu^-1 Q_ux (columns 0..m-1), k = -Q_uu^-1 Q_u (column m): one lane per column
-      for (int cc = lane; cc <= m; cc += 32) {
-        S y[16];
-        for (int i = 0; i < n; ++i) {
-          S s = cc < m ? Qux[i * m + cc] : Qu[i];
-          for (int t = 0; t < i; ++t) s -= Lc[i * n + t] * y[t];
-          y[i] = s / Lc[i * n + i];
-        }
-        for (int i = n - 1; i >= 0; --i) {
-          S s = y[i];
-          for (int t = i + 1; t < n; ++t) s -= Lc[t * n + i] * y[t];
-          y[i] = s / Lc[i * n + i];
-        }
-        for (int i = 0; i < n; ++i) {
-          if (cc < m) Kk[i * m + cc] = -y[i];
-          else kk[i] = -y[i];
-        }
-      }
-      __syncwarp();
-      // Q_uu K and Q_uu k
-      for (int e = lane; e < n * m; e += 32) {
-        const int r = e / m, cc = e % m;
-        S s = S(0);
-        for (int t = 0; t < n; ++t) s += Quu[r * n + t] * Kk[t * m + cc];
-        QK[e] = s;
-      }
-      for (int i = lane; i < n; i += 32) {
-        S s = S(0);
-        for (int t = 0; t < n; ++t) s += Quu[i * n + t] * kk[t];
-        Qk[i] = s;
-      }
-      __syncwarp();
-      // V_x = Q_x + K^T Q_uu k + K^T Q_u + Q_ux^T k
-      for (int i = lane; i < m; i += 32) {
-        S s = Qx[i];
-        for (int t = 0; t < n; ++t) s += Kk[t * m + i] * Qk[t] + Kk[t * m + i] * Qu[t] + Qux[t * m + i] * kk[t];
-        Vx[i] = s;
-      }
-      // V_xx = Q_xx + K^T Q_uu K + K^T Q_ux + Q_ux^T K
-      for (int e = lane; e < m * m; e += 32) {
-        const int r = e / m, cc = e % m;
-        S s = Qxx[e];
-        for (int t = 0; t < n; ++t)
-          s += Kk[t * m + r] * QK[t * m + cc] + Kk[t * m + r] * Qux[t * m + cc] + Qux[t * m + r] * Kk[t * m + cc];
-        Vn[e] = s;
-      }
-      if (lane == 0) {
-        S a = S(0), q2 = S(0);
-        for (int t = 0; t < n; ++t) { a += kk[t] * Qu[t]; q2 += kk[t] * Qk[t]; }
-        dv0 += a;
-        dv1 += S(0.5) * q2;
-      }
-      for (int e = lane; e < n * m; e += 32) Ko[kb * n * m + e] = Kk[e];
-      for (int i = lane; i < n; i += 32) kffo[kb * n + i] = kk[i];
-      __syncwarp();
-      for (int e = lane; e < m * m; e += 32) {
-        const int r = e / m, cc = e % m;
-        Vxx[e] = S(0.5) * (Vn[r * m + cc] + Vn[cc * m + r]);
-      }
-      __syncwarp();
-    }
-    if (lane == 0) {
-      const bool all_pd = pd;
-      dV[2 * (size_t)b] = all_pd ? dv0 : S(NAN);
-      dV[2 * (size_t)b + 1] = all_pd ? dv1 : S(NAN);
-    }
-    for (int e = lane; e < n * m; e += 32) Ko[((size_t)b * knots + H) * n * m + e] = S(0);
-    for (int i = lane; i < n; i += 32) kffo[((size_t)b * knots + H) * n + i] = S(0);
-    __syncwarp();
   }
 }
 
@@ -416,34 +216,10 @@ grid_status riccati(const grid_model* m, int B, int H, S dt, const S* Q, const S
                     S* kff, S* dV, void* stream) {
   grid_status s = check_traj<S>(m, B, H, {Q, QD, U, J, Minv, Qr, QDr, wq, wr, wf, K, kff, dV}, {});
   if (s != GRID_OK) return s;
-  const int n = m->n;
-  if (n > 16) { grid_set_error("the Riccati pass supports n <= 16 (n = %d)", n); return GRID_E_ARG; }
+  if (m->n > 16) { grid_set_error("the Riccati pass supports n <= 16 (n = %d)", m->n); return GRID_E_ARG; }
   if (B == 0) return GRID_OK;
-  auto kern = riccati_kernel<S>;
-  const DevInfo di = dev_info(m->device);
-  static std::atomic<int> opted{0};
-  if (!opted.load()) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin) != cudaSuccess) {
-      grid_set_error("cudaFuncSetAttribute failed");
-      return GRID_E_CUDA;
-    }
-    opted.store(1);
-  }
-  const size_t per_warp = (size_t)ric_layout(n, (int)sizeof(S)).stride * sizeof(S);
-  int warps, per_sm;
-  if (!pick_launch(kern, di.smem_optin, 0, per_warp, warps, per_sm)) {
-    grid_set_error("Riccati workspace of %zu B exceeds shared memory", per_warp);
-    return GRID_E_ARG;
-  }
-  const int grid = (int)std::min<long>(((long)B + warps - 1) / warps, (long)di.nsm * per_sm);
-  kern<<<grid, 32 * warps, warps * per_warp, reinterpret_cast<cudaStream_t>(stream)>>>(
-      n, B, H, dt, Q, QD, U, J, Minv, Qr, QDr, wq, wr, wf, mu, K, kff, dV);
-  const cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess) {
-    grid_set_error("Riccati launch: %s", cudaGetErrorString(err));
-    return GRID_E_CUDA;
-  }
-  return GRID_OK;
+  return launch_riccati<S>(m, B, H, dt, Q, QD, U, J, Minv, Qr, QDr, wq, wr, wf, mu, K, kff, dV,
+                           reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // namespace
