@@ -48,7 +48,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # launch, scaled by knot points to the benchmark's launch.)
 NCU_DRAM_BYTES_PER_KNOT = {"517743476c2097e0": 199.75e6 / 524288,
                            "d1f6cfa03f54f835": 199.17e6 / 524288,
-                           "e04804cb5f3a6d15": 188.95e6 / 524288}
+                           "e04804cb5f3a6d15": 188.95e6 / 524288,
+                           "59c365e8cec7dca6": 189.65e6 / 524288}
 
 
 def kernel_source_hash() -> str:
