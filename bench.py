@@ -50,6 +50,9 @@ NCU_DRAM_BYTES_PER_KNOT = {"517743476c2097e0": 199.75e6 / 524288,
                            "d1f6cfa03f54f835": 199.17e6 / 524288,
                            "e04804cb5f3a6d15": 188.95e6 / 524288,
                            "59c365e8cec7dca6": 189.65e6 / 524288}
+# FP32 (FMA) pipe utilisation of the same captures (sm__inst_executed_pipe_fma, % of peak
+# sustained while active), reported beside the counted-flop fraction.
+NCU_FMA_PIPE = {"e04804cb5f3a6d15": 0.393, "59c365e8cec7dca6": 0.414}
 
 
 def kernel_source_hash() -> str:
@@ -205,6 +208,50 @@ def traj_leg(grid, model, stream, dist, B=2048, H=64, dt=0.01):
             "knot_points_per_s": B * (H + 1) * steps / sec, **parts,
             "note": "one iLQR iteration = rollout + gradient of FD and M^-1 at every knot point + "
                     "backward pass + policy rollout, all on the device (7-DoF chain, FP32)"}
+
+
+def n_sweep(grid, Ns=(32, 64, 128, 256, 512), reps=100):
+    """One launch of a single N-knot trajectory (compute only, device time) for
+    the 7- and 12-DoF robots, FP32 against the FP64-plain form."""
+    import numpy as np
+    import torch
+    import grid_inputs as gi
+    out = {}
+    for name in ("chain7", "tree12"):
+        r = gi.robot(name)
+        m = grid.Model.from_robot(r)
+        row = {}
+        for N in Ns:
+            for dt, tag in ((torch.float32, "f32"), (torch.float64, "f64")):
+                q, qd, tau = (torch.from_numpy(x).to("cuda", dt) for x in gi.states(r.n, N, gi.workload_seed(2, N)))
+                J = torch.empty((N, r.n, 2 * r.n), device="cuda", dtype=dt)
+                row[f"{tag}_N{N}_us"] = device_latency_us(lambda: m.grad_fd(q, qd, tau, out=J), reps, 10)
+        out[name] = row
+        m.close()
+    return out
+
+
+def vjp_leg(grid, stream, dist, B=4096, H=64):
+    """The differentiation workload: FD forward and the VJP through it for the
+    12-DoF tree, B rollouts x H steps = 262,144 knot points in one batch, FP32."""
+    import numpy as np
+    import torch
+    import grid_inputs as gi
+    r = gi.tree12()
+    m = grid.Model.from_robot(r)
+    N = B * H
+    q, qd, tau = (torch.from_numpy(x.astype(np.float32)).cuda() for x in gi.states(r.n, N, 404))
+    g = torch.from_numpy(gi.upstream(r.n, N, 404).astype(np.float32)).cuda()
+    qdd = torch.empty_like(q)
+    outs = tuple(torch.empty_like(q) for _ in range(3))
+    steps = 10
+    sec_fd = time_steps(lambda: m.fd(q, qd, tau, out=qdd), steps, 3, stream, dist)
+    sec_vjp = time_steps(lambda: m.fd_vjp(q, qd, tau, g, out=outs), steps, 3, stream, dist)
+    m.close()
+    return {"knot_points": N, "fd_knot_points_per_s": N * steps / sec_fd,
+            "vjp_knot_points_per_s": N * steps / sec_vjp,
+            "note": "12-DoF tree, 4096 rollouts x 64 steps in one batch, FP32: forward dynamics, and the "
+                    "vector-Jacobian product (dL/dq, dL/dqd, dL/dtau) through it"}
 
 
 def device_latency_us(fn, reps=200, warmup=20):
@@ -365,6 +412,7 @@ def run_ours(args):
     flops_knot = grad_fd_flops_per_knot(robot.parent)
     achieved_tflops = flops_knot * Nk / (ms / 1e3) / 1e12
     dram = NCU_DRAM_BYTES_PER_KNOT.get(kernel_source_hash())
+    fma_pipe = NCU_FMA_PIPE.get(kernel_source_hash())
     if args.only_main:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
@@ -430,8 +478,22 @@ def run_ours(args):
     q1, qd1, tau1 = q[:KNOTS], qd[:KNOTS], tau[:KNOTS]
     J1 = J[:KNOTS]
     lat128 = device_latency_us(lambda: model.grad_fd(q1, qd1, tau1, out=J1))
+    # the same with the paper's I/O: pinned host -> device, kernel, device -> pinned host
+    h1 = [t.cpu().pin_memory() for t in (q1, qd1, tau1)]
+    hJ1 = torch.empty(J1.shape, dtype=J1.dtype).pin_memory()
+    d1 = [torch.empty_like(t) for t in (q1, qd1, tau1)]
+
+    def io_call():
+        for dd, hh in zip(d1, h1):
+            dd.copy_(hh, non_blocking=True)
+        model.grad_fd(*d1, out=J1)
+        hJ1.copy_(J1, non_blocking=True)
+
+    lat128_io = device_latency_us(io_call)
 
     lat_table = latency_table(grid) if rank == 0 else None
+    sweep = n_sweep(grid) if rank == 0 else None
+    vjp = vjp_leg(grid, stream, dist) if rank == 0 and world == 1 else None
     traj = traj_leg(grid, model, stream, dist) if rank == 0 and world == 1 else None
 
     serve = None
@@ -441,8 +503,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, threads, done, el = cpu_oracle_rate(robot)
+        rate1, _, done1, el1 = cpu_oracle_rate(robot, seconds_min=3.0, seconds_max=10.0, threads=1)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{done} knot points of 128-knot trajectories in {el:.1f} s"}
+               "sample": f"{done} knot points of 128-knot trajectories in {el:.1f} s",
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": f"{done1} knot points in {el1:.1f} s"}}
 
     if rank == 0:
         line = {
@@ -461,6 +526,7 @@ def run_ours(args):
                          "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
                          "traffic": None if dram is None else dram * Nk,
                          "flops_per_knot": flops_knot,
+                         "fp32_pipe_util_ncu": fma_pipe,
                          "peak_note": "FP32 from 152 SMs x 128 lanes x 2 x 2070 MHz",
                          "hbm_gbs": (in_bytes + out_bytes) / (ms / 1e3) / 1e9},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
@@ -475,11 +541,14 @@ def run_ours(args):
             "fp64_plain": {"value": fp64_value, "unit": UNIT, "knot_points_per_launch": Nd},
             "tree12": {"value": t12_value, "unit": UNIT, "knot_points_per_launch": Nk // 2},
             "latency_n128_us": lat128,
+            "latency_n128_with_io_us": lat128_io,
+            "latency_n_sweep_us": sweep,
             "latency_n1_us": lat_table,
             "latency_n1_note": "one knot point per call, compute only: median over 200 calls of the "
                                "device time between CUDA events, each call queued behind a device spin "
                                "(RNEA at qdd = tau's values; FP32, and the 30-DoF tree also in mixed precision)",
             "traj_step": traj,
+            "vjp": vjp,
             "serve": serve,
             "cpu_baseline": cpu,
             "clocks": clocks,
