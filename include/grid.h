@@ -122,7 +122,9 @@ int grid_model_dof(const grid_model* model);
  *   "lanes"       threads cooperating on one knot point: 0 = automatic, 8, 16 or 32
  *   "precision"   GRID_FP32 or GRID_MIXED for the float entry points
  *   "ctas_per_sm" resident CTAs per SM the launcher sizes the grid for (0 = auto)
- *   "specialize"  1 (default): serial chains (parent[i] = i - 1) of 2 to 8 bodies
+ *   "specialize"  1 (default): serial chains (parent[i] = i - 1) of 2 to 8 bodies,
+ *                 and forests of 4 x 3, 2 x 6 or 4 x 4 equal chains on the base (in
+ *                 depth-first order, batches above two knot points per SM),
  *                 run the gradient of FD (FP32 and FP64) in a kernel compiled for their
  *                 length (the chain topology of Sec. IV-C fixed at compile time);
  *                 0: always the kernel that reads the topology at run time

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgrid_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["grid_capi.cu", "grid_f32.cu", "grid_mixed.cu", "grid_f64.cu", "grid_chain.cu", "grid_serve.cu",
-           "grid_traj.cu", "grid_riccati.cu", "grid_host.cpp"]
+SOURCES = ["grid_capi.cu", "grid_f32.cu", "grid_mixed.cu", "grid_f64.cu", "grid_chain.cu", "grid_forest.cu",
+           "grid_serve.cu", "grid_traj.cu", "grid_riccati.cu", "grid_host.cpp"]
 
 
 def _nvcc() -> str:

@@ -100,6 +100,16 @@ grid_status grid_create_ex(int n, const int* parent, const int* jtype, const dou
   m->chain = !m->host_d->any_prism;
   for (int i = 0; m->chain && i < m->n; ++i)
     m->chain = m->host_d->parent[i] == i - 1 && m->host_d->perm[i] == i;
+  // K >= 2 identical chains of L bodies on the base, in caller order
+  m->forest_k = m->forest_l = 0;
+  if (!m->host_d->any_prism) {
+    int L = 1;
+    while (L < m->n && m->host_d->parent[L] == L - 1) ++L;
+    bool ok = m->n % L == 0 && m->n / L >= 2;
+    for (int i = 0; ok && i < m->n; ++i)
+      ok = m->host_d->parent[i] == (i % L == 0 ? -1 : i - 1) && m->host_d->perm[i] == i;
+    if (ok) { m->forest_k = m->n / L; m->forest_l = L; }
+  }
   cudaGetDevice(&m->device);
   cudaError_t e1 = cudaMalloc(&m->dev_f, sizeof(ModelDev<float>));
   cudaError_t e2 = cudaMalloc(&m->dev_d, sizeof(ModelDev<double>));

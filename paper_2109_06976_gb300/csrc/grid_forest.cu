@@ -1,0 +1,36 @@
+// Kernel instantiations for forests of K identical serial chains of L bodies
+// on the fixed base (legs of a quadruped, a biped, a hexapod), gradient of FD
+// in FP32 and FP64: the topology and the workspace layout are compile-time
+// constants (ForestTopo), 8 lanes per knot point.
+#include "grid_launch.cuh"
+
+bool forest_compiled(int k, int l) {
+  const int code = 100 * k + l;
+  return code == 403 || code == 206 || code == 404;
+}
+
+template <class S, int MODE>
+grid_status launch_forest(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
+                          const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st) {
+  const int code = 100 * m->forest_k + m->forest_l;
+  switch (code) {
+    case 403:   // 4 legs x 3 joints (12 bodies)
+      return launch_t<S, MODE, 8, 2, 8, false, -403>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    case 206:   // 2 chains x 6 joints (12 bodies)
+      return launch_t<S, MODE, 8, 2, 8, false, -206>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    case 404:   // 4 legs x 4 joints (16 bodies)
+      return launch_t<S, MODE, 8, 2, 8, false, -404>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    default:
+      break;
+  }
+  return GRID_E_TOPOLOGY;
+}
+
+template grid_status launch_forest<float, MODE_GRAD>(const grid_model*, const ModelDev<float>*,
+                                                     const ModelDev<float>*, int, const float*, const float*,
+                                                     const float*, const float*, float*, float*, float*,
+                                                     cudaStream_t);
+template grid_status launch_forest<double, MODE_GRAD>(const grid_model*, const ModelDev<double>*,
+                                                      const ModelDev<double>*, int, const double*, const double*,
+                                                      const double*, const double*, double*, double*, double*,
+                                                      cudaStream_t);

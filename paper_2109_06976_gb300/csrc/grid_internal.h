@@ -167,6 +167,7 @@ struct grid_model {
   int lanes_opt;
   int ctas_opt;
   int chain;                     // parent[i] = i - 1 for every body (a serial chain)
+  int forest_k, forest_l;        // K >= 2 equal chains of L revolute bodies on the base, else 0
   int specialize_opt;            // use the topology-specialised kernels where one exists (default 1)
   ModelDev<float>* dev_f;        // device copies
   ModelDev<double>* dev_d;

@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(128, CHAIN_N > 0 ? 4 : 1) grid_kernel(const Mo
   const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? M.steps[cfg] : 0;
   int stride;
   if constexpr (CHAIN_N > 0) stride = ChainTopo<S, MODE, CHAIN_N>::layout().stride;
+  else if constexpr (CHAIN_N < 0) stride = ForestTopo<S, MODE, -CHAIN_N / 100, -CHAIN_N % 100>::layout().stride;
   else stride = layout_of<MODE>(M).stride;
   uint32_t* sched = reinterpret_cast<uint32_t*>(smem + head);
   for (int i = threadIdx.x; i < nsteps * T; i += blockDim.x) sched[i] = gm->sched[M.sched_off[cfg] + i];
@@ -85,6 +86,12 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
     // the compile-time layout must be the one the host built for this model
     if (hm->n != CHAIN_N || ChainTopo<S, MODE, CHAIN_N>::layout().stride != layout_of<MODE>(*hm).stride) {
       grid_set_error("chain kernel for %d bodies does not match the model", CHAIN_N);
+      return GRID_E_TOPOLOGY;
+    }
+  } else if constexpr (CHAIN_N < 0) {
+    using F = ForestTopo<S, MODE, -CHAIN_N / 100, -CHAIN_N % 100>;
+    if (hm->n != F::n() || F::layout().stride != layout_of<MODE>(*hm).stride) {
+      grid_set_error("forest kernel does not match the model");
       return GRID_E_TOPOLOGY;
     }
   }
@@ -158,6 +165,11 @@ constexpr int kChainMaxN = 8;
 template <class S, int MODE>
 grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                          const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
+// Forests of K equal chains (grid_forest.cu), compiled for a few shapes.
+bool forest_compiled(int k, int l);
+template <class S, int MODE>
+grid_status launch_forest(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
+                          const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
 
 // Picks the lane count T (option or by size) and the M^-1 columns per lane.
 template <class S, int MODE, bool MIXED>
@@ -172,6 +184,9 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   if constexpr (MODE == MODE_GRAD && !MIXED) {
     if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
       return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    if (m->forest_k > 1 && m->specialize_opt && (T == 0 || T == 8) && N > 2 * dev_info(m->device).nsm &&
+        forest_compiled(m->forest_k, m->forest_l))
+      return launch_forest<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   }
   // Default lanes: 8 up to 12 bodies, else 16 (throughput). A batch smaller
   // than two knot points per SM is latency-bound: for more bodies than 8 lanes,

@@ -70,6 +70,31 @@ struct ChainTopo {
   GRID_HD static constexpr bool prism(int) { return false; }   // revolute chains only
 };
 
+// K identical serial chains of L bodies, each hanging from the fixed base, in
+// depth-first numbering (a quadruped's legs: K = 4, L = 3). The phases take
+// their general paths; only the topology folds.
+template <class S, int MODE, int K, int L>
+struct ForestTopo {
+  static constexpr int kUnroll = K * L;
+  static constexpr int kChainN = 0;
+  __device__ explicit ForestTopo(const ModelDev<S>&) {}
+  GRID_HD static constexpr KnotLayout layout() {
+    return make_layout(K * L, K * L * (L + 1) / 2, 0, (int)sizeof(S), layout_kind(MODE));
+  }
+  GRID_HD static constexpr int n() { return K * L; }
+  GRID_HD static constexpr int maxd() { return L; }
+  GRID_HD static constexpr int nbranch() { return 0; }
+  GRID_HD static constexpr int parent(int i) { return i % L == 0 ? -1 : i - 1; }
+  GRID_HD static constexpr int depth(int i) { return i % L; }
+  GRID_HD static constexpr int sub_end(int i) { return (i / L + 1) * L; }
+  GRID_HD static constexpr int comp_lo(int i) { return (i / L) * L; }
+  GRID_HD static constexpr int comp_hi(int i) { return (i / L + 1) * L; }
+  GRID_HD static constexpr int perm(int i) { return i; }
+  GRID_HD static constexpr int skoff(int i) { return (i / L) * (L * (L + 1) / 2) + (i % L) * (i % L + 1) / 2; }
+  GRID_HD static constexpr int branch(int) { return -1; }
+  GRID_HD static constexpr bool prism(int) { return false; }
+};
+
 template <class S, class Tp>
 struct Ctx {
   const ModelDev<S>& M;
@@ -978,7 +1003,12 @@ __device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const 
                              const S* __restrict__ x4, S* __restrict__ out, S* __restrict__ out2,
                              S* __restrict__ out3) {
   using P = typename std::conditional<MIXED, double, S>::type;
-  using Tp = typename std::conditional<CHAIN_N == 0, RtTopo<S, MODE>, ChainTopo<S, MODE, CHAIN_N>>::type;
+  // CHAIN_N: 0 run-time topology, N > 0 a chain of N bodies, -(100 K + L) a forest of K chains of L
+  using Tp = typename std::conditional<
+      CHAIN_N == 0, RtTopo<S, MODE>,
+      typename std::conditional<(CHAIN_N > 0), ChainTopo<S, MODE, (CHAIN_N > 0 ? CHAIN_N : 1)>,
+                                ForestTopo<S, MODE, (CHAIN_N < 0 ? -CHAIN_N / 100 : 1),
+                                           (CHAIN_N < 0 ? -CHAIN_N % 100 : 1)>>::type>::type;
   const Tp tp(M);
   const auto& L = tp.layout();     // the staged layout (runtime topology) or a compile-time constant
   const int n = tp.n();

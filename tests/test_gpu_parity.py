@@ -138,6 +138,35 @@ def test_chain_specialised_kernel(grid, n, seed, general, dtype):
     assert vec_rel_err(qdds, qddg) <= tol
 
 
+def _forest(K, L, seed):
+    import dataclasses
+    base = gi.random_tree(K * L, seed, general=True, max_children=1)
+    par = np.array([-1 if i % L == 0 else i - 1 for i in range(K * L)], dtype=np.int32)
+    return dataclasses.replace(base, name=f"forest{K}x{L}", parent=par)
+
+
+@pytest.mark.parametrize("shape", [None, (4, 3), (2, 6), (4, 4), (3, 2)], ids=lambda x: str(x))
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_forest_specialised_kernel(grid, shape, dtype):
+    """K equal chains on the base (the 12-DoF tree is 4 x 3): the kernel compiled
+    for the forest's shape, on a batch large enough to leave the latency mapping,
+    against the oracle and the run-time-topology kernel ((3, 2) has no compiled
+    shape and takes the general kernel)."""
+    r = gi.tree12() if shape is None else _forest(*shape, 3)
+    n = r.n
+    spec = grid.Model.from_robot(r)
+    gen = grid.Model.from_robot(r)
+    gen.set_option("specialize", 0)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, 400, 13, dtype)
+    Js = spec.grad_fd(q, qd, tau).cpu().numpy()
+    Jg = gen.grad_fd(q, qd, tau).cpu().numpy()
+    ref = oracle.grad_fd(r, q64, qd64, tau64)
+    fl = 1e-6 if shape is None else (1e-4 if dtype == torch.float32 else 1e-6)
+    tol = TOL32 if dtype == torch.float32 else TOL64
+    assert col_rel_err(Js, ref, floor=fl) <= tol
+    assert col_rel_err(Jg, ref, floor=fl) <= tol
+
+
 @pytest.mark.parametrize("key", WORKLOAD)
 def test_grad_fd_workload_sizes(grid, key):
     """The workload batch sizes (N = 16 .. 1024) in one call each."""
