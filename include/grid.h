@@ -124,7 +124,7 @@ int grid_model_dof(const grid_model* model);
  *   "ctas_per_sm" resident CTAs per SM the launcher sizes the grid for (0 = auto)
  *   "specialize"  1 (default): serial chains (parent[i] = i - 1) of 2 to 8 bodies,
  *                 and forests of 4 x 3, 2 x 6 or 4 x 4 equal chains on the base (in
- *                 depth-first order, batches above two knot points per SM),
+ *                 depth-first order; with "lanes" 0),
  *                 run the gradient of FD (FP32 and FP64) in a kernel compiled for their
  *                 length (the chain topology of Sec. IV-C fixed at compile time);
  *                 0: always the kernel that reads the topology at run time

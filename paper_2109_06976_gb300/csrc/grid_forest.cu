@@ -1,7 +1,7 @@
 // Kernel instantiations for forests of K identical serial chains of L bodies
 // on the fixed base (legs of a quadruped, a biped, a hexapod), gradient of FD
 // in FP32 and FP64: the topology and the workspace layout are compile-time
-// constants (ForestTopo), 8 lanes per knot point.
+// constants (ForestTopo); 8 lanes per knot point, 32 for small batches.
 #include "grid_launch.cuh"
 
 bool forest_compiled(int k, int l) {
@@ -12,14 +12,18 @@ bool forest_compiled(int k, int l) {
 template <class S, int MODE>
 grid_status launch_forest(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                           const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st) {
-  const int code = 100 * m->forest_k + m->forest_l;
-  switch (code) {
-    case 403:   // 4 legs x 3 joints (12 bodies)
-      return launch_t<S, MODE, 8, 2, 8, false, -403>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
-    case 206:   // 2 chains x 6 joints (12 bodies)
-      return launch_t<S, MODE, 8, 2, 8, false, -206>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
-    case 404:   // 4 legs x 4 joints (16 bodies)
-      return launch_t<S, MODE, 8, 2, 8, false, -404>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+  // 8 lanes per knot point for throughput; a batch of at most two knot points
+  // per SM is latency-bound and takes one warp per knot point
+  const bool lat = N <= 2 * dev_info(m->device).nsm;
+  switch (100 * m->forest_k + m->forest_l) {
+#define GRID_FOREST(CODE)                                                                                 \
+    case CODE:                                                                                            \
+      if (lat) return launch_t<S, MODE, 32, 1, 8, false, -CODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st); \
+      return launch_t<S, MODE, 8, 2, 8, false, -CODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    GRID_FOREST(403)   // 4 legs x 3 joints (12 bodies)
+    GRID_FOREST(206)   // 2 chains x 6 joints (12 bodies)
+    GRID_FOREST(404)   // 4 legs x 4 joints (16 bodies)
+#undef GRID_FOREST
     default:
       break;
   }

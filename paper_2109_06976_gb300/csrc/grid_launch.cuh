@@ -184,8 +184,7 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   if constexpr (MODE == MODE_GRAD && !MIXED) {
     if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
       return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
-    if (m->forest_k > 1 && m->specialize_opt && (T == 0 || T == 8) && N > 2 * dev_info(m->device).nsm &&
-        forest_compiled(m->forest_k, m->forest_l))
+    if (m->forest_k > 1 && m->specialize_opt && T == 0 && forest_compiled(m->forest_k, m->forest_l))
       return launch_forest<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   }
   // Default lanes: 8 up to 12 bodies, else 16 (throughput). A batch smaller

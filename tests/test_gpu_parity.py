@@ -147,17 +147,18 @@ def _forest(K, L, seed):
 
 @pytest.mark.parametrize("shape", [None, (4, 3), (2, 6), (4, 4), (3, 2)], ids=lambda x: str(x))
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
-def test_forest_specialised_kernel(grid, shape, dtype):
+@pytest.mark.parametrize("N", [37, 400])
+def test_forest_specialised_kernel(grid, shape, dtype, N):
     """K equal chains on the base (the 12-DoF tree is 4 x 3): the kernel compiled
-    for the forest's shape, on a batch large enough to leave the latency mapping,
-    against the oracle and the run-time-topology kernel ((3, 2) has no compiled
-    shape and takes the general kernel)."""
+    for the forest's shape (32 lanes per knot point for the small batch, 8 for
+    the large one) against the oracle and the run-time-topology kernel ((3, 2)
+    has no compiled shape and takes the general kernel)."""
     r = gi.tree12() if shape is None else _forest(*shape, 3)
     n = r.n
     spec = grid.Model.from_robot(r)
     gen = grid.Model.from_robot(r)
     gen.set_option("specialize", 0)
-    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, 400, 13, dtype)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 13, dtype)
     Js = spec.grad_fd(q, qd, tau).cpu().numpy()
     Jg = gen.grad_fd(q, qd, tau).cpu().numpy()
     ref = oracle.grad_fd(r, q64, qd64, tau64)
