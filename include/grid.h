@@ -127,6 +127,10 @@ int grid_model_dof(const grid_model* model);
  *                 depth-first order; with "lanes" 0),
  *                 run the gradient of FD (FP32 and FP64) in a kernel compiled for their
  *                 length (the chain topology of Sec. IV-C fixed at compile time);
+ *                 2: as 1, and any other robot's gradient of FD runs in a kernel
+ *                 compiled at run time (NVRTC, on the first call for each
+ *                 precision and lane count) with its topology tables as constants;
+ *                 GRID_E_CUDA if NVRTC or the driver library cannot be loaded;
  *                 0: always the kernel that reads the topology at run time
  */
 grid_status grid_set_option(grid_model* model, const char* key, int value);

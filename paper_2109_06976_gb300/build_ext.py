@@ -17,7 +17,42 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgrid_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["grid_capi.cu", "grid_f32.cu", "grid_mixed.cu", "grid_f64.cu", "grid_chain.cu", "grid_forest.cu",
-           "grid_serve.cu", "grid_traj.cu", "grid_riccati.cu", "grid_host.cpp"]
+           "grid_serve.cu", "grid_traj.cu", "grid_riccati.cu", "grid_host.cpp", "grid_nvrtc.cpp"]
+# Device headers embedded for run-time compilation (name as included -> file)
+EMBED = [("grid_kernel.cuh", "grid_kernel.cuh"), ("grid_phases.cuh", "grid_phases.cuh"),
+         ("grid_internal.h", "grid_internal.h"), ("spatial.cuh", "spatial.cuh"),
+         ("../../include/grid.h", os.path.join("..", "..", "include", "grid.h"))]
+# Minimal C headers for NVRTC, which has no C library
+RTC_STDDEF = """#pragma once
+typedef unsigned long size_t;
+typedef long ptrdiff_t;
+#define offsetof(T, m) __builtin_offsetof(T, m)
+"""
+RTC_STDINT = """#pragma once
+typedef signed char int8_t; typedef short int16_t; typedef int int32_t; typedef long long int64_t;
+typedef unsigned char uint8_t; typedef unsigned short uint16_t; typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t; typedef unsigned long uintptr_t;
+"""
+
+
+def _write_embed() -> str:
+    """_build/grid_embed.inc: the device headers as string literals (rewritten
+    only when they change)."""
+    items = [(name, open(os.path.join(CSRC, path)).read()) for name, path in EMBED]
+    items += [("stddef.h", RTC_STDDEF), ("stdint.h", RTC_STDINT)]
+    out = [f"static const int kEmbedCount = {len(items)};",
+           "static const char* const kEmbedNames[] = {" + ", ".join(f'"{n}"' for n, _ in items) + "};",
+           "static const char* const kEmbedSources[] = {"]
+    for _, text in items:
+        assert ")GRIDSRC\"" not in text
+        out.append('R"GRIDSRC(' + text + ')GRIDSRC",')
+    out.append("};")
+    path = os.path.join(BUILD, "grid_embed.inc")
+    new = "\n".join(out) + "\n"
+    if not os.path.exists(path) or open(path).read() != new:
+        with open(path, "w") as fh:
+            fh.write(new)
+    return path
 
 
 def _nvcc() -> str:
@@ -39,6 +74,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "grid.h"))
+    embed = _write_embed()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", *ARCH, *extra_flags]
     jobs = []
     objs = []
@@ -46,8 +82,8 @@ def build(verbose: bool = False, extra_flags=()) -> str:
         path = os.path.join(CSRC, src)
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
-        if _stale(obj, [path, *headers]):
-            cmd = [nvcc, *common, "-c", path, "-o", obj]
+        if _stale(obj, [path, *headers, embed]):
+            cmd = [nvcc, *common, "-I", BUILD, "-c", path, "-o", obj]
             if src.endswith(".cu"):
                 cmd += ["-Xptxas", "-v"] if verbose else []
             jobs.append(cmd)
@@ -65,7 +101,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
             print(lg)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc, "-shared", *ARCH, "-cudart", "static", "-o", tmp, *objs])
+        run([nvcc, "-shared", *ARCH, "-cudart", "static", "-o", tmp, *objs, "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

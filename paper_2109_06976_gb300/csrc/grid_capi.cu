@@ -90,6 +90,7 @@ grid_status grid_create_ex(int n, const int* parent, const int* jtype, const dou
   m->lanes_opt = 0;
   m->ctas_opt = 0;
   m->specialize_opt = 1;
+  m->gen = nullptr;
   m->host_f = new ModelDev<float>();
   m->host_d = new ModelDev<double>();
   grid_status s = grid_build_model(n, parent, jtype, axis, X_tree, inertia, gravity, m->host_f, m->host_d);
@@ -137,6 +138,7 @@ grid_status grid_destroy(grid_model* m) {
   cudaDeviceSynchronize();
   cudaFree(m->dev_f);
   cudaFree(m->dev_d);
+  grid_gen_cache_free(m->gen);
   delete m->host_f;
   delete m->host_d;
   delete m;
@@ -159,7 +161,7 @@ grid_status grid_set_option(grid_model* m, const char* key, int value) {
     }
     m->prec = (grid_precision)value;
   } else if (k == "specialize") {
-    if (value != 0 && value != 1) { grid_set_error("specialize must be 0 or 1"); return GRID_E_ARG; }
+    if (value < 0 || value > 2) { grid_set_error("specialize must be 0, 1 or 2"); return GRID_E_ARG; }
     m->specialize_opt = value;
   } else if (k == "ctas_per_sm") {
     if (value < 0) { grid_set_error("ctas_per_sm must be >= 0"); return GRID_E_ARG; }

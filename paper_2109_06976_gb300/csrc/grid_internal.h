@@ -6,6 +6,14 @@
 
 #include "../../include/grid.h"
 
+
+// Small type traits (these headers are also compiled at run time by NVRTC,
+// which has no standard library).
+template <class A, class B> struct grid_same { static constexpr bool value = false; };
+template <class A> struct grid_same<A, A> { static constexpr bool value = true; };
+template <bool C, class A, class B> struct grid_cond { using type = A; };
+template <class A, class B> struct grid_cond<false, A, B> { using type = B; };
+
 #ifdef __CUDACC__
 #define GRID_HD __host__ __device__
 #else
@@ -158,7 +166,13 @@ GRID_HD inline const KnotLayout& layout_of(const ModelDev<S>& m) {
 // the inertia column table, which is read from device memory, and the
 // schedules, whose lane-count slice is copied separately).
 template <class S>
-GRID_HD constexpr int model_head_bytes() { return (int)offsetof(ModelDev<S>, Icol); }
+GRID_HD constexpr int model_head_bytes() {
+#ifdef __CUDACC_RTC__   // run-time compilation: the library passes the offsets it was built with
+  return sizeof(S) == 4 ? GRID_RTC_HEAD_F : GRID_RTC_HEAD_D;
+#else
+  return (int)offsetof(ModelDev<S>, Icol);
+#endif
+}
 
 struct grid_model {
   int n;
@@ -168,12 +182,16 @@ struct grid_model {
   int ctas_opt;
   int chain;                     // parent[i] = i - 1 for every body (a serial chain)
   int forest_k, forest_l;        // K >= 2 equal chains of L revolute bodies on the base, else 0
+  struct grid_gen_cache* gen;    // kernels compiled at run time for this model (grid_nvrtc.cpp)
   int specialize_opt;            // use the topology-specialised kernels where one exists (default 1)
   ModelDev<float>* dev_f;        // device copies
   ModelDev<double>* dev_d;
   ModelDev<float>* host_f;       // host mirrors (for launch decisions)
   ModelDev<double>* host_d;
 };
+
+// Run-time specialisation (grid_nvrtc.cpp)
+void grid_gen_cache_free(struct grid_gen_cache* c);
 
 // Host helpers (grid_host.cpp)
 void grid_set_error(const char* fmt, ...);

@@ -16,44 +16,16 @@
 #include <type_traits>
 
 #include "grid_internal.h"
-#include "grid_phases.cuh"
+#include "grid_kernel.cuh"
 
 // ---------------------------------------------------------------- kernel
-__host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
-
 template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N>
 __global__ void __launch_bounds__(128, CHAIN_N > 0 ? 4 : 1) grid_kernel(const ModelDev<S>* __restrict__ gm, int N,
                                                    const S* __restrict__ q, const S* __restrict__ qd,
                                                    const S* __restrict__ x3, const S* __restrict__ x4,
                                                    S* __restrict__ out, S* __restrict__ out2,
                                                    S* __restrict__ out3) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int cfg = T == 8 ? 0 : (T == 16 ? 1 : 2);
-  constexpr int head = align16(model_head_bytes<S>());
-  const ModelDev<S>& M = *reinterpret_cast<const ModelDev<S>*>(smem);
-  {
-    const int4* src = reinterpret_cast<const int4*>(gm);
-    int4* dst = reinterpret_cast<int4*>(smem);
-    for (int i = threadIdx.x; i < head / 16; i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
-  const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? M.steps[cfg] : 0;
-  int stride;
-  if constexpr (CHAIN_N > 0) stride = ChainTopo<S, MODE, CHAIN_N>::layout().stride;
-  else if constexpr (CHAIN_N < 0) stride = ForestTopo<S, MODE, -CHAIN_N / 100, -CHAIN_N % 100>::layout().stride;
-  else stride = layout_of<MODE>(M).stride;
-  uint32_t* sched = reinterpret_cast<uint32_t*>(smem + head);
-  for (int i = threadIdx.x; i < nsteps * T; i += blockDim.x) sched[i] = gm->sched[M.sched_off[cfg] + i];
-  S* ws = reinterpret_cast<S*>(smem + head + align16(nsteps * T * 4));
-  __syncthreads();
-  constexpr int G = 32 / T;
-  const int lane32 = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
-  S* Wwarp = ws + warp * G * stride;
-  const int ntiles = (N + G - 1) / G;
-  for (int tile = blockIdx.x * wpb + warp; tile < ntiles; tile += gridDim.x * wpb)
-    process_tile<S, MODE, T, CPL, MAXD, MIXED, CHAIN_N>(M, gm, sched, nsteps, Wwarp, lane32, tile * G, N,
-                                                        q, qd, x3, x4, out, out2, out3);
+  grid_kernel_body<S, MODE, T, CPL, MAXD, MIXED, topo_for<S, MODE, CHAIN_N>>(gm, N, q, qd, x3, x4, out, out2, out3);
 }
 
 // ---------------------------------------------------------------- launcher
@@ -165,6 +137,12 @@ constexpr int kChainMaxN = 8;
 template <class S, int MODE>
 grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                          const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
+// Kernels compiled at run time for the model's topology (grid_nvrtc.cpp).
+template <class S>
+grid_status grid_gen_launch(grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
+                            const S* qd, const S* tau, S* J, S* qdd, S* Minv, int T, int CPL, int MAXD, int nsm,
+                            int smem_optin, cudaStream_t st);
+
 // Forests of K equal chains (grid_forest.cu), compiled for a few shapes.
 bool forest_compiled(int k, int l);
 template <class S, int MODE>
@@ -193,6 +171,14 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   // 12- and 30-DoF trees; up to 8 bodies, 8 lanes stay faster).
   if (T == 0) T = (n > 8 && N <= 2 * dev_info(m->device).nsm) ? 32 : (n <= 12 ? 8 : 16);
   const int cpl = (n + T - 1) / T;
+  if constexpr (MODE == MODE_GRAD && !MIXED) {
+    if (m->specialize_opt == 2 && (T == 8 || T == 16 || T == 32)) {
+      const int c = T == 8 ? (cpl <= 1 ? 1 : (cpl <= 2 ? 2 : 4)) : (T == 16 ? (cpl <= 1 ? 1 : 2) : 1);
+      const DevInfo di = dev_info(m->device);
+      return grid_gen_launch<S>(const_cast<grid_model*>(m), hm, dm, N, q, qd, x3, out, out2, out3, T, c,
+                                hm->maxd > 8 ? 32 : 8, di.nsm, di.smem_optin, st);
+    }
+  }
   if (T == 8) {
     if (cpl <= 1) return launch_d<S, MODE, 8, 1, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
     if (cpl <= 2) return launch_d<S, MODE, 8, 2, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);

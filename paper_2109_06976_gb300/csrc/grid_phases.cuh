@@ -15,8 +15,6 @@
 //  D  J = -M^-1 dc                                               lanes over outputs
 #pragma once
 
-#include <type_traits>
-
 #include "grid_internal.h"
 #include "spatial.cuh"
 
@@ -138,7 +136,7 @@ __device__ void ph_transforms(const Ctx<S, Tp>& c) {
       continue;
     }
     S s, co;
-    if constexpr (std::is_same<S, float>::value) sincosf(qk, &s, &co); else sincos(qk, &s, &co);
+    if constexpr (grid_same<S, float>::value) sincosf(qk, &s, &co); else sincos(qk, &s, &co);
     // E_J = R(a, q)^T = cos q 1 + (1 - cos q) a a^T - sin q a~
     S EJ[9];
     const S omc = S(1) - co;
@@ -316,7 +314,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     const S us0 = pr ? u[3] : u[0], us1 = pr ? u[4] : u[1], us2 = pr ? u[5] : u[2];   // S^T U
     const P Dk = P(a[0]) * P(us0) + P(a[1]) * P(us1) + P(a[2]) * P(us2);
     P Dinv;
-    if constexpr (std::is_same<P, float>::value) Dinv = __frcp_rn(Dk);
+    if constexpr (grid_same<P, float>::value) Dinv = __frcp_rn(Dk);
     else Dinv = __drcp_rn(Dk);
     if (l == 0) DINV[i] = Dinv;
 #pragma unroll
@@ -996,19 +994,21 @@ __device__ void ph_vjp_sweep(const Ctx<S, Tp>& c) {
 
 // One warp processes knot points k0 .. k0 + 32/T - 1 (those < N). M is the
 // shared-memory copy of the model, gM the same model in device memory.
-template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N = 0>
-__device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const uint32_t* __restrict__ sched,
+// CHAIN_N: 0 run-time topology, N > 0 a chain of N bodies, -(100 K + L) a forest of K chains of L
+template <class S, int MODE, int CHAIN_N>
+using topo_for = typename grid_cond<
+    CHAIN_N == 0, RtTopo<S, MODE>,
+    typename grid_cond<(CHAIN_N > 0), ChainTopo<S, MODE, (CHAIN_N > 0 ? CHAIN_N : 1)>,
+                       ForestTopo<S, MODE, (CHAIN_N < 0 ? -CHAIN_N / 100 : 1),
+                                  (CHAIN_N < 0 ? -CHAIN_N % 100 : 1)>>::type>::type;
+
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, class Tp>
+__device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, const uint32_t* __restrict__ sched,
                              int nsteps, S* Wwarp, int lane32, int k0, int N, const S* __restrict__ q,
                              const S* __restrict__ qd, const S* __restrict__ x3,
                              const S* __restrict__ x4, S* __restrict__ out, S* __restrict__ out2,
                              S* __restrict__ out3) {
-  using P = typename std::conditional<MIXED, double, S>::type;
-  // CHAIN_N: 0 run-time topology, N > 0 a chain of N bodies, -(100 K + L) a forest of K chains of L
-  using Tp = typename std::conditional<
-      CHAIN_N == 0, RtTopo<S, MODE>,
-      typename std::conditional<(CHAIN_N > 0), ChainTopo<S, MODE, (CHAIN_N > 0 ? CHAIN_N : 1)>,
-                                ForestTopo<S, MODE, (CHAIN_N < 0 ? -CHAIN_N / 100 : 1),
-                                           (CHAIN_N < 0 ? -CHAIN_N % 100 : 1)>>::type>::type;
+  using P = typename grid_cond<MIXED, double, S>::type;
   const Tp tp(M);
   const auto& L = tp.layout();     // the staged layout (runtime topology) or a compile-time constant
   const int n = tp.n();
@@ -1113,4 +1113,13 @@ __device__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const 
     }
     SYNC();
   }
+}
+
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N = 0>
+__device__ __forceinline__ void process_tile(const ModelDev<S>& M, const ModelDev<S>* gM, const uint32_t* __restrict__ sched,
+                             int nsteps, S* Wwarp, int lane32, int k0, int N, const S* __restrict__ q,
+                             const S* __restrict__ qd, const S* __restrict__ x3,
+                             const S* __restrict__ x4, S* __restrict__ out, S* __restrict__ out2,
+                             S* __restrict__ out3) {
+  process_tile_t<S, MODE, T, CPL, MAXD, MIXED, topo_for<S, MODE, CHAIN_N>>(M, gM, sched, nsteps, Wwarp, lane32, k0, N, q, qd, x3, x4, out, out2, out3);
 }
