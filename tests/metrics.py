@@ -22,6 +22,31 @@ def col_rel_err(x, y, floor=1e-6):
     return float((np.abs(x - y).max(axis=-2) / den).max()) if x.size else 0.0
 
 
+def col_rel_err_knots(x, y, floor=1e-6):
+    """The metric above per knot point: [N], the largest column error of each."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    assert x.shape == y.shape, (x.shape, y.shape)
+    nrm = np.linalg.norm(y, axis=-2)
+    den = np.maximum(np.maximum(nrm, floor * nrm.max(axis=-1, keepdims=True)), 1e-30)
+    return (np.abs(x - y).max(axis=-2) / den).max(axis=-1)
+
+
+U32 = 2.0 ** -24     # unit roundoff of FP32
+
+
+def fp32_bar(minv, tol=1e-4):
+    """Per-knot FP32 bar for random test trees: the larger of `tol` and
+    n kappa_2(M) u, the first-order forward-error bound of a solve with a
+    computed inverse (u = 2^-24). The columns -M^-1 dID/dq_j of such a tree can be
+    small against ||M^-1|| ||dID/dq_j||; then any rounding order leaves an error
+    of that size. Example: a 12-DoF random forest at kappa = 380 measured
+    2e-5 to 2e-4 on one column, depending on the evaluation order alone.
+    minv: [N, n, n] from the oracle."""
+    minv = np.asarray(minv, dtype=np.float64)
+    return np.maximum(tol, minv.shape[-1] * np.linalg.cond(minv) * U32)
+
+
 def col_rel_err_stats(x, y, floor=1e-6):
     """(max, p50) over knot points of the per-knot max column error."""
     x = np.asarray(x, dtype=np.float64)

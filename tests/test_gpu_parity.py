@@ -6,7 +6,7 @@ import pytest
 
 import grid_inputs as gi
 import oracle
-from tests.metrics import col_rel_err, col_rel_err_stats, vec_rel_err
+from tests.metrics import col_rel_err, col_rel_err_knots, col_rel_err_stats, fp32_bar, vec_rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -130,11 +130,13 @@ def test_chain_specialised_kernel(grid, n, seed, general, dtype):
     Js, qdds, Jg, qddg = (x.cpu().numpy() for x in (Js, qdds, Jg, qddg))
     ref = oracle.grad_fd(r, q64, qd64, tau64)
     tol, fl = (TOL32, 1e-4) if dtype == torch.float32 else (TOL64, 1e-6)
-    assert col_rel_err(Js, ref, floor=fl) <= tol
+    # FP32: random inertias, so the per-knot bound n kappa(M) u where it exceeds 1e-4
+    bar = fp32_bar(oracle.minv(r, q64)) if dtype == torch.float32 else tol
+    assert np.all(col_rel_err_knots(Js, ref, floor=fl) <= bar)
     assert vec_rel_err(qdds, oracle.fd(r, q64, qd64, tau64)) <= tol
     # both kernels meet the bar; they differ only in rounding order
-    assert col_rel_err(Jg, ref, floor=fl) <= tol
-    assert col_rel_err(Js, Jg, floor=fl) <= tol
+    assert np.all(col_rel_err_knots(Jg, ref, floor=fl) <= bar)
+    assert np.all(col_rel_err_knots(Js, Jg, floor=fl) <= 2 * bar)
     assert vec_rel_err(qdds, qddg) <= tol
 
 
@@ -164,8 +166,10 @@ def test_forest_specialised_kernel(grid, shape, dtype, N):
     ref = oracle.grad_fd(r, q64, qd64, tau64)
     fl = 1e-6 if shape is None else (1e-4 if dtype == torch.float32 else 1e-6)
     tol = TOL32 if dtype == torch.float32 else TOL64
-    assert col_rel_err(Js, ref, floor=fl) <= tol
-    assert col_rel_err(Jg, ref, floor=fl) <= tol
+    if shape is not None and dtype == torch.float32:   # random inertias: per-knot bar
+        tol = fp32_bar(oracle.minv(r, q64))
+    assert np.all(col_rel_err_knots(Js, ref, floor=fl) <= tol)
+    assert np.all(col_rel_err_knots(Jg, ref, floor=fl) <= tol)
 
 
 @pytest.mark.parametrize("key", WORKLOAD)
