@@ -314,7 +314,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     const S us0 = pr ? u[3] : u[0], us1 = pr ? u[4] : u[1], us2 = pr ? u[5] : u[2];   // S^T U
     const P Dk = P(a[0]) * P(us0) + P(a[1]) * P(us1) + P(a[2]) * P(us2);
     P Dinv;
-    if constexpr (grid_same<P, float>::value) Dinv = __frcp_rn(Dk);
+    if constexpr (grid_same<P, float>::value) Dinv = rcp_pivot(Dk);
     else Dinv = __drcp_rn(Dk);
     if (l == 0) DINV[i] = Dinv;
 #pragma unroll
@@ -392,8 +392,10 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
       if (l >= i && l < NB) {                  // P column l
         S mk = MI[i * MS + l];
         if (i > 0) {
-          const P ut = (P(Ui[0]) * P(t[0]) + P(Ui[1]) * P(t[1])) + (P(Ui[2]) * P(t[2]) + P(Ui[3]) * P(t[3])) +
-                       (P(Ui[4]) * P(t[4]) + P(Ui[5]) * P(t[5]));
+          P ut;
+          if constexpr (grid_same<P, S>::value) ut = dot6(Ui, t);
+          else ut = (P(Ui[0]) * P(t[0]) + P(Ui[1]) * P(t[1])) + (P(Ui[2]) * P(t[2]) + P(Ui[3]) * P(t[3])) +
+                    (P(Ui[4]) * P(t[4]) + P(Ui[5]) * P(t[5]));
           mk = S(P(mk) - Dinv * ut);
           MI[i * MS + l] = mk;
         }
@@ -446,8 +448,10 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
             for (int e = 0; e < 6; ++e) pp[e] = BP[(6 * tp.branch(p) + e) * n + k];
           }
           x_mul(E, r, pp, t);
-          const P ut = (P(Ui[0]) * P(t[0]) + P(Ui[1]) * P(t[1])) + (P(Ui[2]) * P(t[2]) + P(Ui[3]) * P(t[3])) +
-                       (P(Ui[4]) * P(t[4]) + P(Ui[5]) * P(t[5]));
+          P ut;
+          if constexpr (grid_same<P, S>::value) ut = dot6(Ui, t);
+          else ut = (P(Ui[0]) * P(t[0]) + P(Ui[1]) * P(t[1])) + (P(Ui[2]) * P(t[2]) + P(Ui[3]) * P(t[3])) +
+                    (P(Ui[4]) * P(t[4]) + P(Ui[5]) * P(t[5]));
           mk = S(P(mk) - Dinv * ut);
           MI[i * MS + k] = mk;
         }

@@ -22,6 +22,19 @@
 #endif
 #endif
 
+// 1 / x for an FP32 pivot D_i of the M^-1 recursion (a positive normal number): the
+// hardware approximation rcp.approx.ftz.f32, within 1 ulp (PTX ISA). It sits on the serial
+// path of the backward sweep, where the correctly rounded form measured 2.4 % slower.
+__device__ __forceinline__ float rcp_pivot(float x) {
+#if defined(__CUDA_ARCH__)
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+#else
+  return 1.0f / x;
+#endif
+}
+
 template <class S>
 __device__ __forceinline__ void cross3(const S* a, const S* b, S* o) {
   o[0] = a[1] * b[2] - a[2] * b[1];
@@ -32,9 +45,9 @@ __device__ __forceinline__ void cross3(const S* a, const S* b, S* o) {
 // o = X m
 template <class S>
 __device__ __forceinline__ void x_mul(const S* E, const S* r, const S* m, S* o) {
-  S t0 = m[3] - (r[1] * m[2] - r[2] * m[1]);
-  S t1 = m[4] - (r[2] * m[0] - r[0] * m[2]);
-  S t2 = m[5] - (r[0] * m[1] - r[1] * m[0]);
+  S t0 = m[3] - r[1] * m[2] + r[2] * m[1];   // v - r x w, two FMAs per row
+  S t1 = m[4] - r[2] * m[0] + r[0] * m[2];
+  S t2 = m[5] - r[0] * m[1] + r[1] * m[0];
 #if GRID_PAIRED_F32
   if constexpr (sizeof(S) == 4) {   // angular and linear rows as pairs
     const float2 p0 = make_float2(m[0], t0), p1 = make_float2(m[1], t1), p2 = make_float2(m[2], t2);
@@ -70,9 +83,9 @@ __device__ __forceinline__ void xt_mul(const S* E, const S* r, const S* f, S* o)
       a[i] = __ffma2_rn(make_float2(E[3 + i], E[3 + i]), p1, a[i]);
       a[i] = __ffma2_rn(make_float2(E[6 + i], E[6 + i]), p2, a[i]);
     }
-    o[0] = a[0].x + (r[1] * a[2].y - r[2] * a[1].y);
-    o[1] = a[1].x + (r[2] * a[0].y - r[0] * a[2].y);
-    o[2] = a[2].x + (r[0] * a[1].y - r[1] * a[0].y);
+    o[0] = a[0].x + r[1] * a[2].y - r[2] * a[1].y;
+    o[1] = a[1].x + r[2] * a[0].y - r[0] * a[2].y;
+    o[2] = a[2].x + r[0] * a[1].y - r[1] * a[0].y;
     o[3] = a[0].y; o[4] = a[1].y; o[5] = a[2].y;
     return;
   }
@@ -83,9 +96,9 @@ __device__ __forceinline__ void xt_mul(const S* E, const S* r, const S* f, S* o)
   S n0 = E[0] * f[0] + E[3] * f[1] + E[6] * f[2];
   S n1 = E[1] * f[0] + E[4] * f[1] + E[7] * f[2];
   S n2 = E[2] * f[0] + E[5] * f[1] + E[8] * f[2];
-  o[0] = n0 + (r[1] * g2 - r[2] * g1);
-  o[1] = n1 + (r[2] * g0 - r[0] * g2);
-  o[2] = n2 + (r[0] * g1 - r[1] * g0);
+  o[0] = n0 + r[1] * g2 - r[2] * g1;
+  o[1] = n1 + r[2] * g0 - r[0] * g2;
+  o[2] = n2 + r[0] * g1 - r[1] * g0;
   o[3] = g0; o[4] = g1; o[5] = g2;
 }
 
@@ -93,12 +106,12 @@ __device__ __forceinline__ void xt_mul(const S* E, const S* r, const S* f, S* o)
 template <class S>
 __device__ __forceinline__ void i_mul(const S* in, const S* m, S* o) {
   const S mass = in[0], h0 = in[1], h1 = in[2], h2 = in[3];
-  o[0] = in[4] * m[0] + in[7] * m[1] + in[8] * m[2] + (h1 * m[5] - h2 * m[4]);
-  o[1] = in[7] * m[0] + in[5] * m[1] + in[9] * m[2] + (h2 * m[3] - h0 * m[5]);
-  o[2] = in[8] * m[0] + in[9] * m[1] + in[6] * m[2] + (h0 * m[4] - h1 * m[3]);
-  o[3] = mass * m[3] - (h1 * m[2] - h2 * m[1]);
-  o[4] = mass * m[4] - (h2 * m[0] - h0 * m[2]);
-  o[5] = mass * m[5] - (h0 * m[1] - h1 * m[0]);
+  o[0] = in[4] * m[0] + in[7] * m[1] + in[8] * m[2] + h1 * m[5] - h2 * m[4];
+  o[1] = in[7] * m[0] + in[5] * m[1] + in[9] * m[2] + h2 * m[3] - h0 * m[5];
+  o[2] = in[8] * m[0] + in[9] * m[1] + in[6] * m[2] + h0 * m[4] - h1 * m[3];
+  o[3] = mass * m[3] - h1 * m[2] + h2 * m[1];
+  o[4] = mass * m[4] - h2 * m[0] + h0 * m[2];
+  o[5] = mass * m[5] - h0 * m[1] + h1 * m[0];
 }
 
 // o = a x b (motion cross product, Eq. (2))
@@ -128,9 +141,9 @@ template <class S>
 __device__ __forceinline__ S x_mul_c(const S* E, const S* r, const S* m, int c) {
   if (c < 3) return E[3 * c] * m[0] + E[3 * c + 1] * m[1] + E[3 * c + 2] * m[2];
   const int k = c - 3;
-  S t0 = m[3] - (r[1] * m[2] - r[2] * m[1]);
-  S t1 = m[4] - (r[2] * m[0] - r[0] * m[2]);
-  S t2 = m[5] - (r[0] * m[1] - r[1] * m[0]);
+  S t0 = m[3] - r[1] * m[2] + r[2] * m[1];   // v - r x w, two FMAs per row
+  S t1 = m[4] - r[2] * m[0] + r[0] * m[2];
+  S t2 = m[5] - r[0] * m[1] + r[1] * m[0];
   return E[3 * k] * t0 + E[3 * k + 1] * t1 + E[3 * k + 2] * t2;
 }
 
@@ -215,7 +228,7 @@ __device__ __forceinline__ S xt_mul_c(const S* Er, const S* f, int c) {
   const S g1 = Er[c1] * f[3] + Er[3 + c1] * f[4] + Er[6 + c1] * f[5];
   const S g2 = Er[c2] * f[3] + Er[3 + c2] * f[4] + Er[6 + c2] * f[5];
   const S nc = Er[c] * f[0] + Er[3 + c] * f[1] + Er[6 + c] * f[2];
-  return nc + (Er[9 + c1] * g2 - Er[9 + c2] * g1);
+  return nc + Er[9 + c1] * g2 - Er[9 + c2] * g1;
 }
 
 // Component c of I m.

@@ -6,7 +6,7 @@ import pytest
 
 import grid_inputs as gi
 import oracle
-from tests.metrics import col_err_split, col_rel_err
+from tests.metrics import FLOOR32, col_err_split, col_rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,12 +41,12 @@ def test_joint_types_match_oracle(grid, robot, dtype):
     # side and their mass matrices reach condition numbers ~1e3, so FP32 rounding
     # (~1e-7 of the largest column, times the conditioning) is held to 1e-3,
     # and a column counts as small below 1e-3 of the largest when a joint is
-    # prismatic (different units) instead of 1e-6.
+    # prismatic (different units) instead of 1e-4.
     if dtype == torch.float64:
         tol, floor = (1e-10, 1e-12), 1e-6
     else:
         tol = (1e-3, 1e-5) if robot.name.startswith("mixed") else (1e-4, 1e-5)
-        floor = 1e-3 if np.any(robot.jtypes() == gi.PRISMATIC) else 1e-6
+        floor = 1e-3 if np.any(robot.jtypes() == gi.PRISMATIC) else FLOOR32
 
     def ok(x, y, vec=False):
         x, y = np.asarray(x), np.asarray(y)

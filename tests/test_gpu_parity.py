@@ -6,7 +6,7 @@ import pytest
 
 import grid_inputs as gi
 import oracle
-from tests.metrics import col_rel_err, col_rel_err_knots, col_rel_err_stats, fp32_bar, vec_rel_err
+from tests.metrics import FLOOR32, FLOOR64, col_rel_err, col_rel_err_knots, col_rel_err_stats, fp32_bar, vec_rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,7 +51,7 @@ def _inputs(n, N, seed, dtype):
 
 
 def _floor(key, dtype):
-    return 1e-6 if (isinstance(key, str) or dtype == torch.float64) else 1e-4
+    return FLOOR64 if dtype == torch.float64 else FLOOR32
 
 
 CASES = [(k, dt) for k in WORKLOAD for dt in (torch.float32, torch.float64)] + \
@@ -164,7 +164,7 @@ def test_forest_specialised_kernel(grid, shape, dtype, N):
     Js = spec.grad_fd(q, qd, tau).cpu().numpy()
     Jg = gen.grad_fd(q, qd, tau).cpu().numpy()
     ref = oracle.grad_fd(r, q64, qd64, tau64)
-    fl = 1e-6 if shape is None else (1e-4 if dtype == torch.float32 else 1e-6)
+    fl = FLOOR32 if dtype == torch.float32 else FLOOR64
     tol = TOL32 if dtype == torch.float32 else TOL64
     if shape is not None and dtype == torch.float32:   # random inertias: per-knot bar
         tol = fp32_bar(oracle.minv(r, q64))
@@ -180,7 +180,7 @@ def test_grad_fd_workload_sizes(grid, key):
     for N in (16, 128, 512) if key != "tree30" else (128, 1024):
         (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, N, gi.workload_seed(2, N), torch.float32)
         J = m.grad_fd(q, qd, tau).cpu().numpy()
-        mx, p50 = col_rel_err_stats(J, oracle.grad_fd(r, q64, qd64, tau64, nthreads=8))
+        mx, p50 = col_rel_err_stats(J, oracle.grad_fd(r, q64, qd64, tau64, nthreads=8), FLOOR32)
         assert mx <= TOL32, (N, mx, p50)
 
 
@@ -196,7 +196,7 @@ def test_grad_fd_bench_size_sampled(grid):
     idx = np.sort(gi.Stream(5).u64(256) % np.uint64(N)).astype(np.int64)
     Js = J[torch.from_numpy(idx).cuda()].cpu().numpy()
     ref = oracle.grad_fd(r, q64[idx], qd64[idx], tau64[idx], nthreads=8)
-    assert col_rel_err(Js, ref) <= TOL32
+    assert col_rel_err(Js, ref, FLOOR32) <= TOL32
     assert torch.isfinite(J).all()
 
 
@@ -208,8 +208,8 @@ def test_mixed_precision_tree30(grid):
     mm = _model(grid, "tree30", "mixed")
     (q, qd, tau), (q64, qd64, tau64) = _inputs(30, 128, gi.workload_seed(3, 128), torch.float32)
     ref = oracle.grad_fd(r, q64, qd64, tau64, nthreads=8)
-    e32 = col_rel_err(m32.grad_fd(q, qd, tau).cpu().numpy(), ref)
-    emx = col_rel_err(mm.grad_fd(q, qd, tau).cpu().numpy(), ref)
+    e32 = col_rel_err(m32.grad_fd(q, qd, tau).cpu().numpy(), ref, FLOOR32)
+    emx = col_rel_err(mm.grad_fd(q, qd, tau).cpu().numpy(), ref, FLOOR32)
     assert e32 <= TOL32 and emx <= TOL32, (e32, emx)
 
 
@@ -280,7 +280,7 @@ def test_precision_report_tree30(grid, capsys):
                 "grad_fd": (J.cpu().numpy(), ref_J),
             }
             for name, (x, y) in outs.items():
-                mx, p50 = col_rel_err_stats(x, y)
+                mx, p50 = col_rel_err_stats(x, y, FLOOR32)
                 lines.append(f"tree30 {prec:5s} N={N:4d} {name:8s} max {mx:.2e} p50 {p50:.2e}")
                 assert mx <= TOL32, lines[-1]
     with capsys.disabled():
