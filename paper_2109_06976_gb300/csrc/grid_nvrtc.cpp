@@ -96,6 +96,7 @@ std::string kernel_source(const ModelDev<S>& D, int T, int CPL, int MAXD) {
   s += "template <class S, int MODE>\nstruct GenTopo {\n"
        "  static constexpr int kUnroll = " + N + ";\n"
        "  static constexpr int kChainN = 0;\n"
+       "  static constexpr bool kConsecutivePaths = false;\n"
        "  __device__ explicit GenTopo(const ModelDev<S>&) {}\n"
        "  GRID_HD static constexpr KnotLayout layout() { return make_layout(" + N + ", " + std::to_string(D.nsk) +
        ", " + std::to_string(D.nbranch) + ", (int)sizeof(S), layout_kind(MODE)); }\n"

@@ -29,6 +29,7 @@ template <class S, int MODE>
 struct RtTopo {
   static constexpr int kUnroll = 1;
   static constexpr int kChainN = 0;       // not a compile-time chain
+  static constexpr bool kConsecutivePaths = false;
   const ModelDev<S>& M;
   __device__ explicit RtTopo(const ModelDev<S>& m) : M(m) {}
   __device__ const KnotLayout& layout() const { return layout_of<MODE>(M); }
@@ -50,6 +51,7 @@ template <class S, int MODE, int N>
 struct ChainTopo {
   static constexpr int kUnroll = N;
   static constexpr int kChainN = N;
+  static constexpr bool kConsecutivePaths = true;   // ancestor at depth d of k: k - depth(k) + d
   __device__ explicit ChainTopo(const ModelDev<S>&) {}
   GRID_HD static constexpr KnotLayout layout() {
     return make_layout(N, N * (N + 1) / 2, 0, (int)sizeof(S), layout_kind(MODE));
@@ -75,6 +77,7 @@ template <class S, int MODE, int K, int L>
 struct ForestTopo {
   static constexpr int kUnroll = K * L;
   static constexpr int kChainN = 0;
+  static constexpr bool kConsecutivePaths = true;
   __device__ explicit ForestTopo(const ModelDev<S>&) {}
   GRID_HD static constexpr KnotLayout layout() {
     return make_layout(K * L, K * L * (L + 1) / 2, 0, (int)sizeof(S), layout_kind(MODE));
@@ -113,6 +116,15 @@ struct Ctx {
 #define GRID_SHFL(v, src) __shfl_sync(0xffffffffu, (v), (src))
 #endif
 #define SYNC() GRID_SYNC()
+
+// Body of row d of body k's subspace rows (its ancestor at depth d): stored in
+// the row's slot 7, or k - depth(k) + d where every root path is numbered
+// consecutively (chains, forests of chains), which saves a conversion per row.
+template <class Tp, class S>
+__device__ __forceinline__ int row_body(int k, int dk, int d, S slot7) {
+  if constexpr (Tp::kConsecutivePaths) return k - dk + d;
+  else return (int)slot7;
+}
 
 // ---------------------------------------------------------------- B1
 template <class S, int T, class Tp>
@@ -503,21 +515,19 @@ __device__ void ph_rnea_bodies(const Ctx<S, Tp>& c, int qdd_off) {
       ld4(rows + 8 * d, s);
       ld4(rows + 8 * d + 4, s + 4);
       const S qd = s[6];
-      S sq[6], t[6];
+      S sq[6];
 #pragma unroll
       for (int e = 0; e < 6; ++e) { sq[e] = s[e] * qd; v[e] += sq[e]; }
-      crm_mul(v, sq, t);
+      crm_mul_acc(v, sq, a);
       S qdd = S(0);
-      if (qdd_off >= 0) qdd = W[qdd_off + tp.perm((int)s[7])];
+      if (qdd_off >= 0) qdd = W[qdd_off + tp.perm(row_body<Tp>(k, dk, d, s[7]))];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) a[e] += t[e] + s[e] * qdd;
+      for (int e = 0; e < 6; ++e) a[e] += s[e] * qdd;
     }
-    S g[6], ia[6], vg[6];
+    S g[6], ia[6];
     i_mul(M.inert[k], v, g);
     i_mul(M.inert[k], a, ia);
-    crf_mul(v, g, vg);
-#pragma unroll
-    for (int e = 0; e < 6; ++e) ia[e] += vg[e];
+    crf_mul_acc(v, g, ia);
     st6(W + L.VG + 12 * k, v);
     st6u(W + L.VG + 12 * k + 6, g);
     st6(W + U + L.A + 8 * k, a);
@@ -593,7 +603,7 @@ __device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
         S s[8];
         ld4(rows + 8 * d, s);
         ld4(rows + 8 * d + 4, s + 4);
-        const S qdd = W[L.QDD + (int)s[7]];
+        const S qdd = W[L.QDD + row_body<Tp>(k, dk, d, s[7])];
 #pragma unroll
         for (int e = 0; e < 6; ++e) da[e] += s[e] * qdd;
       }
@@ -605,14 +615,11 @@ __device__ void ph_update_and_forces(const Ctx<S, Tp>& c) {
     ld6(FA + 8 * k, fo);
     const S qdk = W[L.QD + tp.perm(k)];
     const bool pr = tp.prism(k);
-    S idt[6], vxs[6], w[6];
-    i_mul(M.inert[k], da, idt);
+    S vxs[6], w[6];
+    i_mul_acc(M.inert[k], da, fo);
     cross_s(v, ax, pr, vxs);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      w[e] = a[e] + da[e] - qdk * vxs[e];
-      fo[e] += idt[e];
-    }
+    for (int e = 0; e < 6; ++e) w[e] = a[e] + da[e] - qdk * vxs[e];
     st6(FA + 8 * k, fo);
     S B[6];
     cross_s(w, ax, pr, B);
@@ -758,18 +765,13 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
     }
     {
       const S sq[3] = {ax[0] * qdk, ax[1] * qdk, ax[2] * qdk};
-      S t[6];
-      cross_s(ndv, sq, pr, t);   // dv x S qd
-#pragma unroll
-      for (int e = 0; e < 6; ++e) nda[e] += t[e];
+      cross_s_acc(ndv, sq, pr, nda);   // + dv x S qd
     }
-    S df[6], t1[6], t2[6], idv[6];
+    S df[6], idv[6];
     i_mul(in, nda, df);
-    crf_mul(ndv, g, t1);
+    crf_mul_acc(ndv, g, df);
     i_mul(in, ndv, idv);
-    crf_mul(v, idv, t2);
-#pragma unroll
-    for (int e = 0; e < 6; ++e) df[e] += t1[e] + t2[e];
+    crf_mul_acc(v, idv, df);
     if (root && uq) {                          // backward-pass term S x* F of Alg. 1
       S Ph[6];
       ld6u(W + L.BPH + 12 * k + 6, Ph);
@@ -778,13 +780,15 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
     }
     if constexpr (Tp::kChainN > 0) {
       // chain: body d is the ancestor at depth d; every step owns its body.
-      // Rows past depth dk are not needed: their loads repeat row dk and the
-      // result is discarded, which keeps the loop free of branches.
+      // Rows past depth dk are not needed: their loads read the rows of the
+      // next bodies (inside the table: skoff(k) + N - 1 < N (N + 1) / 2) and
+      // the result is discarded, which keeps the loop free of branches and
+      // its addresses constant offsets.
       static_assert(Tp::kChainN <= MAXD, "accumulators");
 #pragma unroll
       for (int d = 0; d < Tp::kChainN; ++d) {
         S sr[6];
-        ld6(rows + 8 * min(d, dk), sr);
+        ld6(rows + 8 * d, sr);
         const S t = dot6(sr, df);
         acc[d] += d <= dk ? t : S(0);
       }
@@ -906,7 +910,7 @@ __device__ void ph_vjp_seeds(const Ctx<S, Tp>& c) {
       S s[8];
       ld4(rows + 8 * d, s);
       ld4(rows + 8 * d + 4, s + 4);
-      const S lam = W[U + L.LAM + (int)s[7]];
+      const S lam = W[U + L.LAM + row_body<Tp>(k, dk, d, s[7])];
 #pragma unroll
       for (int e = 0; e < 6; ++e) psi[e] += s[e] * lam;
     }

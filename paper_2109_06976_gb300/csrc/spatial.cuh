@@ -136,6 +136,43 @@ __device__ __forceinline__ void crf_mul(const S* a, const S* f, S* o) {
   o[5] = a[0] * f[4] - a[1] * f[3];
 }
 
+// Accumulating forms, o += ...: the first product of every component folds into an
+// FMA with the accumulator instead of a separate add.
+template <class S>
+__device__ __forceinline__ void i_mul_acc(const S* in, const S* m, S* o) {
+  const S mass = in[0], h0 = in[1], h1 = in[2], h2 = in[3];
+  o[0] = o[0] + in[4] * m[0] + in[7] * m[1] + in[8] * m[2] + h1 * m[5] - h2 * m[4];
+  o[1] = o[1] + in[7] * m[0] + in[5] * m[1] + in[9] * m[2] + h2 * m[3] - h0 * m[5];
+  o[2] = o[2] + in[8] * m[0] + in[9] * m[1] + in[6] * m[2] + h0 * m[4] - h1 * m[3];
+  o[3] = o[3] + mass * m[3] - h1 * m[2] + h2 * m[1];
+  o[4] = o[4] + mass * m[4] - h2 * m[0] + h0 * m[2];
+  o[5] = o[5] + mass * m[5] - h0 * m[1] + h1 * m[0];
+}
+template <class S>
+__device__ __forceinline__ void crm_mul_acc(const S* a, const S* b, S* o) {
+  o[0] = o[0] + a[1] * b[2] - a[2] * b[1];
+  o[1] = o[1] + a[2] * b[0] - a[0] * b[2];
+  o[2] = o[2] + a[0] * b[1] - a[1] * b[0];
+  o[3] = o[3] + a[1] * b[5] - a[2] * b[4] + a[4] * b[2] - a[5] * b[1];
+  o[4] = o[4] + a[2] * b[3] - a[0] * b[5] + a[5] * b[0] - a[3] * b[2];
+  o[5] = o[5] + a[0] * b[4] - a[1] * b[3] + a[3] * b[1] - a[4] * b[0];
+}
+template <class S>
+__device__ __forceinline__ void crf_mul_acc(const S* a, const S* f, S* o) {
+  o[0] = o[0] + a[1] * f[2] - a[2] * f[1] + a[4] * f[5] - a[5] * f[4];
+  o[1] = o[1] + a[2] * f[0] - a[0] * f[2] + a[5] * f[3] - a[3] * f[5];
+  o[2] = o[2] + a[0] * f[1] - a[1] * f[0] + a[3] * f[4] - a[4] * f[3];
+  o[3] = o[3] + a[1] * f[5] - a[2] * f[4];
+  o[4] = o[4] + a[2] * f[3] - a[0] * f[5];
+  o[5] = o[5] + a[0] * f[4] - a[1] * f[3];
+}
+template <class S>
+__device__ __forceinline__ void cross3_acc(const S* a, const S* b, S* o) {
+  o[0] = o[0] + a[1] * b[2] - a[2] * b[1];
+  o[1] = o[1] + a[2] * b[0] - a[0] * b[2];
+  o[2] = o[2] + a[0] * b[1] - a[1] * b[0];
+}
+
 // Component c (0..5) of X m, reading operands from memory.
 template <class S>
 __device__ __forceinline__ S x_mul_c(const S* E, const S* r, const S* m, int c) {
@@ -195,6 +232,16 @@ __device__ __forceinline__ void cross_s(const S* v, const S* a, bool pr, S* out)
   } else {
     cross3(v, a, out);
     cross3(v + 3, a, out + 3);
+  }
+}
+// o += v x S
+template <class S>
+__device__ __forceinline__ void cross_s_acc(const S* v, const S* a, bool pr, S* o) {
+  if (pr) {
+    cross3_acc(v, a, o + 3);
+  } else {
+    cross3_acc(v, a, o);
+    cross3_acc(v + 3, a, o + 3);
   }
 }
 // S x* f = [a x n; a x f] (revolute) or [a x f; 0] (prismatic), f = [n; f]
