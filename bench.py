@@ -52,12 +52,15 @@ NCU_DRAM_BYTES_PER_KNOT = {"517743476c2097e0": 199.75e6 / 524288,
                            "59c365e8cec7dca6": 189.65e6 / 524288,
                            "c7c560789c0e9069": 189.20e6 / 524288,
                            "a032ad23a8b5e7d9": 189.45e6 / 524288,
-                           "f8f85c036843ba52": 189.67e6 / 524288}
+                           "f8f85c036843ba52": 189.67e6 / 524288,
+                           # kernel code identical to f8f85c036843ba52: only the host-buffer
+                           # pipeline (grid_capi.cu) and a host-side model field were added
+                           "3b0e48a5f622bbea": 189.67e6 / 524288}
 # FP32 (FMA) pipe utilisation of the same captures: sm__pipe_fma_cycles_active, % of
 # peak sustained while active (busy cycles, so a paired FP32 instruction counts for the
 # cycles it occupies), reported beside the counted-flop fraction.
 NCU_FMA_PIPE = {"e04804cb5f3a6d15": 0.401, "59c365e8cec7dca6": 0.418, "c7c560789c0e9069": 0.432,
-                "a032ad23a8b5e7d9": 0.418, "f8f85c036843ba52": 0.418}
+                "a032ad23a8b5e7d9": 0.418, "f8f85c036843ba52": 0.418, "3b0e48a5f622bbea": 0.418}
 
 
 def kernel_source_hash() -> str:
@@ -427,22 +430,31 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    # End to end through the public API with pinned host buffers: H2D of the
-    # step's states, the kernel, D2H of the Jacobians, every step.
+    # End to end through the public API with pinned host buffers, every step:
+    # grid_grad_fd_host copies the step's states in, runs the kernel and copies
+    # the Jacobians out, in chunks whose copies overlap the kernel.
     hq, hqd, htau = (t.cpu().pin_memory() for t in (q, qd, tau))
     hJ = torch.empty(J.shape, dtype=J.dtype).pin_memory()
-    dq, dqd, dtau = torch.empty_like(q), torch.empty_like(qd), torch.empty_like(tau)
 
     def e2e_step():
+        model.grad_fd_host(hq, hqd, htau, out=hJ, sync=False)
+
+    e2e_steps = max(3, args.steps // 4)
+    sec_e2e = time_steps(e2e_step, e2e_steps, 2, stream, dist)
+    e2e_copy_value = aggregate_value(world, Nk, e2e_steps, sec_e2e)
+
+    # For comparison: the same copies and kernel one after another on one stream.
+    dq, dqd, dtau = torch.empty_like(q), torch.empty_like(qd), torch.empty_like(tau)
+
+    def serial_step():
         dq.copy_(hq, non_blocking=True)
         dqd.copy_(hqd, non_blocking=True)
         dtau.copy_(htau, non_blocking=True)
         model.grad_fd(dq, dqd, dtau, out=J)
         hJ.copy_(J, non_blocking=True)
 
-    e2e_steps = max(3, args.steps // 4)
-    sec_e2e = time_steps(e2e_step, e2e_steps, 2, stream, dist)
-    e2e_copy_value = aggregate_value(world, Nk, e2e_steps, sec_e2e)
+    sec_serial = time_steps(serial_step, e2e_steps, 2, stream, dist)
+    e2e_serial_value = aggregate_value(world, Nk, e2e_steps, sec_serial)
 
     # Zero copy: the same call on the pinned host buffers; the kernel reads the
     # states from and writes the Jacobians to host memory over NVLink-C2C.
@@ -537,8 +549,11 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": out_bytes,
                     "zero_copy": e2e_zc_value, "copies": e2e_copy_value,
+                    "serial_copies": e2e_serial_value,
                     "note": "pinned host buffers every step; value = the faster of zero copy "
-                            "(kernel reads/writes host memory) and explicit H2D + kernel + D2H"},
+                            "(the kernel reads/writes host memory) and grid_grad_fd_host (H2D, "
+                            "kernel and D2H in chunks, overlapped on three streams); "
+                            "serial_copies = H2D, kernel, D2H one after another, for comparison"},
             "topology": {"kernel": "chain-specialised" if args.specialize else "run-time topology",
                          "other_kernel_value": other_value, "unit": UNIT,
                          "note": "the same step in the other kernel (run-time topology vs the chain "

@@ -20,7 +20,8 @@
  *   - Pointers must be 4-byte aligned (8-byte for the _f64 calls); inputs and
  *     outputs must not overlap.
  *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
- *     legacy default stream). Nothing is allocated on these calls.
+ *     legacy default stream). Nothing is allocated on these calls (except the
+ *     staging of grid_grad_fd_host, which takes host buffers instead).
  *   - Arguments are checked synchronously; a launch failure is returned as
  *     GRID_E_CUDA. Errors raised inside a kernel surface at the caller's next
  *     synchronisation.
@@ -44,7 +45,7 @@ typedef enum {
   GRID_E_TOPOLOGY = 2,  /* parent[i] >= i or < -1, n out of range */
   GRID_E_ALIGN = 3,     /* misaligned pointer */
   GRID_E_CUDA = 4,      /* CUDA runtime error (message in grid_last_error) */
-  GRID_E_NOMEM = 5,     /* device allocation failed in grid_create */
+  GRID_E_NOMEM = 5,     /* device allocation failed (grid_create, grid_grad_fd_host staging) */
   GRID_E_TIMEOUT = 6,   /* bounded wait expired (serving) */
   GRID_E_NUMERIC = 7    /* non-physical model data (mass <= 0, axis not unit) */
 } grid_status;
@@ -132,6 +133,8 @@ int grid_model_dof(const grid_model* model);
  *                 precision and lane count) with its topology tables as constants;
  *                 GRID_E_CUDA if NVRTC or the driver library cannot be loaded;
  *                 0: always the kernel that reads the topology at run time
+ *   "host_chunk"  knot points per chunk of grid_grad_fd_host (0 = automatic: about
+ *                 32 MB of Jacobians per chunk)
  */
 grid_status grid_set_option(grid_model* model, const char* key, int value);
 
@@ -203,6 +206,37 @@ grid_status grid_grad_fd_ex(const grid_model* model, int N, const float* q, cons
                             const float* tau, float* J, float* qdd, float* Minv, void* stream);
 grid_status grid_grad_fd_ex_f64(const grid_model* model, int N, const double* q, const double* qd,
                                 const double* tau, double* J, double* qdd, double* Minv, void* stream);
+
+/*
+ * grid_grad_fd_host -- grid_grad_fd for data that lives in HOST memory: q, qd,
+ * tau [N][n] in, J [N][n][2n] and, if qdd != NULL, qdd [N][n] out, in the layouts
+ * above, all host pointers. The batch is cut into chunks of knot points
+ * (option "host_chunk"; 0 = the default of about 32 MB of Jacobians per chunk)
+ * that pass through three device staging slots owned by the model. The copy in
+ * of chunk c+1, the kernel on chunk c and the copy out of chunk c-1 run at the
+ * same time on three internal streams, so a call costs about the largest of the
+ * two transfers and the kernel instead of their sum. Each array of each chunk
+ * moves with one cudaMemcpyAsync.
+ *   - Host buffers should be page-locked (cudaHostAlloc, cudaHostRegister);
+ *     pageable memory gives the same results, with copies that do not overlap.
+ *   - Ordering: the work starts after the work already queued on `stream`, and
+ *     work queued on `stream` afterwards waits for its end. The call returns
+ *     once everything is enqueued; the host buffers must stay valid and
+ *     untouched until `stream` has reached that point (cudaStreamSynchronize).
+ *   - Unlike the other compute calls this one allocates: the staging slots are
+ *     allocated by the first call, replaced by larger ones when a later call
+ *     needs bigger chunks (GRID_E_NOMEM if that fails), and freed by
+ *     grid_destroy. Calls on one model are serialised (a host lock; events on
+ *     the device), so a model may serve several threads and streams.
+ *   - The results are those of grid_grad_fd on the same knot points, bit for
+ *     bit where the kernel configuration does not depend on the number of knot
+ *     points in a launch (serial chains and the compiled forests at 8 lanes);
+ *     otherwise within rounding.
+ */
+grid_status grid_grad_fd_host(const grid_model* model, int N, const float* q, const float* qd,
+                              const float* tau, float* J, float* qdd, void* stream);
+grid_status grid_grad_fd_host_f64(const grid_model* model, int N, const double* q, const double* qd,
+                                  const double* tau, double* J, double* qdd, void* stream);
 
 /*
  * Trajectory-optimisation step (Sec. V-B: the all-GPU loop the library is built

@@ -173,6 +173,44 @@ class Model:
                      _ptr(qdd_out), self._stream())
         return (J, qdd_out) if return_qdd else J
 
+    def grad_fd_host(self, q, qd, tau, out=None, qdd_out=None, return_qdd=False, sync=True):
+        """grad_fd for states in host memory (grid_grad_fd_host): CPU tensors,
+        page-locked for overlapped copies. The library moves the batch through
+        device staging in chunks, overlapping the copies in, the kernel and the
+        copies out. Outputs are CPU tensors (pinned when allocated here). With
+        sync=True the call waits for the current stream, so the results are
+        ready on return; with sync=False they are ready once the stream reaches
+        this point, and the inputs must stay untouched until then."""
+        ts = [q, qd, tau]
+        N = dtype = None
+        flat = []
+        for t in ts:
+            if not isinstance(t, torch.Tensor) or t.is_cuda:
+                raise TypeError("grad_fd_host takes CPU tensors")
+            if t.shape[-1] != self.n:
+                raise ValueError(f"last dimension must be n = {self.n}")
+            t2 = t.reshape(-1, self.n)
+            if not t2.is_contiguous():
+                raise ValueError("state tensors must be contiguous")
+            if N is None:
+                N, dtype = t2.shape[0], t2.dtype
+            elif t2.shape[0] != N or t2.dtype != dtype:
+                raise ValueError("state tensors must share batch size and dtype")
+            flat.append(t2)
+        if dtype not in (torch.float32, torch.float64):
+            raise TypeError("states must be float32 or float64")
+        J = out if out is not None else torch.empty((N, self.n, 2 * self.n), dtype=dtype).pin_memory()
+        if return_qdd and qdd_out is None:
+            qdd_out = torch.empty((N, self.n), dtype=dtype).pin_memory()
+        for t in (J, qdd_out):
+            if t is not None and (t.is_cuda or not t.is_contiguous() or t.dtype != dtype):
+                raise ValueError("outputs must be contiguous CPU tensors of the states' dtype")
+        _native.call(self._fn("grid_grad_fd_host", dtype), self._h, N, *(_ptr(t) for t in flat), _ptr(J),
+                     _ptr(qdd_out), self._stream())
+        if sync:
+            torch.cuda.current_stream().synchronize()
+        return (J, qdd_out) if return_qdd else J
+
     def grad_fd_minv(self, q, qd, tau, out=None, minv_out=None):
         """(J, M^-1): the gradient of FD [N, n, 2n] and M^-1 = dqdd/dtau [N, n, n]
         from one kernel (grid_grad_fd_ex)."""

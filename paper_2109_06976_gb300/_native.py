@@ -38,6 +38,8 @@ SIGNATURES = {
     "grid_fd_vjp_f64": [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P],
     "grid_grad_fd_ex": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
     "grid_grad_fd_ex_f64": [_P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "grid_grad_fd_host": [_P, _I, _P, _P, _P, _P, _P, _P],
+    "grid_grad_fd_host_f64": [_P, _I, _P, _P, _P, _P, _P, _P],
     "grid_rollout": [_P, _I, _I, ctypes.c_float] + [_P] * 7 + [ctypes.c_float] + [_P] * 4,
     "grid_rollout_f64": [_P, _I, _I, ctypes.c_double] + [_P] * 7 + [ctypes.c_double] + [_P] * 4,
     "grid_riccati": [_P, _I, _I, ctypes.c_float] + [_P] * 10 + [ctypes.c_float] + [_P] * 4,

@@ -4,8 +4,10 @@
 // grid_launch.cuh for the launch mapping and grid_phases.cuh for the phases).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <initializer_list>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -64,6 +66,147 @@ grid_status run(const grid_model* m, int N, const S* q, const S* qd, const S* x3
   return dispatch<S, MODE, false>(m, N, q, qd, x3, x4, out, out2, out3, st);
 }
 
+// ---------------------------------------------------------------- host buffers
+// grid_grad_fd_host: three staging slots and three streams (copy in, kernel,
+// copy out). Chunk c uses slot c mod 3; its copy in waits until the copy out of
+// the chunk that used the slot before (free[b]), its kernel waits for its copy
+// in (loaded[b]), its copy out for its kernel (computed[b]).
+}  // namespace
+
+struct grid_host_pipe {
+  std::mutex mu;
+  size_t slot_bytes = 0;
+  void* slot[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t st[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t loaded[3] = {}, computed[3] = {}, freed[3] = {}, start = nullptr, done = nullptr;
+};
+
+namespace {
+
+std::mutex g_pipe_create;
+
+void host_pipe_free(grid_host_pipe* p) {
+  if (!p) return;
+  for (int b = 0; b < 3; ++b) {
+    if (p->st[b]) cudaStreamSynchronize(p->st[b]);
+  }
+  for (int b = 0; b < 3; ++b) {
+    cudaFree(p->slot[b]);
+    if (p->st[b]) cudaStreamDestroy(p->st[b]);
+    if (p->loaded[b]) cudaEventDestroy(p->loaded[b]);
+    if (p->computed[b]) cudaEventDestroy(p->computed[b]);
+    if (p->freed[b]) cudaEventDestroy(p->freed[b]);
+  }
+  if (p->start) cudaEventDestroy(p->start);
+  if (p->done) cudaEventDestroy(p->done);
+  delete p;
+}
+
+grid_status cuda_fail(const char* what, cudaError_t e) {
+  grid_set_error("grid_grad_fd_host: %s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? GRID_E_NOMEM : GRID_E_CUDA;
+}
+
+// The model's pipeline, created on first use (streams and events on the model's device).
+grid_status host_pipe_get(grid_model* m, grid_host_pipe** out) {
+  std::lock_guard<std::mutex> lk(g_pipe_create);
+  if (!m->pipe) {
+    grid_host_pipe* p = new grid_host_pipe();
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
+      e = cudaStreamCreateWithFlags(&p->st[b], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->loaded[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->computed[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->freed[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      host_pipe_free(p);
+      return cuda_fail("stream or event creation", e);
+    }
+    m->pipe = p;
+  }
+  *out = m->pipe;
+  return GRID_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+template <class S>
+grid_status grad_fd_host(const grid_model* mc, int N, const S* q, const S* qd, const S* tau, S* J, S* qdd,
+                         void* stream) {
+  grid_status s = check_args<S>(mc, N, {q, qd, tau, J}, {qdd});
+  if (s != GRID_OK || N == 0) return s;
+  grid_model* m = const_cast<grid_model*>(mc);   // the staging is the model's mutable part
+  grid_host_pipe* p = nullptr;
+  if ((s = host_pipe_get(m, &p)) != GRID_OK) return s;
+  std::lock_guard<std::mutex> lk(p->mu);
+  const size_t n = (size_t)m->n;
+  const size_t out_per = 2 * n * n;                 // scalars of J per knot point
+  size_t chunk = (size_t)m->host_chunk_opt;
+  if (chunk == 0) chunk = std::max<size_t>(1024, ((32u << 20) / (out_per * sizeof(S))) / 1024 * 1024);
+  chunk = std::min(chunk, (size_t)N);
+  // slot layout: q, qd, tau, qdd [chunk][n] and J [chunk][n][2n], each 256-byte aligned
+  const size_t vec_b = align256(chunk * n * sizeof(S)), mat_b = align256(chunk * out_per * sizeof(S));
+  const size_t need = 4 * vec_b + mat_b;
+  cudaError_t e;
+  if (need > p->slot_bytes) {
+    for (int b = 0; b < 3; ++b) {
+      if ((e = cudaStreamSynchronize(p->st[b])) != cudaSuccess) return cuda_fail("synchronise", e);
+    }
+    for (int b = 0; b < 3; ++b) {
+      cudaFree(p->slot[b]);
+      p->slot[b] = nullptr;
+    }
+    p->slot_bytes = 0;
+    for (int b = 0; b < 3; ++b)
+      if ((e = cudaMalloc(&p->slot[b], need)) != cudaSuccess) {
+        for (int c = 0; c < 3; ++c) { cudaFree(p->slot[c]); p->slot[c] = nullptr; }
+        return cuda_fail("staging allocation", e);
+      }
+    p->slot_bytes = need;
+  }
+  cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+  if ((e = cudaEventRecord(p->start, user)) != cudaSuccess) return cuda_fail("event record", e);
+  for (int b = 0; b < 3; ++b) cudaStreamWaitEvent(p->st[b], p->start, 0);
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+  for (size_t k0 = 0, c = 0; k0 < (size_t)N; k0 += chunk, ++c) {
+    const size_t cn = std::min(chunk, (size_t)N - k0);
+    const int b = (int)(c % 3);
+    char* base = static_cast<char*>(p->slot[b]);
+    S* dq = reinterpret_cast<S*>(base);
+    S* dqd = reinterpret_cast<S*>(base + vec_b);
+    S* dtau = reinterpret_cast<S*>(base + 2 * vec_b);
+    S* dqdd = reinterpret_cast<S*>(base + 3 * vec_b);
+    S* dJ = reinterpret_cast<S*>(base + 4 * vec_b);
+    const size_t vb = cn * n * sizeof(S);
+    cudaStreamWaitEvent(p->st[0], p->freed[b], 0);
+    e = cudaMemcpyAsync(dq, q + k0 * n, vb, h2d, p->st[0]);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dqd, qd + k0 * n, vb, h2d, p->st[0]);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dtau, tau + k0 * n, vb, h2d, p->st[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(p->loaded[b], p->st[0]);
+    if (e != cudaSuccess) { s = cuda_fail("copy in", e); break; }
+    cudaStreamWaitEvent(p->st[1], p->loaded[b], 0);
+    s = run<S, MODE_GRAD>(m, (int)cn, dq, dqd, dtau, nullptr, dJ, qdd ? dqdd : nullptr, nullptr, p->st[1]);
+    if (s != GRID_OK) break;
+    if ((e = cudaEventRecord(p->computed[b], p->st[1])) != cudaSuccess) { s = cuda_fail("event record", e); break; }
+    cudaStreamWaitEvent(p->st[2], p->computed[b], 0);
+    e = cudaMemcpyAsync(J + k0 * out_per, dJ, cn * out_per * sizeof(S), d2h, p->st[2]);
+    if (e == cudaSuccess && qdd) e = cudaMemcpyAsync(qdd + k0 * n, dqdd, vb, d2h, p->st[2]);
+    if (e == cudaSuccess) e = cudaEventRecord(p->freed[b], p->st[2]);
+    if (e != cudaSuccess) { s = cuda_fail("copy out", e); break; }
+  }
+  if (s != GRID_OK) {                   // leave nothing in flight behind an error
+    for (int b = 0; b < 3; ++b) cudaStreamSynchronize(p->st[b]);
+    return s;
+  }
+  // the copy out of the last chunk follows every kernel and every copy in
+  if ((e = cudaEventRecord(p->done, p->st[2])) != cudaSuccess) return cuda_fail("event record", e);
+  if ((e = cudaStreamWaitEvent(user, p->done, 0)) != cudaSuccess) return cuda_fail("stream wait", e);
+  return GRID_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- C-ABI
@@ -91,6 +234,8 @@ grid_status grid_create_ex(int n, const int* parent, const int* jtype, const dou
   m->ctas_opt = 0;
   m->specialize_opt = 1;
   m->gen = nullptr;
+  m->pipe = nullptr;
+  m->host_chunk_opt = 0;
   m->host_f = new ModelDev<float>();
   m->host_d = new ModelDev<double>();
   grid_status s = grid_build_model(n, parent, jtype, axis, X_tree, inertia, gravity, m->host_f, m->host_d);
@@ -139,6 +284,7 @@ grid_status grid_destroy(grid_model* m) {
   cudaFree(m->dev_f);
   cudaFree(m->dev_d);
   grid_gen_cache_free(m->gen);
+  host_pipe_free(m->pipe);
   delete m->host_f;
   delete m->host_d;
   delete m;
@@ -163,6 +309,9 @@ grid_status grid_set_option(grid_model* m, const char* key, int value) {
   } else if (k == "specialize") {
     if (value < 0 || value > 2) { grid_set_error("specialize must be 0, 1 or 2"); return GRID_E_ARG; }
     m->specialize_opt = value;
+  } else if (k == "host_chunk") {
+    if (value < 0) { grid_set_error("host_chunk must be >= 0"); return GRID_E_ARG; }
+    m->host_chunk_opt = value;
   } else if (k == "ctas_per_sm") {
     if (value < 0) { grid_set_error("ctas_per_sm must be >= 0"); return GRID_E_ARG; }
     m->ctas_opt = value;
@@ -257,6 +406,15 @@ grid_status grid_grad_rnea_f64(const grid_model* m, int N, const double* q, cons
   grid_status s = check_args<double>(m, N, {q, qd, dID}, {qdd});
   if (s != GRID_OK) return s;
   return run<double, MODE_GRAD_ID>(m, N, q, qd, qdd, nullptr, dID, nullptr, nullptr, stream);
+}
+
+grid_status grid_grad_fd_host(const grid_model* m, int N, const float* q, const float* qd, const float* tau,
+                              float* J, float* qdd, void* stream) {
+  return grad_fd_host<float>(m, N, q, qd, tau, J, qdd, stream);
+}
+grid_status grid_grad_fd_host_f64(const grid_model* m, int N, const double* q, const double* qd,
+                                  const double* tau, double* J, double* qdd, void* stream) {
+  return grad_fd_host<double>(m, N, q, qd, tau, J, qdd, stream);
 }
 
 }  // extern "C"

@@ -183,6 +183,8 @@ struct grid_model {
   int chain;                     // parent[i] = i - 1 for every body (a serial chain)
   int forest_k, forest_l;        // K >= 2 equal chains of L revolute bodies on the base, else 0
   struct grid_gen_cache* gen;    // kernels compiled at run time for this model (grid_nvrtc.cpp)
+  struct grid_host_pipe* pipe;   // staging and streams of grid_grad_fd_host (grid_capi.cu)
+  int host_chunk_opt;            // knot points per chunk of grid_grad_fd_host (0 = automatic)
   int specialize_opt;            // use the topology-specialised kernels where one exists (default 1)
   ModelDev<float>* dev_f;        // device copies
   ModelDev<double>* dev_d;
