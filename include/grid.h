@@ -127,7 +127,9 @@ int grid_model_dof(const grid_model* model);
  *                 and forests of 4 x 3, 2 x 6 or 4 x 4 equal chains on the base (in
  *                 depth-first order; with "lanes" 0),
  *                 run the gradient of FD (FP32 and FP64) in a kernel compiled for their
- *                 length (the chain topology of Sec. IV-C fixed at compile time);
+ *                 length (the chain topology of Sec. IV-C fixed at compile time); a
+ *                 forest without fixed bodies runs as independent chains (its
+ *                 chains do not interact through the fixed base);
  *                 2: as 1, and any other robot's gradient of FD runs in a kernel
  *                 compiled at run time (NVRTC, on the first call for each
  *                 precision and lane count) with its topology tables as constants;

@@ -66,6 +66,54 @@ grid_status run(const grid_model* m, int N, const S* q, const S* qd, const S* x3
   return dispatch<S, MODE, false>(m, N, q, qd, x3, x4, out, out2, out3, st);
 }
 
+// ---------------------------------------------------------------- forest branches
+bool nb_moving_equals_bodies(int nb, const int* jtype) {
+  if (!jtype) return true;
+  for (int i = 0; i < nb; ++i)
+    if (jtype[i] != GRID_JOINT_REVOLUTE) return false;
+  return true;
+}
+
+void free_branches(grid_model* m) {
+  cudaFree(m->br_dev_f);
+  cudaFree(m->br_dev_d);
+  delete[] m->br_host_f;
+  delete[] m->br_host_d;
+  m->br_dev_f = nullptr; m->br_dev_d = nullptr; m->br_host_f = nullptr; m->br_host_d = nullptr;
+  m->branches = 0;
+}
+
+// The K chain models of a forest of K chains of L bodies (caller bodies c L ..
+// c L + L - 1, parent c L - 1 .. of each, the first on the base). Any failure
+// leaves branches = 0: the forest kernel then serves the model.
+void build_branches(grid_model* m, const int* parent, const double* axis, const double* X_tree,
+                    const double* inertia, const double* gravity) {
+  const int K = m->forest_k, L = m->forest_l;
+  for (int c = 0; c < K; ++c)
+    for (int i = 0; i < L; ++i)
+      if (parent[c * L + i] != (i == 0 ? -1 : c * L + i - 1)) return;
+  m->br_host_f = new ModelDev<float>[K]();
+  m->br_host_d = new ModelDev<double>[K]();
+  int par[GRID_MAX_DOF];
+  for (int i = 0; i < L; ++i) par[i] = i - 1;
+  for (int c = 0; c < K; ++c) {
+    if (grid_build_model(L, par, nullptr, axis + 3 * c * L, X_tree + 12 * c * L, inertia + 10 * c * L, gravity,
+                         &m->br_host_f[c], &m->br_host_d[c]) != GRID_OK) {
+      free_branches(m);
+      return;
+    }
+  }
+  if (cudaMalloc(&m->br_dev_f, K * sizeof(ModelDev<float>)) != cudaSuccess ||
+      cudaMalloc(&m->br_dev_d, K * sizeof(ModelDev<double>)) != cudaSuccess ||
+      cudaMemcpy(m->br_dev_f, m->br_host_f, K * sizeof(ModelDev<float>), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->br_dev_d, m->br_host_d, K * sizeof(ModelDev<double>), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    free_branches(m);
+    return;
+  }
+  m->branches = K;
+}
+
 // ---------------------------------------------------------------- host buffers
 // grid_grad_fd_host: three staging slots and three streams (copy in, kernel,
 // copy out). Chunk c uses slot c mod 3; its copy in waits until the copy out of
@@ -256,6 +304,8 @@ grid_status grid_create_ex(int n, const int* parent, const int* jtype, const dou
       ok = m->host_d->parent[i] == (i % L == 0 ? -1 : i - 1) && m->host_d->perm[i] == i;
     if (ok) { m->forest_k = m->n / L; m->forest_l = L; }
   }
+  m->branches = 0;
+  m->br_dev_f = nullptr; m->br_dev_d = nullptr; m->br_host_f = nullptr; m->br_host_d = nullptr;
   cudaGetDevice(&m->device);
   cudaError_t e1 = cudaMalloc(&m->dev_f, sizeof(ModelDev<float>));
   cudaError_t e2 = cudaMalloc(&m->dev_d, sizeof(ModelDev<double>));
@@ -274,6 +324,11 @@ grid_status grid_create_ex(int n, const int* parent, const int* jtype, const dou
     delete m->host_f; delete m->host_d; delete m;
     return GRID_E_CUDA;
   }
+  // A forest without fixed bodies (caller body i = joint i) also gets one model
+  // per chain, built from the caller's arrays, for the branch kernel; without
+  // them the forest runs in its own kernel.
+  if (m->forest_k > 1 && nb_moving_equals_bodies(n, jtype) && m->n == n)
+    build_branches(m, parent, axis, X_tree, inertia, gravity);
   *out = m;
   return GRID_OK;
 }
@@ -285,6 +340,7 @@ grid_status grid_destroy(grid_model* m) {
   cudaFree(m->dev_d);
   grid_gen_cache_free(m->gen);
   host_pipe_free(m->pipe);
+  free_branches(m);
   delete m->host_f;
   delete m->host_d;
   delete m;

@@ -1,7 +1,10 @@
 // Kernel instantiations for forests of K identical serial chains of L bodies
 // on the fixed base (legs of a quadruped, a biped, a hexapod), gradient of FD
-// in FP32 and FP64: the topology and the workspace layout are compile-time
-// constants (ForestTopo); 8 lanes per knot point, 32 for small batches.
+// in FP32 and FP64. When the model holds one model per chain (no fixed bodies),
+// the chains run independently in the branch kernel (BranchTopo: 8 lanes per
+// chain and knot point, the chain kernel's phases). Otherwise the topology and
+// the workspace layout of the whole forest are compile-time constants
+// (ForestTopo); 8 lanes per knot point, 32 for small batches.
 #include "grid_launch.cuh"
 
 bool forest_compiled(int k, int l) {
@@ -12,6 +15,21 @@ bool forest_compiled(int k, int l) {
 template <class S, int MODE>
 grid_status launch_forest(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                           const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st) {
+  // With one model per chain: the branch kernel, 8 lanes per chain and knot
+  // point (a warp holds 4 / K knot points), N K virtual knot points.
+  if (m->branches == m->forest_k && (long)N * m->forest_k <= 0x7fffffffL) {
+    const ModelDev<S>* bh;
+    const ModelDev<S>* bd;
+    if constexpr (std::is_same<S, float>::value) { bh = m->br_host_f; bd = m->br_dev_f; }
+    else { bh = m->br_host_d; bd = m->br_dev_d; }
+    const int NV = N * m->forest_k;
+    switch (100 * m->forest_k + m->forest_l) {
+      case 403: return launch_t<S, MODE, 8, 1, 8, false, 3, 4>(m, bh, bd, NV, q, qd, x3, x4, out, out2, out3, st);
+      case 206: return launch_t<S, MODE, 8, 1, 8, false, 6, 2>(m, bh, bd, NV, q, qd, x3, x4, out, out2, out3, st);
+      case 404: return launch_t<S, MODE, 8, 1, 8, false, 4, 4>(m, bh, bd, NV, q, qd, x3, x4, out, out2, out3, st);
+      default: break;
+    }
+  }
   // 8 lanes per knot point for throughput; a batch of at most two knot points
   // per SM is latency-bound and takes one warp per knot point
   const bool lat = N <= 2 * dev_info(m->device).nsm;

@@ -182,6 +182,11 @@ struct grid_model {
   int ctas_opt;
   int chain;                     // parent[i] = i - 1 for every body (a serial chain)
   int forest_k, forest_l;        // K >= 2 equal chains of L revolute bodies on the base, else 0
+  int branches;                  // K when the forest also has one model per chain (below), else 0
+  ModelDev<float>* br_dev_f;     // the K chain models: device arrays and host mirrors
+  ModelDev<double>* br_dev_d;
+  ModelDev<float>* br_host_f;
+  ModelDev<double>* br_host_d;
   struct grid_gen_cache* gen;    // kernels compiled at run time for this model (grid_nvrtc.cpp)
   struct grid_host_pipe* pipe;   // staging and streams of grid_grad_fd_host (grid_capi.cu)
   int host_chunk_opt;            // knot points per chunk of grid_grad_fd_host (0 = automatic)

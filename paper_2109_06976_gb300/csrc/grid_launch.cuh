@@ -28,6 +28,19 @@ __global__ void __launch_bounds__(128, CHAIN_N > 0 ? 4 : 1) grid_kernel(const Mo
   grid_kernel_body<S, MODE, T, CPL, MAXD, MIXED, topo_for<S, MODE, CHAIN_N>>(gm, N, q, qd, x3, x4, out, out2, out3);
 }
 
+// A forest of KB chains of L bodies run as KB independent chains (BranchTopo):
+// N counts the virtual knot points (knot points x KB); gm is the array of the
+// KB chain models.
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int L, int KB>
+__global__ void __launch_bounds__(128, 4) grid_branch_kernel(const ModelDev<S>* __restrict__ gm, int N,
+                                                  const S* __restrict__ q, const S* __restrict__ qd,
+                                                  const S* __restrict__ x3, const S* __restrict__ x4,
+                                                  S* __restrict__ out, S* __restrict__ out2,
+                                                  S* __restrict__ out3) {
+  grid_kernel_body<S, MODE, T, CPL, MAXD, MIXED, BranchTopo<S, MODE, L, KB>, KB>(gm, N, q, qd, x3, x4, out, out2,
+                                                                                   out3);
+}
+
 // ---------------------------------------------------------------- launcher
 constexpr int kMaxWarps = 4;    // warps per CTA (matches __launch_bounds__)
 
@@ -49,11 +62,18 @@ static inline DevInfo dev_info(int dev) {
   return cache[dev];
 }
 
-template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N = 0>
+// KB > 1: the branch kernel for a forest of KB chains of CHAIN_N bodies; hm is
+// the first chain's host model, dm the device array of the KB chain models and N
+// the number of virtual knot points.
+template <class S, int MODE, int T, int CPL, int MAXD, bool MIXED, int CHAIN_N = 0, int KB = 1>
 grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N,
                      const S* q, const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3,
                      cudaStream_t st) {
-  auto kern = grid_kernel<S, MODE, T, CPL, MAXD, MIXED, CHAIN_N>;
+  static_assert(KB == 1 || CHAIN_N > 0, "branches are chains");
+  auto kern = [] {
+    if constexpr (KB > 1) return grid_branch_kernel<S, MODE, T, CPL, MAXD, MIXED, CHAIN_N, KB>;
+    else return grid_kernel<S, MODE, T, CPL, MAXD, MIXED, CHAIN_N>;
+  }();
   if constexpr (CHAIN_N > 0) {
     // the compile-time layout must be the one the host built for this model
     if (hm->n != CHAIN_N || ChainTopo<S, MODE, CHAIN_N>::layout().stride != layout_of<MODE>(*hm).stride) {
@@ -71,7 +91,7 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
   constexpr int G = 32 / T;
   const int nsteps = (MODE == MODE_GRAD || MODE == MODE_GRAD_ID) ? hm->steps[cfg] : 0;
   const DevInfo di = dev_info(m->device);
-  const size_t fixed = align16(model_head_bytes<S>()) + align16(nsteps * T * 4);
+  const size_t fixed = KB * align16(model_head_bytes<S>()) + align16(nsteps * T * 4);
   const size_t per_warp = (size_t)G * layout_of<MODE>(*hm).stride * sizeof(S);
   // Opt in to large dynamic shared memory once per instantiation.
   static std::atomic<int> opted{0};

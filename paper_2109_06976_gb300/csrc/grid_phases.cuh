@@ -30,6 +30,7 @@ struct RtTopo {
   static constexpr int kUnroll = 1;
   static constexpr int kChainN = 0;       // not a compile-time chain
   static constexpr bool kConsecutivePaths = false;
+  static constexpr int kBranches = 0;
   const ModelDev<S>& M;
   __device__ explicit RtTopo(const ModelDev<S>& m) : M(m) {}
   __device__ const KnotLayout& layout() const { return layout_of<MODE>(M); }
@@ -52,6 +53,7 @@ struct ChainTopo {
   static constexpr int kUnroll = N;
   static constexpr int kChainN = N;
   static constexpr bool kConsecutivePaths = true;   // ancestor at depth d of k: k - depth(k) + d
+  static constexpr int kBranches = 0;
   __device__ explicit ChainTopo(const ModelDev<S>&) {}
   GRID_HD static constexpr KnotLayout layout() {
     return make_layout(N, N * (N + 1) / 2, 0, (int)sizeof(S), layout_kind(MODE));
@@ -70,6 +72,19 @@ struct ChainTopo {
   GRID_HD static constexpr bool prism(int) { return false; }   // revolute chains only
 };
 
+// K serial chains of L bodies on the fixed base (a forest whose chains differ
+// only in their parameters) run as K independent chains: the joints c L .. c L +
+// L - 1 of knot point k are the joints of "virtual" knot point k K + c in the
+// same memory (knot-major arrays), lane group g of a warp uses chain g mod K's
+// model, and only J and M^-1 are placed differently: the chain's blocks on the
+// diagonal of the K L-joint outputs, zeros elsewhere (the chains do not interact
+// through a fixed base).
+template <class S, int MODE, int L, int K>
+struct BranchTopo : ChainTopo<S, MODE, L> {
+  static constexpr int kBranches = K;
+  __device__ explicit BranchTopo(const ModelDev<S>& m) : ChainTopo<S, MODE, L>(m) {}
+};
+
 // K identical serial chains of L bodies, each hanging from the fixed base, in
 // depth-first numbering (a quadruped's legs: K = 4, L = 3). The phases take
 // their general paths; only the topology folds.
@@ -78,6 +93,7 @@ struct ForestTopo {
   static constexpr int kUnroll = K * L;
   static constexpr int kChainN = 0;
   static constexpr bool kConsecutivePaths = true;
+  static constexpr int kBranches = 0;
   __device__ explicit ForestTopo(const ModelDev<S>&) {}
   GRID_HD static constexpr KnotLayout layout() {
     return make_layout(K * L, K * L * (L + 1) / 2, 0, (int)sizeof(S), layout_kind(MODE));
@@ -831,7 +847,7 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
 // ---------------------------------------------------------------- D
 // J = -M^-1 dc, restricted to base-branch blocks, written in caller order.
 template <class S, int T, int CPL, class Tp>
-__device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J) {
+__device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J, int rs = 0, int cq = 0, int cqd = 0) {
   const ModelDev<S>& M = c.M;
   const Tp& tp = c.tp;
   S* W = c.W;
@@ -840,6 +856,7 @@ __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J) {
   const int U = L.UNION;
   const S* DC = W + U + L.DC;
   const S* MI = W + L.MINV;
+  if (rs == 0) { rs = n2; cq = 0; cqd = n; }   // J rows of 2n; else rows of rs with the blocks at cq, cqd
   constexpr int NM = CPL * T;                  // >= n, a multiple of 4
   // Lane owns output columns col = l, l + T, ...: its dc column sits in
   // registers and every M^-1 row is read with 128-bit loads. J (this knot
@@ -851,10 +868,10 @@ __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J) {
     S dcr[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) dcr[m] = (m >= lo && m < hi) ? DC[m * n2 + col] : S(0);
-    const int ucol = (col < n ? 0 : n) + tp.perm(j);
+    const int ucol = (col < n ? cq : cqd) + tp.perm(j);
     if (J) {
-      for (int i = 0; i < lo; ++i) J[tp.perm(i) * n2 + ucol] = S(0);     // other base branches
-      for (int i = hi; i < n; ++i) J[tp.perm(i) * n2 + ucol] = S(0);
+      for (int i = 0; i < lo; ++i) J[tp.perm(i) * rs + ucol] = S(0);     // other base branches
+      for (int i = hi; i < n; ++i) J[tp.perm(i) * rs + ucol] = S(0);
     }
 #pragma unroll (Tp::kUnroll)
     for (int i = lo; i < hi; ++i) {
@@ -868,7 +885,7 @@ __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J) {
           acc += mm[0] * dcr[m] + mm[1] * dcr[m + 1] + mm[2] * dcr[m + 2] + mm[3] * dcr[m + 3];
         }
       }
-      if (J) J[tp.perm(i) * n2 + ucol] = -acc;
+      if (J) J[tp.perm(i) * rs + ucol] = -acc;
     }
   }
   SYNC();
@@ -1057,7 +1074,22 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
     ph_update_and_forces<S, T, true>(c);
     if (MODE == MODE_GRAD) {
       ph_columns<S, T, MAXD>(c, sched, nsteps);
-      ph_product<S, T, CPL>(c, g < nvalid ? out + (size_t)(k0 + g) * 2 * n * n : nullptr);
+      if constexpr (Tp::kBranches > 0) {
+        // rows b n .. b n + n - 1 of the K n-joint knot point: the chain's blocks at
+        // columns b n and K n + b n, zeros in the rest of those rows
+        constexpr int K = Tp::kBranches;
+        const int nr = K * n, b = (k0 + g) % K;
+        S* Jb = g < nvalid ? out + (size_t)((k0 + g) / K) * 2 * nr * nr + (size_t)b * n * 2 * nr : nullptr;
+        ph_product<S, T, CPL>(c, Jb, 2 * nr, b * n, nr + b * n);
+        if (Jb) {
+          for (int e = c.l; e < n * 2 * nr; e += T) {
+            const int col = e % (2 * nr), u = col < nr ? col - b * n : col - nr - b * n;
+            if (u < 0 || u >= n) Jb[e] = S(0);
+          }
+        }
+      } else {
+        ph_product<S, T, CPL>(c, g < nvalid ? out + (size_t)(k0 + g) * 2 * n * n : nullptr);
+      }
     }
     if (MODE == MODE_VJP) {
       ph_vjp_seeds<S, T>(c);
@@ -1074,10 +1106,20 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
       }
     }
     if (out3 && g < nvalid) {                       // M^-1 in caller order (full symmetric)
-      S* Mo = out3 + (size_t)(k0 + g) * n * n;
-      for (int e = c.l; e < n * n; e += T) {
-        const int i = e / n, j = e % n;
-        Mo[tp.perm(i) * n + tp.perm(j)] = W[L.MINV + i * L.MS + j];
+      if constexpr (Tp::kBranches > 0) {            // the chain's diagonal block, zeros beside it
+        constexpr int K = Tp::kBranches;
+        const int nr = K * n, b = (k0 + g) % K;
+        S* Mo = out3 + (size_t)((k0 + g) / K) * nr * nr + (size_t)b * n * nr;
+        for (int e = c.l; e < n * nr; e += T) {
+          const int i = e / nr, u = e % nr - b * n;
+          Mo[e] = (u >= 0 && u < n) ? W[L.MINV + i * L.MS + u] : S(0);
+        }
+      } else {
+        S* Mo = out3 + (size_t)(k0 + g) * n * n;
+        for (int e = c.l; e < n * n; e += T) {
+          const int i = e / n, j = e % n;
+          Mo[tp.perm(i) * n + tp.perm(j)] = W[L.MINV + i * L.MS + j];
+        }
       }
     }
     SYNC();

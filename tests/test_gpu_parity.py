@@ -172,6 +172,31 @@ def test_forest_specialised_kernel(grid, shape, dtype, N):
     assert np.all(col_rel_err_knots(Jg, ref, floor=fl) <= tol)
 
 
+@pytest.mark.parametrize("N", [1, 203])
+def test_forest_branches_write_whole_outputs(grid, N):
+    """A forest on the fixed base runs as independent chains (one lane group per
+    chain and knot point): J and M^-1 get every entry written, the chains'
+    diagonal blocks and exact zeros elsewhere (outputs pre-filled with NaN)."""
+    r = gi.tree12()
+    m = grid.Model.from_robot(r)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(12, N, 17, torch.float32)
+    J = torch.full((N, 12, 24), float("nan"), device="cuda")
+    Mi = torch.full((N, 12, 12), float("nan"), device="cuda")
+    m.grad_fd_minv(q, qd, tau, out=J, minv_out=Mi)
+    Jh, Mh = J.cpu().numpy(), Mi.cpu().numpy()
+    assert np.isfinite(Jh).all() and np.isfinite(Mh).all()
+    for c in range(4):
+        rows = slice(3 * c, 3 * c + 3)
+        jmask = np.ones(24, bool)
+        jmask[3 * c:3 * c + 3] = jmask[12 + 3 * c:12 + 3 * c + 3] = False
+        mmask = np.ones(12, bool)
+        mmask[3 * c:3 * c + 3] = False
+        assert np.all(Jh[:, rows][:, :, jmask] == 0) and np.all(Mh[:, rows][:, :, mmask] == 0)
+    assert col_rel_err(Jh, oracle.grad_fd(r, q64, qd64, tau64), FLOOR32) <= TOL32
+    assert col_rel_err(Mh, oracle.minv(r, q64), FLOOR32) <= TOL32
+    m.close()
+
+
 @pytest.mark.parametrize("key", WORKLOAD)
 def test_grad_fd_workload_sizes(grid, key):
     """The workload batch sizes (N = 16 .. 1024) in one call each."""
