@@ -56,13 +56,16 @@ NCU_DRAM_BYTES_PER_KNOT = {"517743476c2097e0": 199.75e6 / 524288,
                            # kernel code identical to f8f85c036843ba52: only the host-buffer
                            # pipeline (grid_capi.cu) and a host-side model field were added
                            "3b0e48a5f622bbea": 189.67e6 / 524288,
-                           "ea367adecd85eda9": 189.21e6 / 524288}
+                           "ea367adecd85eda9": 189.21e6 / 524288,
+                           # 7-DoF chain kernel identical to ea367adecd85eda9: only the branch
+                           # kernel's launch bounds changed
+                           "afb5ee0d6c339fe3": 189.21e6 / 524288}
 # FP32 (FMA) pipe utilisation of the same captures: sm__pipe_fma_cycles_active, % of
 # peak sustained while active (busy cycles, so a paired FP32 instruction counts for the
 # cycles it occupies), reported beside the counted-flop fraction.
 NCU_FMA_PIPE = {"e04804cb5f3a6d15": 0.401, "59c365e8cec7dca6": 0.418, "c7c560789c0e9069": 0.432,
                 "a032ad23a8b5e7d9": 0.418, "f8f85c036843ba52": 0.418, "3b0e48a5f622bbea": 0.418,
-                "ea367adecd85eda9": 0.417}
+                "ea367adecd85eda9": 0.417, "afb5ee0d6c339fe3": 0.417}
 
 
 def kernel_source_hash() -> str:
