@@ -417,6 +417,23 @@ def run_ours(args):
     def step():
         model.grad_fd(q, qd, tau, out=J)
 
+    if args.only_tree12:
+        # the 12-DoF tree's step alone (half the main batch), for profiling captures
+        t12 = gi.tree12()
+        m12 = grid.Model.from_robot(t12)
+        N12 = Nk // 2
+        q12, qd12, tau12 = (torch.from_numpy(x.astype(np.float32)).cuda()
+                            for x in gi.states(12, N12, seed + 1))
+        J12 = torch.empty((N12, 12, 24), device="cuda")
+        sec12 = time_steps(lambda: m12.grad_fd(q12, qd12, tau12, out=J12), args.steps, args.warmup, stream, dist)
+        if rank == 0:
+            print(json.dumps({"metric": "gradient of FD, 12-DoF tree", "value": world * N12 * args.steps / sec12,
+                              "unit": UNIT, "ms_per_step": sec12 / args.steps * 1e3, "knot_points": N12}),
+                  flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+
     with ClockSampler(local) as clk:
         sec = time_steps(step, args.steps, args.warmup, stream, dist)
     clocks = clk.summary()
@@ -603,6 +620,8 @@ def main():
                     help="1: chain-specialised kernel for the 7-DoF chain; 0: run-time topology kernel")
     ap.add_argument("--only-main", action="store_true",
                     help="time only the main FP32 step (used for profiling captures)")
+    ap.add_argument("--only-tree12", action="store_true",
+                    help="time only the 12-DoF tree's step (used for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
