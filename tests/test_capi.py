@@ -58,3 +58,17 @@ def test_host_side_validation_without_gpu(lib):
     st = lib.grid_create(40, parent.ctypes.data_as(P), axis.ctypes.data_as(P), xt.ctypes.data_as(P),
                          inert.ctypes.data_as(P), g.ctypes.data_as(P), 0, ctypes.byref(h))
     assert st == 2
+
+
+def test_host_buffer_call_checks_arguments_without_gpu(lib):
+    """grid_grad_fd_host and the host_chunk option refuse a null model on the
+    host, before any CUDA call."""
+    P = ctypes.c_void_p
+    for name in ("grid_grad_fd_host", "grid_grad_fd_host_f64"):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = [P, ctypes.c_int, P, P, P, P, P, P]
+        assert fn(None, 4, None, None, None, None, None, None) == 1
+    lib.grid_set_option.restype = ctypes.c_int
+    lib.grid_set_option.argtypes = [P, ctypes.c_char_p, ctypes.c_int]
+    assert lib.grid_set_option(None, b"host_chunk", 1024) == 1
