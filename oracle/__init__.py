@@ -64,7 +64,6 @@ def _load():
             model = [_I, _P, _P, _P, _P, _P, _P]
             sig = {
                 "oracle_rnea": model + [_I, _P, _P, _P, _P, _I],
-                "oracle_rnea_bodies": model + [_I, _P, _P, _P, _P, _P, _P, _P],
                 "oracle_mass_matrix": model + [_I, _P, _P, _I],
                 "oracle_minv": model + [_I, _P, _P, _I],
                 "oracle_fd": model + [_I, _P, _P, _P, _P, _I],
@@ -129,16 +128,6 @@ def rnea(robot, q, qd, qdd, nthreads=1):
     keep, margs = _model_args(robot)
     _check(_load().oracle_rnea(*margs, N, _ptr(q), _ptr(qd), _ptr(qdd), _ptr(tau), nthreads), "rnea")
     return tau
-
-
-def rnea_bodies(robot, q, qd, qdd):
-    """Per-body v, a, f (own), F (accumulated), each [N, bodies, 6]."""
-    N, (q, qd, qdd) = _states(robot, q, qd, qdd)
-    outs = [np.empty((N, robot.n, 6)) for _ in range(4)]
-    keep, margs = _model_args(robot)
-    _check(_load().oracle_rnea_bodies(*margs, N, _ptr(q), _ptr(qd), _ptr(qdd),
-                                      *[_ptr(o) for o in outs]), "rnea_bodies")
-    return tuple(outs)
 
 
 def mass_matrix(robot, q, nthreads=1):

@@ -468,20 +468,6 @@ int oracle_rnea(ORACLE_MODEL_ARGS, int N, const double* q, const double* qd, con
   });
 }
 
-// Per-body RNEA intermediates v, a, f (own) and F (accumulated), [N][nb][6].
-int oracle_rnea_bodies(ORACLE_MODEL_ARGS, int N, const double* q, const double* qd, const double* qdd,
-                       double* v, double* a, double* f, double* F) {
-  ORACLE_BUILD
-  for (int k = 0; k < N; ++k) {
-    RneaOut<double> r = rnea<double>(m, q + k * n, qd + k * n, qdd + k * n);
-    for (int i = 0; i < nb; ++i) for (int c = 0; c < 6; ++c) {
-      v[(k * nb + i) * 6 + c] = r.v[i][c]; a[(k * nb + i) * 6 + c] = r.a[i][c];
-      f[(k * nb + i) * 6 + c] = r.f[i][c]; F[(k * nb + i) * 6 + c] = r.F[i][c];
-    }
-  }
-  return 0;
-}
-
 int oracle_mass_matrix(ORACLE_MODEL_ARGS, int N, const double* q, double* M, int nthreads) {
   ORACLE_BUILD
   return parallel_for(N, nthreads, [&](int k) {

@@ -24,7 +24,9 @@ Backward pass (Li and Todorov 2004; Tassa, Erez and Todorov 2012), k = H-1 .. 0:
 starting from V_x = W_f (x_H - r_H), V_xx = W_f.
 
 Pins (tests/test_oracle_traj.py): the rollout of a slider under constant force
-against its closed form; A and B against central differences of the step;
+against its closed form; the rollout under a feedback policy on the same slider
+against the closed-loop fixed point and powers of the closed-loop matrix; A and
+B against central differences of the step;
 the Riccati gains of a linear time-invariant system against the discrete
 algebraic Riccati equation solved by scipy; one iteration on a linear system
 reaching the optimum of the equality-constrained QP solved by a dense KKT

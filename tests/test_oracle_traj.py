@@ -132,3 +132,47 @@ def test_one_iteration_solves_linear_quadratic_problem():
             g += Phi[k].T @ W[k] @ (psi[k] - ref[b, k])
         Uopt = np.linalg.solve(Hm, -g).reshape(H, m)
         np.testing.assert_allclose(U1[b], Uopt, rtol=1e-9, atol=1e-10)
+
+
+def test_policy_rollout_closed_loop_slider():
+    """The policy branch of the rollout, u_k = U_k + alpha kff_k + K_k (x_k - xnom_k),
+    on a vertical slider (q'' = u/m - g exactly). With U = m g + u0, K = [-kp, -kd]
+    and constant kff and xnom = (qn, qdn), the closed loop is a damped oscillator
+    about the fixed point q* = qn + (u0 + alpha kff + kd qdn) / kp, qd* = 0, and
+    the semi-implicit step maps the offset e = x - x* by the constant matrix
+        A_cl = [[1 - dt^2 kp/m, dt (1 - dt kd/m)], [-dt kp/m, 1 - dt kd/m]],
+    so e_k = A_cl^k e_0 (matrix powers, no recursion). A flipped sign of K dx,
+    alpha applied to K instead of kff, or alpha left out moves the fixed point or
+    the decay and fails this pin."""
+    m, dt, H, alpha = 1.7, 0.01, 60, 0.37
+    r = gi.slider(m=m, axis=(0.0, 0.0, 1.0))
+    g = 9.81
+    kp = np.array([40.0, 15.0])
+    kd = np.array([6.0, 2.5])
+    u0 = np.array([0.8, -1.1])
+    kffv = np.array([2.0, -3.0])
+    qn = np.array([0.25, -0.4])
+    qdn = np.array([0.3, -0.2])
+    q0 = np.array([[0.5], [0.1]])
+    qd0 = np.array([[-0.2], [0.4]])
+    Bn = 2
+    U = np.repeat((m * g + u0)[:, None, None], H, axis=1)
+    K = np.zeros((Bn, H, 1, 2))
+    K[:, :, 0, 0] = -kp[:, None]
+    K[:, :, 0, 1] = -kd[:, None]
+    kff = np.repeat(kffv[:, None, None], H, axis=1)
+    Qnom = np.repeat(qn[:, None, None], H + 1, axis=1)
+    QDnom = np.repeat(qdn[:, None, None], H + 1, axis=1)
+    q, qd, ua = traj.rollout(r, dt, q0, qd0, U, K=K, kff=kff, Qnom=Qnom, QDnom=QDnom, alpha=alpha)
+    for b in range(Bn):
+        qs = qn[b] + (u0[b] + alpha * kffv[b] + kd[b] * qdn[b]) / kp[b]
+        Acl = np.array([[1 - dt * dt * kp[b] / m, dt * (1 - dt * kd[b] / m)],
+                        [-dt * kp[b] / m, 1 - dt * kd[b] / m]])
+        e0 = np.array([q0[b, 0] - qs, qd0[b, 0]])
+        for k in range(H + 1):
+            e = np.linalg.matrix_power(Acl, k) @ e0
+            np.testing.assert_allclose(q[b, k, 0], qs + e[0], rtol=1e-11, atol=1e-11)
+            np.testing.assert_allclose(qd[b, k, 0], e[1], rtol=1e-11, atol=1e-11)
+            if k < H:    # the applied control holds the slider's acceleration: m (q'' + g)
+                qdd = (-kp[b] * e[0] - kd[b] * e[1]) / m
+                np.testing.assert_allclose(ua[b, k, 0], m * (qdd + g), rtol=1e-11, atol=1e-10)
