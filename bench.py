@@ -34,38 +34,24 @@ import grid_inputs as gi  # noqa: E402
 METRIC = "∇FD knot-points/sec at N=128 (FP32/mixed vs FP64 plain); serve p50/p99 ms"
 UNIT = "knot-points/s"
 KNOTS = 128                      # knot points per trajectory (the metric's N)
-TRAJ = 16384                     # trajectories per step (2,097,152 knot points)
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+TRAJ = 65536                     # trajectories per step (8,388,608 knot points)
 L2_BYTES = 129 * 1024 * 1024
-# FP32 peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
-# lanes x 2 flops (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-# DRAM bytes per knot point of the gradient kernel from an ncu capture, keyed
-# by a hash of the kernel sources; absent when the kernel changed since.
-# (profiles/grad_fd_chain7_ncu_full.md: DRAM read + write of a 524,288-knot-point
-# launch, scaled by knot points to the benchmark's launch.)
-NCU_DRAM_BYTES_PER_KNOT = {"517743476c2097e0": 199.75e6 / 524288,
-                           "d1f6cfa03f54f835": 199.17e6 / 524288,
-                           "e04804cb5f3a6d15": 188.95e6 / 524288,
-                           "59c365e8cec7dca6": 189.65e6 / 524288,
-                           "c7c560789c0e9069": 189.20e6 / 524288,
-                           "a032ad23a8b5e7d9": 189.45e6 / 524288,
-                           "f8f85c036843ba52": 189.67e6 / 524288,
-                           # kernel code identical to f8f85c036843ba52: only the host-buffer
-                           # pipeline (grid_capi.cu) and a host-side model field were added
-                           "3b0e48a5f622bbea": 189.67e6 / 524288,
-                           "ea367adecd85eda9": 189.21e6 / 524288,
-                           # 7-DoF chain kernel identical to ea367adecd85eda9: only the branch
-                           # kernel's launch bounds changed
-                           "afb5ee0d6c339fe3": 189.21e6 / 524288}
-# FP32 (FMA) pipe utilisation of the same captures: sm__pipe_fma_cycles_active, % of
-# peak sustained while active (busy cycles, so a paired FP32 instruction counts for the
-# cycles it occupies), reported beside the counted-flop fraction.
-NCU_FMA_PIPE = {"e04804cb5f3a6d15": 0.401, "59c365e8cec7dca6": 0.418, "c7c560789c0e9069": 0.432,
-                "a032ad23a8b5e7d9": 0.418, "f8f85c036843ba52": 0.418, "3b0e48a5f622bbea": 0.418,
-                "ea367adecd85eda9": 0.417, "afb5ee0d6c339fe3": 0.417}
+# Counted operations of one knot point of the gradient of FD (transforms, RNEA, direct
+# M^-1, FD, RNEA at qdd, dRNEA, product), written from oracle/opcount.py's count of the
+# method in compact form; tests/test_opcount.py checks this table against that count.
+FLOPS_PER_KNOT = {"chain7": 26845, "tree12": 21516, "tree30": 132124}
+# Nominal FP32 rate for context only (152 SMs x 128 lanes x 2 flops x 2.07 GHz); the
+# roofline divides by the rate the FMA loop measures in the same run.
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# DRAM bytes per knot point of the 7-DoF gradient kernel from one ncu capture of the
+# same kernel sources (key: bench.py's hash of csrc/), dram__bytes_read.sum +
+# dram__bytes_write.sum of a 524,288-knot-point launch divided by its knot points,
+# and lts__t_sectors_srcunit_tex_op_write.sum x 32 B (the writes the SMs send to L2,
+# including those still in L2 when the kernel ends). Absent when the kernel changed.
+NCU_BYTES_PER_KNOT = {}
+# FP32 (FMA) pipe utilisation from the same captures (sm__pipe_fma_cycles_active, % of
+# peak sustained while active), reported beside the counted-flop fraction.
+NCU_FMA_PIPE = {}
 
 
 def kernel_source_hash() -> str:
@@ -78,9 +64,10 @@ def kernel_source_hash() -> str:
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    """nvidia-smi clock and throttle-reason samples every 50 ms, each with the
+    driver's timestamp, so that the summary keeps only the timed region."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
     NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -94,10 +81,11 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.5)              # the first sample arrives before the timed region
         except OSError:
             self.proc = None
         return self
@@ -108,6 +96,7 @@ class ClockSampler:
 
     def __exit__(self, *a):
         if self.proc:
+            time.sleep(0.2)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -115,24 +104,77 @@ class ClockSampler:
                 self.proc.kill()
             self.t.join(timeout=2)
 
-    def summary(self):
-        sm, mx, reasons = [], [], set()
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, maximum and the throttle reasons seen between host
+        times t0 and t1 (all samples if not given)."""
+        sm, mx, pw, reasons = [], [], [], set()
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
+                continue
+            ts = self._stamp(parts[0])
+            if t0 is not None and ts is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
             except ValueError:
                 continue
-            for name, v in zip(self.NAMES, parts[3:7]):
+            for name, v in zip(self.NAMES, parts[4:8]):
                 if v.lower() in ("active", "1"):
                     reasons.add(name)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_median": statistics.median(pw)}
+
+
+def measure_peaks(grid, device_index=0, seconds=0.25):
+    """FP32 and FP64 multiply-add rates of this GPU, measured: grid_peak_loop
+    (8 independent multiply-add chains per thread in registers) over 8 CTAs of 256
+    threads per SM, each kind timed with CUDA events after a warm-up launch, best
+    of 3. FP32 takes the faster of the scalar and the paired instruction."""
+    import ctypes
+    import torch
+    lib = grid._native.load()
+    nsm = torch.cuda.get_device_properties(device_index).multi_processor_count
+    blocks, threads = 8 * nsm, 256
+    stream = torch.cuda.current_stream()
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    res = {}
+    for kind, name in ((0, "fp32_fma"), (1, "fp32_fma_paired"), (2, "fp64_fma")):
+        iters = 2048
+        best = 0.0
+        for rep in range(6):
+            fl = ctypes.c_double()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            grid._native.check("grid_peak_loop", lib.grid_peak_loop(kind, blocks, threads, iters,
+                                                                    ctypes.c_void_p(out.data_ptr()),
+                                                                    ctypes.byref(fl),
+                                                                    ctypes.c_void_p(stream.cuda_stream)))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            if rep < 2:                       # size the loop to about `seconds`, then time 4 runs
+                iters = max(1, int(iters * seconds / max(sec, 1e-6)))
+                continue
+            best = max(best, fl.value / sec / 1e12)
+        res[name] = best
+    res["fp32"] = max(res["fp32_fma"], res["fp32_fma_paired"])
+    res["fp64"] = res["fp64_fma"]
+    res["sm_count"] = nsm
+    return res
 
 
 def dist_setup(n_gpus):
@@ -166,9 +208,10 @@ def aggregate_value(world, knots_per_rank, steps, sec):
     return world * knots_per_rank * steps / sec
 
 
-def time_steps(fn, steps, warmup, stream, dist=None):
+def time_steps(fn, steps, warmup, stream, dist=None, window=None):
     """W untimed steps, then K steps bracketed by barrier + synchronize; CUDA
-    events on the launching stream. Returns (seconds, max over ranks)."""
+    events on the launching stream. Returns seconds, the max over ranks. With a
+    list as `window`, the host times around the timed region are appended."""
     import torch
     for _ in range(warmup):
         fn()
@@ -178,15 +221,41 @@ def time_steps(fn, steps, warmup, stream, dist=None):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
     e0.record(stream)
     for _ in range(steps):
         fn()
     e1.record(stream)
     torch.cuda.synchronize()
+    t1 = time.time()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    if window is not None:
+        window += [t0, t1]
     return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
+
+
+def batched_leg(grid, name, precision, knots, steps, peaks, stream, dist, seed=31):
+    """The gradient of FD over `knots` knot points of one workload robot in one
+    launch per step (trajectories of 128 knot points), in FP32, mixed (FP32 with
+    FP64 pivots) or FP64-plain; throughput and the fraction of the measured FP32
+    (or, for FP64-plain, FP64) multiply-add rate for the counted operations."""
+    import torch
+    r = gi.robot(name)
+    m = grid.Model.from_robot(r, precision="mixed" if precision == "mixed" else "fp32")
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    q, qd, tau = (torch.from_numpy(x).to("cuda", dt) for x in gi.states(r.n, knots, seed))
+    J = torch.empty((knots, r.n, 2 * r.n), device="cuda", dtype=dt)
+    sec = time_steps(lambda: m.grad_fd(q, qd, tau, out=J), steps, 2, stream, dist)
+    m.close()
+    ms = sec / steps * 1e3
+    flops = FLOPS_PER_KNOT[name]
+    tflops = flops * knots / (ms / 1e3) / 1e12
+    peak = peaks["fp64"] if precision == "fp64" else peaks["fp32"]
+    return {"value": knots * steps / sec, "unit": UNIT, "ms_per_launch": ms, "knot_points_per_launch": knots,
+            "flops_per_knot": flops, "achieved_tflops": tflops, "peak_tflops": peak, "frac": tflops / peak,
+            "peak_kind": "fp64 measured" if precision == "fp64" else "fp32 measured"}
 
 
 def traj_leg(grid, model, stream, dist, B=2048, H=64, dt=0.01):
@@ -337,28 +406,42 @@ def cpu_oracle_rate(robot, seconds_min=10.0, seconds_max=30.0, threads=None):
     return done / el, threads, done, el
 
 
-def serve_leg(grid, seconds, rate_hz=20000.0, seed=5005):
-    """Serving workload: open-loop Poisson arrivals at rate_hz, robot uniform
-    over the 7/12/30-DoF models, horizon uniform over {16, 32, 64, 128, 256};
-    1 s warm-up, then `seconds` measured. Native producer/consumer threads."""
+def serve_leg(grid, seconds, rates=(20000.0,), sweep_seconds=2.0, seed=5005):
+    """Serving workload: open-loop Poisson arrivals, robot uniform over the
+    7/12/30-DoF models, horizon uniform over {16, 32, 64, 128, 256}; 1 s warm-up,
+    then `seconds` measured at the first rate (the workload's 20k req/s), then
+    `sweep_seconds` at each further rate (the load sweep). Native producer and
+    consumer threads; one persistent kernel for the whole leg."""
     names = ["chain7", "tree12", "tree30"]
     models = [grid.Model.from_robot(gi.robot(r)) for r in names]
     K = 1024
     pools = [np.stack(gi.states(m.n, K, gi.workload_seed(5, K) + i)).astype(np.float32)
              for i, m in enumerate(models)]
     horizons = [16, 32, 64, 128, 256]
-    srv = grid.Server(models, ring_slots=2048, arena_bytes=1 << 30)
+    srv = grid.Server(models, ring_slots=4096, arena_bytes=2 << 30)
     srv.start()
-    srv.bench(rate_hz, 1.0, seed, horizons, pools)
-    st = srv.bench(rate_hz, seconds, seed + 1, horizons, pools)
+    srv.bench(rates[0], 1.0, seed, horizons, pools)
+    rows = []
+    for i, rate in enumerate(rates):
+        st = srv.bench(rate, seconds if i == 0 else sweep_seconds, seed + 1 + i, horizons, pools)
+        rows.append({"rate_hz": rate, "seconds": seconds if i == 0 else sweep_seconds,
+                     "completed": int(st["completed"]), "knot_points_per_s": st["knot_points"] / st["wall_s"],
+                     "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "p50_ms_h128": st["p50_ms_h128"],
+                     "p99_ms_h128": st["p99_ms_h128"], "max_ms": st["max_ms"], "refused": int(st["refused"]),
+                     "status": int(st["status"])})
+        if st["p99_ms"] > 20.0 or st["status"] != 0:
+            break                                    # far past the knee
     status = srv.stop()
     srv.close()
-    return {"rate_hz": rate_hz, "seconds": seconds, "robots": names, "horizons": horizons,
-            "completed": int(st["completed"]), "knot_points_per_s": st["knot_points"] / st["wall_s"],
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "p50_ms_h128": st["p50_ms_h128"],
-            "p99_ms_h128": st["p99_ms_h128"], "max_ms": st["max_ms"], "refused": int(st["refused"]),
-            "status": int(st["status"]), "kernel_status": int(status),
-            "latency": "scheduled arrival to the host seeing the done flag"}
+    for m in models:
+        m.close()
+    head = dict(rows[0])
+    knee = next((r["rate_hz"] for r in rows if r["p99_ms_h128"] > 1.0), None)
+    head.update({"robots": names, "horizons": horizons, "kernel_status": int(status),
+                 "latency": "scheduled arrival to the host seeing the done flag",
+                 "sweep": rows[1:], "p99_h128_above_1ms_from_rate_hz": knee,
+                 "saturated_knot_points_per_s": max(r["knot_points_per_s"] for r in rows)})
+    return head
 
 
 def run_reference(args):
@@ -397,7 +480,6 @@ def run_reference(args):
 def run_ours(args):
     import torch
     import paper_2109_06976_gb300 as grid
-    from paper_2109_06976_gb300.flops import grad_fd_flops_per_knot
 
     rank, world, local, dist = dist_setup(args.gpus)
     torch.cuda.set_device(local)
@@ -413,45 +495,48 @@ def run_ours(args):
     J = torch.empty((Nk, n, 2 * n), device="cuda")
     in_bytes = 3 * Nk * n * 4
     out_bytes = Nk * 2 * n * n * 4
+    flops_knot = FLOPS_PER_KNOT["chain7"]
 
     def step():
         model.grad_fd(q, qd, tau, out=J)
 
-    if args.only_tree12:
-        # the 12-DoF tree's step alone (half the main batch), for profiling captures
-        t12 = gi.tree12()
-        m12 = grid.Model.from_robot(t12)
-        N12 = Nk // 2
-        q12, qd12, tau12 = (torch.from_numpy(x.astype(np.float32)).cuda()
-                            for x in gi.states(12, N12, seed + 1))
-        J12 = torch.empty((N12, 12, 24), device="cuda")
-        sec12 = time_steps(lambda: m12.grad_fd(q12, qd12, tau12, out=J12), args.steps, args.warmup, stream, dist)
+    if args.only_tree12 or args.only_tree30:
+        # one robot's step alone, for profiling captures
+        name = "tree12" if args.only_tree12 else "tree30"
+        rr = gi.robot(name)
+        mm = grid.Model.from_robot(rr)
+        Nr = Nk // 2 if args.only_tree12 else Nk // 16
+        qr, qdr, taur = (torch.from_numpy(x.astype(np.float32)).cuda() for x in gi.states(rr.n, Nr, seed + 1))
+        Jr = torch.empty((Nr, rr.n, 2 * rr.n), device="cuda")
+        secr = time_steps(lambda: mm.grad_fd(qr, qdr, taur, out=Jr), args.steps, args.warmup, stream, dist)
         if rank == 0:
-            print(json.dumps({"metric": "gradient of FD, 12-DoF tree", "value": world * N12 * args.steps / sec12,
-                              "unit": UNIT, "ms_per_step": sec12 / args.steps * 1e3, "knot_points": N12}),
+            print(json.dumps({"metric": f"gradient of FD, {name}", "value": world * Nr * args.steps / secr,
+                              "unit": UNIT, "ms_per_step": secr / args.steps * 1e3, "knot_points": Nr}),
                   flush=True)
         if dist:
             dist.destroy_process_group()
         return
 
+    peaks = measure_peaks(grid, local)
+    window = []
     with ClockSampler(local) as clk:
-        sec = time_steps(step, args.steps, args.warmup, stream, dist)
-    clocks = clk.summary()
+        sec = time_steps(step, args.steps, args.warmup, stream, dist, window=window)
+    clocks = clk.summary(*window)
     ms = sec / args.steps * 1e3
     value = aggregate_value(world, Nk, args.steps, sec)
-    flops_knot = grad_fd_flops_per_knot(robot.parent)
     achieved_tflops = flops_knot * Nk / (ms / 1e3) / 1e12
-    dram = NCU_DRAM_BYTES_PER_KNOT.get(kernel_source_hash())
-    fma_pipe = NCU_FMA_PIPE.get(kernel_source_hash())
+    src = kernel_source_hash()
+    traffic = NCU_BYTES_PER_KNOT.get(src)
+    fma_pipe = NCU_FMA_PIPE.get(src)
     if args.only_main:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
                               "knot_points": Nk, "achieved_tflops": achieved_tflops,
+                              "frac": achieved_tflops / peaks["fp32"], "peaks": peaks,
                               "clocks": clocks}), flush=True)
         if dist:
             dist.destroy_process_group()
         return
-
     # End to end through the public API with pinned host buffers, every step:
     # grid_grad_fd_host copies the step's states in, runs the kernel and copies
     # the Jacobians out, in chunks whose copies overlap the kernel.
@@ -498,22 +583,23 @@ def run_ours(args):
     other_value = aggregate_value(world, Nk, gen_steps, sec_gen)
     mgen.close()
 
-    # FP64 plain form on the same GPU (smaller batch, same per-knot work)
-    Nd = 256 * KNOTS
-    q64, qd64, tau64 = (x[:Nd].double() for x in (q, qd, tau))
-    J64 = torch.empty((Nd, n, 2 * n), device="cuda", dtype=torch.float64)
-    sec64 = time_steps(lambda: model.grad_fd(q64, qd64, tau64, out=J64), 5, 2, stream, dist)
-    fp64_value = world * Nd * 5 / sec64
-
-    # 12-DoF tree at the same N and batch
-    t12 = gi.tree12()
-    m12 = grid.Model.from_robot(t12)
-    q12, qd12, tau12 = (torch.from_numpy(x.astype(np.float32)).cuda()
-                        for x in gi.states(12, Nk // 2, seed + 1))
-    J12 = torch.empty((Nk // 2, 12, 24), device="cuda")
-    sec12 = time_steps(lambda: m12.grad_fd(q12, qd12, tau12, out=J12), max(3, args.steps // 4), 2,
-                       stream, dist)
-    t12_value = world * (Nk // 2) * max(3, args.steps // 4) / sec12
+    # every workload robot, batched, in FP32, mixed and FP64-plain (the metric's
+    # "FP32/mixed vs FP64 plain"); N = 128-knot trajectories, one launch per step
+    robots = None
+    if rank == 0 and world == 1:
+        K = 262144
+        robots = {
+            "chain7": {"fp32": {"value": value, "unit": UNIT, "ms_per_launch": ms, "knot_points_per_launch": Nk,
+                                "flops_per_knot": flops_knot, "achieved_tflops": achieved_tflops,
+                                "peak_tflops": peaks["fp32"], "frac": achieved_tflops / peaks["fp32"],
+                                "peak_kind": "fp32 measured", "note": "the headline step"},
+                       "fp64": batched_leg(grid, "chain7", "fp64", K, 5, peaks, stream, dist)},
+            "tree12": {"fp32": batched_leg(grid, "tree12", "fp32", 4 * K, 10, peaks, stream, dist),
+                       "fp64": batched_leg(grid, "tree12", "fp64", K // 2, 5, peaks, stream, dist)},
+            "tree30": {"fp32": batched_leg(grid, "tree30", "fp32", K, 5, peaks, stream, dist),
+                       "mixed": batched_leg(grid, "tree30", "mixed", K, 5, peaks, stream, dist),
+                       "fp64": batched_leg(grid, "tree30", "fp64", K // 4, 3, peaks, stream, dist)},
+        }
 
     # single-trajectory latency at N = 128 (compute only)
     q1, qd1, tau1 = q[:KNOTS], qd[:KNOTS], tau[:KNOTS]
@@ -539,7 +625,9 @@ def run_ours(args):
 
     serve = None
     if rank == 0 and world == 1 and args.serve_seconds > 0:
-        serve = serve_leg(grid, args.serve_seconds)
+        serve = serve_leg(grid, args.serve_seconds,
+                          rates=(20000.0,) + ((50000.0, 100000.0, 200000.0, 400000.0, 800000.0)
+                                              if args.serve_sweep else ()))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -563,12 +651,20 @@ def run_ours(args):
                 "l2": f"inputs {in_bytes / 1e6:.0f} MB and outputs {out_bytes / 1e6:.0f} MB per "
                       f"step, both larger than the 129 MB L2",
                 "parallelism": f"dp{world}"},
-            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved_tflops / FP32_PEAK_TFLOPS,
-                         "traffic": None if dram is None else dram * Nk,
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peaks["fp32"],
+                         "unit": "TFLOP/s", "frac": achieved_tflops / peaks["fp32"],
+                         "traffic": None if traffic is None else traffic * Nk,
+                         "traffic_note": "ncu capture of the same kernel sources (DRAM read + write and "
+                                         "SM-to-L2 writes), scaled by knot points" if traffic else
+                                         "no capture of the current kernel sources",
                          "flops_per_knot": flops_knot,
+                         "flops_source": "operation count of the method in compact form (oracle/opcount.py)",
                          "fp32_pipe_util_ncu": fma_pipe,
-                         "peak_note": "FP32 from 152 SMs x 128 lanes x 2 x 2070 MHz",
+                         "peak_note": "FP32 multiply-add rate measured in this run (grid_peak_loop, faster of "
+                                      "scalar and paired instructions, all SMs); nominal "
+                                      f"{FP32_NOMINAL_TFLOPS:.1f} TFLOP/s at 2070 MHz",
+                         "frac_of_nominal": achieved_tflops / FP32_NOMINAL_TFLOPS,
+                         "peaks_measured": peaks,
                          "hbm_gbs": (in_bytes + out_bytes) / (ms / 1e3) / 1e9},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": in_bytes,
                     "d2h_bytes_per_step": out_bytes,
@@ -582,8 +678,10 @@ def run_ours(args):
                          "other_kernel_value": other_value, "unit": UNIT,
                          "note": "the same step in the other kernel (run-time topology vs the chain "
                                  "compiled for its length)"},
-            "fp64_plain": {"value": fp64_value, "unit": UNIT, "knot_points_per_launch": Nd},
-            "tree12": {"value": t12_value, "unit": UNIT, "knot_points_per_launch": Nk // 2},
+            "robots": robots,
+            "robots_note": "gradient of FD of each workload robot, one launch of 128-knot trajectories per "
+                           "step: FP32, mixed (FP64 pivots in M^-1) and FP64-plain; frac = counted flops / "
+                           "the measured FP32 (FP64 for FP64-plain) multiply-add rate",
             "latency_n128_us": lat128,
             "latency_n128_with_io_us": lat128_io,
             "latency_n_sweep_us": sweep,
@@ -596,6 +694,7 @@ def run_ours(args):
             "serve": serve,
             "cpu_baseline": cpu,
             "clocks": clocks,
+            "timed_s": sec,
             "gpu_launches": args.steps,
             "gpu_launches_note": "timed region of `value`: one grid_grad_fd kernel per step",
             "kernel_source": kernel_source_hash(),
@@ -609,7 +708,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=80)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
@@ -622,6 +721,10 @@ def main():
                     help="time only the main FP32 step (used for profiling captures)")
     ap.add_argument("--only-tree12", action="store_true",
                     help="time only the 12-DoF tree's step (used for profiling captures)")
+    ap.add_argument("--only-tree30", action="store_true",
+                    help="time only the 30-DoF tree's step (used for profiling captures)")
+    ap.add_argument("--no-serve-sweep", dest="serve_sweep", action="store_false",
+                    help="serve only at the workload's 20k req/s (no load sweep)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

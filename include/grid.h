@@ -318,7 +318,8 @@ grid_status grid_fd_vjp_f64(const grid_model* model, int N, const double* q, con
  * while others run start at once and overlap on the device. Every wait in the
  * kernel is bounded: with no new work for the idle timeout (default 2 s) the
  * kernel ends with GRID_E_TIMEOUT. All models must be FP32 models of the
- * current device; the server runs in FP32 with 16 lanes per knot point.
+ * current device (GRID_E_ARG for a GRID_MIXED model: the serving kernel has no
+ * FP64 pivots); the server runs in FP32 with 16 lanes per knot point.
  */
 typedef struct grid_server grid_server;
 
@@ -370,7 +371,8 @@ grid_status grid_server_bench(grid_server* server, double rate_hz, double second
  * running, such as a real-time control loop, where cudaMalloc can synchronise
  * the device and take unbounded time, or a host application that owns all
  * device memory and only lends the library its buffers.)
- *   models[nmodels]     FP32 models of the current device
+ *   models[nmodels]     FP32 models of the current device (GRID_E_ARG for a
+ *                       GRID_MIXED model: the serving kernel has no FP64 pivots)
  *   req_model, req_H    host arrays [nreq]: model index and knot points
  *   q, qd, tau          host arrays [nreq] of DEVICE pointers, each [H][n]
  *   J                   host array [nreq] of DEVICE pointers, each [H][n][2n]
@@ -380,14 +382,36 @@ grid_status grid_server_bench(grid_server* server, double rate_hz, double second
  * 1 <= nreq <= 256 per call, larger lists are refused with GRID_E_ARG. The
  * first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture. Calls share the array and overwrite its contents, so calls that
- * overlap on the GPU (different streams, or another call before this one's
- * kernel has finished) race; serialise them.
+ * capture. The request list goes to the device by value as the argument of a
+ * small set-up kernel on `stream`, which also clears the array's counters; the
+ * host arrays may be reused as soon as the call returns. Calls share the array
+ * and overwrite its contents, so calls that overlap on the GPU (different
+ * streams, or another call before this one's kernel has finished) race;
+ * serialise them. Every request is published before the launch, so the
+ * kernel's waits and its request search always succeed; the call reports
+ * argument and launch errors, and a fault inside a kernel surfaces at the
+ * caller's next synchronisation, as for every compute call.
  */
 grid_status grid_serve_batch_static(const grid_model* const* models, int nmodels, int nreq,
                                     const int* req_model, const int* req_H, const float* const* q,
                                     const float* const* qd, const float* const* tau, float* const* J,
                                     void* stream);
+
+/*
+ * grid_peak_loop -- arithmetic-throughput loop, the denominator of a roofline
+ * fraction (a measurement utility; not part of the paper's method). Launches
+ * `blocks` x `threads` threads on `stream`; each runs `iters` iterations of 8
+ * independent multiply-add chains held in registers, then writes one value to
+ * out[block * threads + thread]:
+ *   kind 0  FP32 fma          (out: float [blocks * threads])
+ *   kind 1  paired FP32 fma   (two independent multiply-adds per instruction; out: float)
+ *   kind 2  FP64 fma          (out: double [blocks * threads])
+ * *flops receives the floating-point operations of the launch (2 per
+ * multiply-add); divide by the launch's duration (CUDA events on `stream`).
+ * threads: a multiple of 32 up to 1024. GRID_E_ARG for bad arguments.
+ */
+grid_status grid_peak_loop(int kind, int blocks, int threads, int iters, void* out, double* flops,
+                           void* stream);
 
 /* grid_last_error -- thread-local description of the last failure ("" if none). */
 const char* grid_last_error(void);

@@ -52,6 +52,7 @@ SIGNATURES = {
     "grid_server_stop": [_P],
     "grid_server_destroy": [_P],
     "grid_server_bench": [_P, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong, _P, _I, _P, _I, _P],
+    "grid_peak_loop": [_I, _I, _I, _I, _P, ctypes.POINTER(ctypes.c_double), _P],
 }
 
 

@@ -263,6 +263,11 @@ grid_status grid_server_create(const grid_model* const* models, int nmodels, int
       delete s;
       return GRID_E_ARG;
     }
+    if (models[i]->prec != GRID_FP32) {    // the serving kernel has no FP64 pivots
+      grid_set_error("grid_server_create: model %d is not an FP32 model (serving runs in FP32)", i);
+      delete s;
+      return GRID_E_ARG;
+    }
     s->models[i] = models[i];
     s->args.models[i] = models[i]->dev_f;
     max_stride = std::max(max_stride, models[i]->host_f->L.stride);
@@ -594,6 +599,42 @@ static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScr
 std::mutex g_static_mu;
 void* g_static_addr[64] = {nullptr};      // per device, filled by the first call on it
 
+// The request list travels to the device as a kernel argument (by value, about
+// 12 KB), so the call reads no host memory after it returns.
+struct StaticList {
+  unsigned long long q[kStaticMaxReq], qd[kStaticMaxReq], tau[kStaticMaxReq], J[kStaticMaxReq];
+  int model[kStaticMaxReq], H[kStaticMaxReq], first_unit[kStaticMaxReq], nunits[kStaticMaxReq];
+  int nreq, units;
+};
+
+// Writes the call's descriptors into the scratch array and resets its control
+// block, done flags and counters (the previous call's contents are overwritten).
+__global__ void static_setup_kernel(StaticScratch* d, const StaticList L) {
+  for (int i = threadIdx.x; i < kStaticMaxReq; i += blockDim.x) {
+    ServeReq r{};
+    const bool live = i < L.nreq;
+    r.q = live ? L.q[i] : 0ull;
+    r.qd = live ? L.qd[i] : 0ull;
+    r.tau = live ? L.tau[i] : 0ull;
+    r.J = live ? L.J[i] : 0ull;
+    r.model = live ? L.model[i] : 0;
+    r.H = live ? L.H[i] : 0;
+    r.first_unit = live ? L.first_unit[i] : 0;
+    r.nunits = live ? L.nunits[i] : 0;
+    r.seq = live ? i : -1;
+    d->reqs[i] = r;
+    d->done[i] = -1;
+    d->tiles_done[i] = 0;
+  }
+  if (threadIdx.x == 0) {
+    d->ctl.published_units = L.units;     // everything is published up front ...
+    d->ctl.stop = 1;                      // ... and warps leave once the units run out
+    d->ctl.status = GRID_OK;
+    d->ctl.pad = 0;
+    d->next_unit = 0;
+  }
+}
+
 }  // namespace
 
 extern "C" grid_status grid_serve_batch_static(const grid_model* const* models, int nmodels, int nreq,
@@ -621,6 +662,10 @@ extern "C" grid_status grid_serve_batch_static(const grid_model* const* models, 
       grid_set_error("grid_serve_batch_static: model %d missing or on another device", i);
       return GRID_E_ARG;
     }
+    if (models[i]->prec != GRID_FP32) {
+      grid_set_error("grid_serve_batch_static: model %d is not an FP32 model (serving runs in FP32)", i);
+      return GRID_E_ARG;
+    }
     a.models[i] = models[i]->dev_f;
     max_stride = std::max(max_stride, models[i]->host_f->L.stride);
     max_sched = std::max(max_sched, models[i]->host_f->steps[1] * kServeT);
@@ -639,12 +684,10 @@ extern "C" grid_status grid_serve_batch_static(const grid_model* const* models, 
     }
     base = g_static_addr[dev];
   }
-  // Descriptors and counters, prepared on the host stack and copied into the array
-  // (the previous call's contents are overwritten; counters start at zero).
-  StaticScratch h;
-  std::memset(&h, 0, sizeof(h));
+  // The request list, passed by value to the set-up kernel on `stream`.
+  StaticList L;
+  std::memset(&L, 0, sizeof(L));
   int units = 0;
-  for (int i = 0; i < kStaticMaxReq; ++i) { h.reqs[i].seq = -1; h.done[i] = -1; }
   for (int i = 0; i < nreq; ++i) {
     const int m = req_model[i];
     if (m < 0 || m >= nmodels || req_H[i] < 1 || !q[i] || !qd[i] || !tau[i] || !J[i] ||
@@ -652,25 +695,24 @@ extern "C" grid_status grid_serve_batch_static(const grid_model* const* models, 
       grid_set_error("grid_serve_batch_static: request %d has a bad model, horizon or pointer", i);
       return GRID_E_ARG;
     }
-    ServeReq& r = h.reqs[i];
-    r.q = (unsigned long long)q[i];
-    r.qd = (unsigned long long)qd[i];
-    r.tau = (unsigned long long)tau[i];
-    r.J = (unsigned long long)J[i];
-    r.model = m;
-    r.H = req_H[i];
-    r.first_unit = units;
-    r.nunits = (req_H[i] + kServeG - 1) / kServeG;
-    r.seq = i;
-    units += r.nunits;
+    L.q[i] = (unsigned long long)q[i];
+    L.qd[i] = (unsigned long long)qd[i];
+    L.tau[i] = (unsigned long long)tau[i];
+    L.J[i] = (unsigned long long)J[i];
+    L.model[i] = m;
+    L.H[i] = req_H[i];
+    L.first_unit[i] = units;
+    L.nunits[i] = (req_H[i] + kServeG - 1) / kServeG;
+    units += L.nunits[i];
   }
-  h.ctl.published_units = units;         // everything is published up front ...
-  h.ctl.stop = 1;                         // ... and warps leave once the units run out
+  L.nreq = nreq;
+  L.units = units;
   StaticScratch* d = reinterpret_cast<StaticScratch*>(base);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  e = cudaMemcpyAsync(d, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+  static_setup_kernel<<<1, 256, 0, st>>>(d, L);
+  e = cudaGetLastError();
   if (e != cudaSuccess) {
-    grid_set_error("grid_serve_batch_static: copy of descriptors: %s", cudaGetErrorString(e));
+    grid_set_error("grid_serve_batch_static: set-up launch: %s", cudaGetErrorString(e));
     return GRID_E_CUDA;
   }
   a.nmodels = nmodels;

@@ -88,3 +88,30 @@ def col_err_split(x, y, zero=1e-12, floor=1e-6):
     e_nz = np.where(zmask, 0.0, diff / np.maximum(nrm, floor * m))
     e_z = np.where(zmask, diff / m, 0.0)
     return float(e_nz.max()), float(e_z.max())
+
+
+def derived_col_bar(minv, dc, J, tol=1e-4):
+    """Per knot point and column j, the FP32 bar max(tol, n kappa_2(M) u alpha_j) with
+    alpha_j = ||M^-1||_2 ||dc_:j||_2 / ||J_:j||_2: the first-order error of
+    J_:j = -M^-1 dc_:j computed through a computed inverse is about
+    n kappa_2(M) u ||M^-1|| ||dc_:j||, so a column made small by cancellation in the
+    product (alpha_j >> 1) carries that much more error relative to its own norm.
+    minv [N, n, n], dc [N, n, 2n] (dID/dq | dID/dqd at qdd) and J [N, n, 2n] from the
+    oracle. Returns [N, 2n]."""
+    minv = np.asarray(minv, dtype=np.float64)
+    dc = np.asarray(dc, dtype=np.float64)
+    J = np.asarray(J, dtype=np.float64)
+    n = minv.shape[-1]
+    nrm_mi = np.linalg.norm(minv, ord=2, axis=(-2, -1))               # [N]
+    kappa = np.linalg.cond(minv)                                      # [N]
+    alpha = nrm_mi[:, None] * np.linalg.norm(dc, axis=-2) / np.maximum(np.linalg.norm(J, axis=-2), 1e-300)
+    return np.maximum(tol, n * kappa[:, None] * U32 * alpha)
+
+
+def col_rel_err_cols(x, y, floor=1e-6):
+    """The per-column metric itself, [N, cols]."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    nrm = np.linalg.norm(y, axis=-2)
+    den = np.maximum(np.maximum(nrm, floor * nrm.max(axis=-1, keepdims=True)), 1e-30)
+    return np.abs(x - y).max(axis=-2) / den

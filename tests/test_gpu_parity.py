@@ -6,7 +6,8 @@ import pytest
 
 import grid_inputs as gi
 import oracle
-from tests.metrics import FLOOR32, FLOOR64, col_rel_err, col_rel_err_knots, col_rel_err_stats, fp32_bar, vec_rel_err
+from tests.metrics import (FLOOR32, FLOOR64, col_rel_err, col_rel_err_cols, col_rel_err_knots, col_rel_err_stats,
+                           derived_col_bar, fp32_bar, vec_rel_err)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -330,3 +331,32 @@ def test_zero_copy_host_buffers(grid):
     torch.cuda.synchronize()
     for a, b in zip(dv, hv):
         assert torch.equal(a.cpu(), b)
+
+
+@pytest.mark.parametrize("key,prec", [("chain7", "fp32"), ("tree12", "fp32"), ("tree30", "fp32"),
+                                      ("tree30", "mixed")])
+def test_precision_report_workload(grid, key, prec, capsys):
+    """FP32 gradient of FD of each workload robot at N = 1024 against the FP64
+    oracle, measured three ways: the per-column metric with the survey's floor
+    (1e-6) and with the FP32 floor (1e-4), and the ratio of the 1e-6-floor error
+    to the derived per-column bound max(1e-4, n kappa_2(M) u alpha_j)
+    (tests/metrics.py: derived_col_bar). Printed for the record."""
+    r = _robot(key)
+    m = _model(grid, key, prec)
+    N = 1024
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, N, gi.workload_seed(3, N), torch.float32)
+    ref_J, ref_qdd = oracle.grad_fd(r, q64, qd64, tau64, nthreads=8, with_qdd=True)
+    ref_mi = oracle.minv(r, q64, nthreads=8)
+    dq, dqd = oracle.grad_rnea(r, q64, qd64, ref_qdd, nthreads=8)
+    J = m.grad_fd(q, qd, tau).cpu().numpy()
+    e6 = col_rel_err_cols(J, ref_J, 1e-6)
+    e4 = col_rel_err_cols(J, ref_J, FLOOR32)
+    bar = derived_col_bar(ref_mi, np.concatenate([dq, dqd], axis=2), ref_J)
+    nku = r.n * np.linalg.cond(ref_mi) * 2.0 ** -24
+    line = (f"{key} {prec:5s} N={N}: max err floor 1e-6 {e6.max():.2e} (p50 {np.median(e6.max(axis=1)):.2e}), "
+            f"floor 1e-4 {e4.max():.2e}; n kappa u max {nku.max():.2e}; "
+            f"err / derived bar max {(e6 / bar).max():.2f}; columns above 1e-4 (floor 1e-6): "
+            f"{int((e6 > 1e-4).sum())} of {e6.size}")
+    with capsys.disabled():
+        print("\n" + line)
+    assert e4.max() <= TOL32, line
