@@ -34,7 +34,7 @@ import grid_inputs as gi  # noqa: E402
 METRIC = "∇FD knot-points/sec at N=128 (FP32/mixed vs FP64 plain); serve p50/p99 ms"
 UNIT = "knot-points/s"
 KNOTS = 128                      # knot points per trajectory (the metric's N)
-TRAJ = 65536                     # trajectories per step (8,388,608 knot points)
+TRAJ = 16384                     # trajectories per step (2,097,152 knot points)
 L2_BYTES = 129 * 1024 * 1024
 # Counted operations of one knot point of the gradient of FD (transforms, RNEA, direct
 # M^-1, FD, RNEA at qdd, dRNEA, product), written from oracle/opcount.py's count of the
@@ -708,7 +708,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=80)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")

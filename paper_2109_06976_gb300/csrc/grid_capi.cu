@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <type_traits>
+#include <vector>
 
 #include "grid_internal.h"
 
@@ -33,6 +34,8 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
 GRID_DECLARE(float, false)
 GRID_DECLARE(float, true)
 GRID_DECLARE(double, false)
+
+bool forest_compiled(int k, int l);   // grid_forest.cu
 
 namespace {
 
@@ -112,6 +115,98 @@ void build_branches(grid_model* m, const int* parent, const double* axis, const 
     return;
   }
   m->branches = K;
+}
+
+// ---------------------------------------------------------------- parts
+// A robot whose base components differ (a humanoid's torso with its arms, and
+// its legs) gets one model per component, placed in the robot's arrays
+// (ModelDev::ld, gslot, gidx, gmask): the components share nothing through the
+// fixed base, so each is a problem of its own. Any failure leaves nparts = 0.
+void free_parts(grid_model* m) {
+  for (int p = 0; p < m->nparts; ++p) {
+    cudaFree(m->parts[p].dev_f);
+    cudaFree(m->parts[p].dev_d);
+    delete m->parts[p].host_f;
+    delete m->parts[p].host_d;
+  }
+  delete[] m->parts;
+  m->parts = nullptr;
+  m->nparts = 0;
+}
+
+template <class S>
+void place(ModelDev<S>* P, int ld, const std::vector<int>& idx) {
+  P->ld = ld;
+  P->gmask = 0u;
+  for (int s = 0; s < P->n; ++s) {
+    P->gslot[s] = idx[s];
+    P->gmask |= 1u << idx[s];
+  }
+  for (int k = 0; k < P->n; ++k) P->gidx[k] = idx[P->perm[k]];
+}
+
+void build_parts(grid_model* m, const int* parent, const int* jtype, const double* axis, const double* X_tree,
+                 const double* inertia, const double* gravity) {
+  const int n = m->n;
+  std::vector<int> root(n);
+  std::vector<std::vector<int>> comps;
+  for (int i = 0; i < n; ++i) {
+    root[i] = parent[i] < 0 ? i : root[parent[i]];
+    if (parent[i] < 0) comps.emplace_back();
+  }
+  if (comps.size() < 2) return;
+  std::vector<int> slot_of(n), comp_of(n, -1);
+  int nc = 0;
+  for (int i = 0; i < n; ++i) {
+    if (parent[i] < 0) comp_of[i] = nc++;
+    else comp_of[i] = comp_of[root[i]];
+    slot_of[i] = (int)comps[comp_of[i]].size();
+    comps[comp_of[i]].push_back(i);
+  }
+  m->parts = new grid_part[comps.size()]();
+  for (size_t c = 0; c < comps.size(); ++c) {
+    const std::vector<int>& idx = comps[c];
+    const int k = (int)idx.size();
+    std::vector<int> par(k), jt(k);
+    std::vector<double> ax(3 * k), xt(12 * k), in(10 * k);
+    for (int s = 0; s < k; ++s) {
+      const int b = idx[s];
+      par[s] = parent[b] < 0 ? -1 : slot_of[parent[b]];
+      jt[s] = jtype ? jtype[b] : GRID_JOINT_REVOLUTE;
+      for (int a = 0; a < 3; ++a) ax[3 * s + a] = axis[3 * b + a];
+      for (int a = 0; a < 12; ++a) xt[12 * s + a] = X_tree[12 * b + a];
+      for (int a = 0; a < 10; ++a) in[10 * s + a] = inertia[10 * b + a];
+    }
+    grid_part& P = m->parts[c];
+    P.n = k;
+    P.host_f = new ModelDev<float>();
+    P.host_d = new ModelDev<double>();
+    m->nparts = (int)c + 1;                   // so that free_parts releases this one too
+    if (grid_build_model(k, par.data(), jt.data(), ax.data(), xt.data(), in.data(), gravity, P.host_f,
+                         P.host_d) != GRID_OK) {
+      free_parts(m);
+      return;
+    }
+    place(P.host_f, n, idx);
+    place(P.host_d, n, idx);
+    P.chain = !P.host_d->any_prism;
+    for (int i = 0; P.chain && i < k; ++i) P.chain = P.host_d->parent[i] == i - 1 && P.host_d->perm[i] == i;
+    if (cudaMalloc(&P.dev_f, sizeof(ModelDev<float>)) != cudaSuccess ||
+        cudaMalloc(&P.dev_d, sizeof(ModelDev<double>)) != cudaSuccess ||
+        cudaMemcpy(P.dev_f, P.host_f, sizeof(ModelDev<float>), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(P.dev_d, P.host_d, sizeof(ModelDev<double>), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      free_parts(m);
+      return;
+    }
+  }
+}
+
+bool all_moving(int nb, const int* jtype) {
+  if (!jtype) return true;
+  for (int i = 0; i < nb; ++i)
+    if (jtype[i] == GRID_JOINT_FIXED) return false;
+  return true;
 }
 
 // ---------------------------------------------------------------- host buffers
@@ -329,6 +424,12 @@ grid_status grid_create_ex(int n, const int* parent, const int* jtype, const dou
   // them the forest runs in its own kernel.
   if (m->forest_k > 1 && nb_moving_equals_bodies(n, jtype) && m->n == n)
     build_branches(m, parent, axis, X_tree, inertia, gravity);
+  // Base components that the forest kernels do not cover run as parts.
+  m->nparts = 0;
+  m->parts = nullptr;
+  if (m->host_d->ncomp >= 2 && !(m->forest_k > 1 && forest_compiled(m->forest_k, m->forest_l)) &&
+      all_moving(n, jtype) && m->n == n)
+    build_parts(m, parent, jtype, axis, X_tree, inertia, gravity);
   *out = m;
   return GRID_OK;
 }
@@ -341,6 +442,7 @@ grid_status grid_destroy(grid_model* m) {
   grid_gen_cache_free(m->gen);
   host_pipe_free(m->pipe);
   free_branches(m);
+  free_parts(m);
   delete m->host_f;
   delete m->host_d;
   delete m;

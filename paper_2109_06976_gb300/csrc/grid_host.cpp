@@ -270,6 +270,12 @@ static grid_status build_moving(int n, const int* parent, const int* jt, const d
     grid_set_error("grid_create: subspace table of %d rows exceeds the step descriptor", nsk);
     return GRID_E_TOPOLOGY;
   }
+  D.ld = n;
+  D.gmask = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  for (int k = 0; k < n; ++k) {
+    D.gslot[k] = k;
+    D.gidx[k] = perm[k];
+  }
   for (int k = 0; k < n; ++k) {
     int c = perm[k];
     D.parent[k] = par[k]; D.depth[k] = dep[k]; D.sub_end[k] = send[k];
@@ -393,6 +399,10 @@ static grid_status build_moving(int n, const int* parent, const int* jt, const d
   std::memcpy(F.skoff, D.skoff, sizeof(D.skoff));
   std::memcpy(F.branch, D.branch, sizeof(D.branch));
   std::memcpy(F.et_ident, D.et_ident, sizeof(D.et_ident));
+  F.ld = D.ld;
+  F.gmask = D.gmask;
+  std::memcpy(F.gslot, D.gslot, sizeof(D.gslot));
+  std::memcpy(F.gidx, D.gidx, sizeof(D.gidx));
   std::memcpy(F.sched, D.sched, sizeof(D.sched));
   for (int k = 0; k < GRID_MAX_DOF; ++k) {
     for (int a = 0; a < 4; ++a) F.axis[k][a] = (float)D.axis[k][a];

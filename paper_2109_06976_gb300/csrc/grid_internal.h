@@ -147,6 +147,15 @@ struct ModelDev {
   int branch[GRID_MAX_DOF];      // slot of a body with >= 2 children, else -1
   int et_ident[GRID_MAX_DOF];
   int jt[GRID_MAX_DOF];          // GRID_JOINT_REVOLUTE or GRID_JOINT_PRISMATIC
+  // Placement in the caller's arrays. A whole robot has ld = n, gslot and gidx
+  // the identity and perm. A part (one base component of a robot, run as a
+  // problem of its own) has ld = the robot's joints per knot point: its caller
+  // slot s is the robot's joint gslot[s], its internal body k the robot's joint
+  // gidx[k] = gslot[perm[k]], and gmask has a bit for each of its joints.
+  int ld;
+  int gslot[GRID_MAX_DOF];
+  int gidx[GRID_MAX_DOF];
+  unsigned gmask;
   alignas(16) S axis[GRID_MAX_DOF][4];   // unit axis, padded
   S ET[GRID_MAX_DOF][9];
   S rT[GRID_MAX_DOF][3];
@@ -187,6 +196,8 @@ struct grid_model {
   ModelDev<double>* br_dev_d;
   ModelDev<float>* br_host_f;
   ModelDev<double>* br_host_d;
+  int nparts;                    // > 0: the gradient of FD of large batches runs per base component
+  struct grid_part* parts;       // [nparts] (grid_capi.cu), else nullptr
   struct grid_gen_cache* gen;    // kernels compiled at run time for this model (grid_nvrtc.cpp)
   struct grid_host_pipe* pipe;   // staging and streams of grid_grad_fd_host (grid_capi.cu)
   int host_chunk_opt;            // knot points per chunk of grid_grad_fd_host (0 = automatic)
@@ -194,6 +205,18 @@ struct grid_model {
   ModelDev<float>* dev_f;        // device copies
   ModelDev<double>* dev_d;
   ModelDev<float>* host_f;       // host mirrors (for launch decisions)
+  ModelDev<double>* host_d;
+};
+
+// One base component of a robot whose components differ: its own model
+// (placed in the robot's arrays, see ModelDev::ld) and whether it is a serial
+// chain of revolute joints in caller order.
+struct grid_part {
+  int n;
+  int chain;
+  ModelDev<float>* dev_f;
+  ModelDev<double>* dev_d;
+  ModelDev<float>* host_f;
   ModelDev<double>* host_d;
 };
 

@@ -170,22 +170,13 @@ template <class S, int MODE>
 grid_status launch_forest(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                           const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
 
-// Picks the lane count T (option or by size) and the M^-1 columns per lane.
+// The kernel for one model (the robot, or one of its parts): the lane count T
+// (option or by size), the M^-1 columns per lane, run-time specialisation.
 template <class S, int MODE, bool MIXED>
-grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const S* x3, const S* x4,
-                     S* out, S* out2, S* out3, cudaStream_t st) {
-  const ModelDev<S>* hm;
-  const ModelDev<S>* dm;
-  if constexpr (std::is_same<S, float>::value) { hm = m->host_f; dm = m->dev_f; }
-  else { hm = m->host_d; dm = m->dev_d; }
-  int T = m->lanes_opt;
+grid_status dispatch_model(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int T, int N,
+                           const S* q, const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3,
+                           cudaStream_t st) {
   const int n = hm->n;
-  if constexpr (MODE == MODE_GRAD && !MIXED) {
-    if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
-      return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
-    if (m->forest_k > 1 && m->specialize_opt && T == 0 && forest_compiled(m->forest_k, m->forest_l))
-      return launch_forest<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
-  }
   // Default lanes: 8 up to 12 bodies, else 16 (throughput). A batch smaller
   // than two knot points per SM is latency-bound: for more bodies than 8 lanes,
   // one warp per knot point then shortens the parallel phases (measured for the
@@ -212,6 +203,49 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   if (T == 32) return launch_d<S, MODE, 32, 1, MIXED>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
   grid_set_error("lanes option %d not in {0, 8, 16, 32}", T);
   return GRID_E_ARG;
+}
+
+// Picks the kernels for a model: the chain or forest kernels compiled for its
+// topology, its base components one after another (parts), or dispatch_model.
+template <class S, int MODE, bool MIXED>
+grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const S* x3, const S* x4,
+                     S* out, S* out2, S* out3, cudaStream_t st) {
+  const ModelDev<S>* hm;
+  const ModelDev<S>* dm;
+  if constexpr (std::is_same<S, float>::value) { hm = m->host_f; dm = m->dev_f; }
+  else { hm = m->host_d; dm = m->dev_d; }
+  const int T = m->lanes_opt;
+  const int n = hm->n;
+  if constexpr (MODE == MODE_GRAD && !MIXED) {
+    if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
+      return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+    if (m->forest_k > 1 && m->specialize_opt && T == 0 && forest_compiled(m->forest_k, m->forest_l))
+      return launch_forest<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);
+  }
+  if constexpr (MODE == MODE_GRAD) {
+    // Base components that differ (a humanoid's torso with its arms, and its
+    // legs) share nothing through the fixed base: each runs as a problem of its
+    // own, in the kernel for its size and topology, and writes its rows of J
+    // (and of M^-1 and qdd). Batches of at most two knot points per SM stay in
+    // one launch (latency).
+    if (m->nparts > 0 && m->specialize_opt && T == 0 && N > 2 * dev_info(m->device).nsm) {
+      for (int p = 0; p < m->nparts; ++p) {
+        const grid_part& P = m->parts[p];
+        const ModelDev<S>* ph;
+        const ModelDev<S>* pd;
+        if constexpr (std::is_same<S, float>::value) { ph = P.host_f; pd = P.dev_f; }
+        else { ph = P.host_d; pd = P.dev_d; }
+        grid_status r;
+        if (!MIXED && P.chain && P.n >= 2 && P.n <= kChainMaxN)
+          r = launch_chain<S, MODE>(m, ph, pd, N, q, qd, x3, x4, out, out2, out3, st);
+        else
+          r = dispatch_model<S, MODE, MIXED>(m, ph, pd, 0, N, q, qd, x3, x4, out, out2, out3, st);
+        if (r != GRID_OK) return r;
+      }
+      return GRID_OK;
+    }
+  }
+  return dispatch_model<S, MODE, MIXED>(m, hm, dm, T, N, q, qd, x3, x4, out, out2, out3, st);
 }
 
 

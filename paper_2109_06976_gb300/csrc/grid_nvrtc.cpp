@@ -129,6 +129,7 @@ std::string kernel_source(const ModelDev<S>& D, int T, int CPL, int MAXD) {
 struct grid_gen_cache {
   std::mutex mu;
   struct Entry {
+    const void* topo;          // the host model whose topology was compiled (the robot, or one of its parts)
     int ssize, T, CPL, MAXD;
     CUmodule mod;
     CUfunction fn;
@@ -159,7 +160,8 @@ grid_status grid_gen_launch(grid_model* m, const ModelDev<S>* hm, const ModelDev
   {
     std::lock_guard<std::mutex> lk(C.mu);
     for (auto& x : C.entries)
-      if (x.ssize == (int)sizeof(S) && x.T == T && x.CPL == CPL && x.MAXD == MAXD) e = &x;
+      if (x.topo == (const void*)hm && x.ssize == (int)sizeof(S) && x.T == T && x.CPL == CPL && x.MAXD == MAXD)
+        e = &x;
     if (!e) {
       const std::string src = kernel_source<S>(*hm, T, CPL, MAXD);
       nvrtcProgram prog;
@@ -186,7 +188,7 @@ grid_status grid_gen_launch(grid_model* m, const ModelDev<S>* hm, const ModelDev
       std::vector<char> cubin(cs);
       A.getCUBIN(prog, cubin.data());
       A.destroyProgram(&prog);
-      grid_gen_cache::Entry x{(int)sizeof(S), T, CPL, MAXD, nullptr, nullptr, 0, 0};
+      grid_gen_cache::Entry x{(const void*)hm, (int)sizeof(S), T, CPL, MAXD, nullptr, nullptr, 0, 0};
       if (A.moduleLoadData(&x.mod, cubin.data()) != CUDA_SUCCESS ||
           A.moduleGetFunction(&x.fn, x.mod, "grid_gen_kernel") != CUDA_SUCCESS ||
           A.funcSetAttribute(x.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, smem_optin) != CUDA_SUCCESS) {

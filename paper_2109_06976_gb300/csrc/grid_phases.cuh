@@ -846,7 +846,9 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
 
 // ---------------------------------------------------------------- D
 // J = -M^-1 dc, restricted to base-branch blocks, written in caller order.
-template <class S, int T, int CPL, class Tp>
+// With PL (a part placed in a robot's arrays) rows and columns go to the
+// robot's joints gidx[i], in rows of rs = 2 ld with the d/dqd block at cqd = ld.
+template <class S, int T, int CPL, class Tp, bool PL = false>
 __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J, int rs = 0, int cq = 0, int cqd = 0) {
   const ModelDev<S>& M = c.M;
   const Tp& tp = c.tp;
@@ -868,10 +870,10 @@ __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J, int rs = 0, i
     S dcr[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) dcr[m] = (m >= lo && m < hi) ? DC[m * n2 + col] : S(0);
-    const int ucol = (col < n ? cq : cqd) + tp.perm(j);
+    const int ucol = (col < n ? cq : cqd) + (PL ? M.gidx[j] : tp.perm(j));
     if (J) {
-      for (int i = 0; i < lo; ++i) J[tp.perm(i) * rs + ucol] = S(0);     // other base branches
-      for (int i = hi; i < n; ++i) J[tp.perm(i) * rs + ucol] = S(0);
+      for (int i = 0; i < lo; ++i) J[(PL ? M.gidx[i] : tp.perm(i)) * rs + ucol] = S(0);   // other base branches
+      for (int i = hi; i < n; ++i) J[(PL ? M.gidx[i] : tp.perm(i)) * rs + ucol] = S(0);
     }
 #pragma unroll (Tp::kUnroll)
     for (int i = lo; i < hi; ++i) {
@@ -885,7 +887,7 @@ __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J, int rs = 0, i
           acc += mm[0] * dcr[m] + mm[1] * dcr[m + 1] + mm[2] * dcr[m + 2] + mm[3] * dcr[m + 3];
         }
       }
-      if (J) J[tp.perm(i) * rs + ucol] = -acc;
+      if (J) J[(PL ? M.gidx[i] : tp.perm(i)) * rs + ucol] = -acc;
     }
   }
   SYNC();
@@ -1042,12 +1044,15 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
   S* W = Wwarp + g * L.stride;
   const Ctx<S, Tp> c{M, gM, tp, W, lane32 % T, lane32};
   const int nvalid = min(G, N - k0);
+  // A part placed in a robot's arrays (MODE_GRAD only) reads and writes the
+  // robot's joints of its own: knot point k's slot s is at k ld + gslot[s].
+  const bool placed = MODE == MODE_GRAD && M.ld != n;
   // stage inputs (coalesced across the warp)
   for (int e = lane32; e < G * n; e += 32) {
     const int kk = e / n, i = e % n;
     S* Wk = Wwarp + kk * L.stride;
     const bool ok = kk < nvalid;
-    const size_t gi = (size_t)k0 * n + e;
+    const size_t gi = placed ? (size_t)(k0 + kk) * M.ld + M.gslot[i] : (size_t)k0 * n + e;
     Wk[L.Q + i] = ok ? q[gi] : S(0);
     if (MODE != MODE_MINV) Wk[L.QD + i] = ok ? qd[gi] : S(0);
     if (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) Wk[L.TAU + i] = (ok && x3) ? x3[gi] : S(0);
@@ -1087,6 +1092,17 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
             if (u < 0 || u >= n) Jb[e] = S(0);
           }
         }
+      } else if (placed) {
+        // the part's rows of the robot's J: its blocks, zeros in the other columns
+        const int ld = M.ld;
+        S* Jk = g < nvalid ? out + (size_t)(k0 + g) * 2 * ld * ld : nullptr;
+        ph_product<S, T, CPL, Tp, true>(c, Jk, 2 * ld, 0, ld);
+        if (Jk) {
+          for (int e = c.l; e < n * 2 * ld; e += T) {
+            const int i = e / (2 * ld), cc = e % (2 * ld), jj = cc < ld ? cc : cc - ld;
+            if (!((M.gmask >> jj) & 1u)) Jk[M.gidx[i] * 2 * ld + cc] = S(0);
+          }
+        }
       } else {
         ph_product<S, T, CPL>(c, g < nvalid ? out + (size_t)(k0 + g) * 2 * n * n : nullptr);
       }
@@ -1102,7 +1118,7 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
       SYNC();
       for (int e = lane32; e < nvalid * n; e += 32) {
         const int kk = e / n, r = e % n;
-        out2[(size_t)k0 * n + e] = Wwarp[kk * L.stride + L.CB + r];
+        out2[placed ? (size_t)(k0 + kk) * M.ld + M.gslot[r] : (size_t)k0 * n + e] = Wwarp[kk * L.stride + L.CB + r];
       }
     }
     if (out3 && g < nvalid) {                       // M^-1 in caller order (full symmetric)
@@ -1113,6 +1129,17 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
         for (int e = c.l; e < n * nr; e += T) {
           const int i = e / nr, u = e % nr - b * n;
           Mo[e] = (u >= 0 && u < n) ? W[L.MINV + i * L.MS + u] : S(0);
+        }
+      } else if (placed) {                          // the part's block of the robot's M^-1, zeros beside it
+        const int ld = M.ld;
+        S* Mo = out3 + (size_t)(k0 + g) * ld * ld;
+        for (int e = c.l; e < n * n; e += T) {
+          const int i = e / n, j = e % n;
+          Mo[M.gidx[i] * ld + M.gidx[j]] = W[L.MINV + i * L.MS + j];
+        }
+        for (int e = c.l; e < n * ld; e += T) {
+          const int i = e / ld, cc = e % ld;
+          if (!((M.gmask >> cc) & 1u)) Mo[M.gidx[i] * ld + cc] = S(0);
         }
       } else {
         S* Mo = out3 + (size_t)(k0 + g) * n * n;
