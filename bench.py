@@ -54,10 +54,15 @@ NCU_BYTES_PER_KNOT = {}
 NCU_FMA_PIPE = {}
 
 
+# The device code of the 7-DoF chain kernel (the key of the ncu tables above).
+KERNEL_FILES = ("grid_internal.h", "grid_phases.cuh", "spatial.cuh", "grid_kernel.cuh", "grid_launch.cuh",
+                "grid_chain.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2109_06976_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_FILES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

@@ -148,13 +148,12 @@ struct ModelDev {
   int et_ident[GRID_MAX_DOF];
   int jt[GRID_MAX_DOF];          // GRID_JOINT_REVOLUTE or GRID_JOINT_PRISMATIC
   // Placement in the caller's arrays. A whole robot has ld = n, gslot and gidx
-  // the identity and perm. A part (one base component of a robot, run as a
-  // problem of its own) has ld = the robot's joints per knot point: its caller
-  // slot s is the robot's joint gslot[s], its internal body k the robot's joint
-  // gidx[k] = gslot[perm[k]], and gmask has a bit for each of its joints.
+  // (below, read from device memory) the identity and perm. A part (one base
+  // component of a robot, run as a problem of its own) has ld = the robot's
+  // joints per knot point: its caller slot s is the robot's joint gslot[s], its
+  // internal body k the robot's joint gidx[k] = gslot[perm[k]], and gmask has a
+  // bit for each of its joints.
   int ld;
-  int gslot[GRID_MAX_DOF];
-  int gidx[GRID_MAX_DOF];
   unsigned gmask;
   alignas(16) S axis[GRID_MAX_DOF][4];   // unit axis, padded
   S ET[GRID_MAX_DOF][9];
@@ -163,6 +162,8 @@ struct ModelDev {
   alignas(16) S a0[8];                   // base acceleration -g, padded
   // -- not staged into shared memory:
   alignas(16) S Icol[GRID_MAX_DOF][6][8];// columns of the 6x6 spatial inertia, padded
+  int gslot[GRID_MAX_DOF];       // placement tables of a part (see ld)
+  int gidx[GRID_MAX_DOF];
   uint32_t sched[GRID_SCHED_MAX];
 };
 

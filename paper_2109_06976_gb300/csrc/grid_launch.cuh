@@ -77,8 +77,10 @@ grid_status launch_t(const grid_model* m, const ModelDev<S>* hm, const ModelDev<
   }();
   if constexpr (CHAIN_N > 0) {
     // the compile-time layout must be the one the host built for this model
-    if (hm->n != CHAIN_N || ChainTopo<S, MODE, CHAIN_N>::layout().stride != layout_of<MODE>(*hm).stride) {
-      grid_set_error("chain kernel for %d bodies does not match the model", CHAIN_N);
+    constexpr int NB = CHAIN_N % 100;
+    if (hm->n != NB || ChainTopo<S, MODE, NB>::layout().stride != layout_of<MODE>(*hm).stride ||
+        (CHAIN_N > 100) != (hm->ld != hm->n)) {
+      grid_set_error("chain kernel for %d bodies does not match the model", NB);
       return GRID_E_TOPOLOGY;
     }
   } else if constexpr (CHAIN_N < 0) {
@@ -158,6 +160,11 @@ constexpr int kChainMaxN = 8;
 template <class S, int MODE>
 grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                          const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
+// The same for a chain that is a part placed in a robot's arrays (grid_chain_part.cu).
+template <class S, int MODE>
+grid_status launch_chain_part(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N,
+                              const S* q, const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3,
+                              cudaStream_t st);
 // Kernels compiled at run time for the model's topology (grid_nvrtc.cpp).
 template <class S>
 grid_status grid_gen_launch(grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
@@ -177,11 +184,13 @@ grid_status dispatch_model(const grid_model* m, const ModelDev<S>* hm, const Mod
                            const S* q, const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3,
                            cudaStream_t st) {
   const int n = hm->n;
-  // Default lanes: 8 up to 12 bodies, else 16 (throughput). A batch smaller
+  // Default lanes: 8 up to 12 bodies, 16 up to 16, else 32 (throughput; above
+  // 16 bodies one warp per knot point halves the workspace per warp, measured on
+  // the 30-DoF tree and its 20-body torso-and-arms component). A batch smaller
   // than two knot points per SM is latency-bound: for more bodies than 8 lanes,
   // one warp per knot point then shortens the parallel phases (measured for the
   // 12- and 30-DoF trees; up to 8 bodies, 8 lanes stay faster).
-  if (T == 0) T = (n > 8 && N <= 2 * dev_info(m->device).nsm) ? 32 : (n <= 12 ? 8 : 16);
+  if (T == 0) T = (n > 8 && N <= 2 * dev_info(m->device).nsm) ? 32 : (n <= 12 ? 8 : (n <= 16 ? 16 : 32));
   const int cpl = (n + T - 1) / T;
   if constexpr (MODE == MODE_GRAD && !MIXED) {
     if (m->specialize_opt == 2 && (T == 8 || T == 16 || T == 32)) {
@@ -237,7 +246,7 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
         else { ph = P.host_d; pd = P.dev_d; }
         grid_status r;
         if (!MIXED && P.chain && P.n >= 2 && P.n <= kChainMaxN)
-          r = launch_chain<S, MODE>(m, ph, pd, N, q, qd, x3, x4, out, out2, out3, st);
+          r = launch_chain_part<S, MODE>(m, ph, pd, N, q, qd, x3, x4, out, out2, out3, st);
         else
           r = dispatch_model<S, MODE, MIXED>(m, ph, pd, 0, N, q, qd, x3, x4, out, out2, out3, st);
         if (r != GRID_OK) return r;

@@ -97,6 +97,7 @@ std::string kernel_source(const ModelDev<S>& D, int T, int CPL, int MAXD) {
        "  static constexpr int kUnroll = " + N + ";\n"
        "  static constexpr int kChainN = 0;\n"
        "  static constexpr bool kConsecutivePaths = false;\n"
+       "  static constexpr int kPlace = 2;\n"
        "  static constexpr int kBranches = 0;\n"
        "  __device__ explicit GenTopo(const ModelDev<S>&) {}\n"
        "  GRID_HD static constexpr KnotLayout layout() { return make_layout(" + N + ", " + std::to_string(D.nsk) +

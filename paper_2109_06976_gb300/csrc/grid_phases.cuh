@@ -25,8 +25,11 @@
 // offsets and the workspace layout follow from N at compile time, so loops
 // over bodies unroll and their indices fold (per-body constants such as axes
 // and inertias stay in the staged model).
+// kPlace: whether the model may be a part placed in a robot's arrays
+// (ModelDev::ld): 0 never, 1 always, 2 read from the model at run time.
 template <class S, int MODE>
 struct RtTopo {
+  static constexpr int kPlace = 2;
   static constexpr int kUnroll = 1;
   static constexpr int kChainN = 0;       // not a compile-time chain
   static constexpr bool kConsecutivePaths = false;
@@ -48,8 +51,9 @@ struct RtTopo {
   __device__ bool prism(int i) const { return M.jt[i] != 0; }
 };
 
-template <class S, int MODE, int N>
+template <class S, int MODE, int N, bool PL = false>
 struct ChainTopo {
+  static constexpr int kPlace = PL ? 1 : 0;
   static constexpr int kUnroll = N;
   static constexpr int kChainN = N;
   static constexpr bool kConsecutivePaths = true;   // ancestor at depth d of k: k - depth(k) + d
@@ -90,6 +94,7 @@ struct BranchTopo : ChainTopo<S, MODE, L> {
 // their general paths; only the topology folds.
 template <class S, int MODE, int K, int L>
 struct ForestTopo {
+  static constexpr int kPlace = 0;
   static constexpr int kUnroll = K * L;
   static constexpr int kChainN = 0;
   static constexpr bool kConsecutivePaths = true;
@@ -870,10 +875,10 @@ __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J, int rs = 0, i
     S dcr[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) dcr[m] = (m >= lo && m < hi) ? DC[m * n2 + col] : S(0);
-    const int ucol = (col < n ? cq : cqd) + (PL ? M.gidx[j] : tp.perm(j));
+    const int ucol = (col < n ? cq : cqd) + (PL ? c.gM->gidx[j] : tp.perm(j));
     if (J) {
-      for (int i = 0; i < lo; ++i) J[(PL ? M.gidx[i] : tp.perm(i)) * rs + ucol] = S(0);   // other base branches
-      for (int i = hi; i < n; ++i) J[(PL ? M.gidx[i] : tp.perm(i)) * rs + ucol] = S(0);
+      for (int i = 0; i < lo; ++i) J[(PL ? c.gM->gidx[i] : tp.perm(i)) * rs + ucol] = S(0);   // other base branches
+      for (int i = hi; i < n; ++i) J[(PL ? c.gM->gidx[i] : tp.perm(i)) * rs + ucol] = S(0);
     }
 #pragma unroll (Tp::kUnroll)
     for (int i = lo; i < hi; ++i) {
@@ -887,7 +892,7 @@ __device__ void ph_product(const Ctx<S, Tp>& c, S* __restrict__ J, int rs = 0, i
           acc += mm[0] * dcr[m] + mm[1] * dcr[m + 1] + mm[2] * dcr[m + 2] + mm[3] * dcr[m + 3];
         }
       }
-      if (J) J[(PL ? M.gidx[i] : tp.perm(i)) * rs + ucol] = -acc;
+      if (J) J[(PL ? c.gM->gidx[i] : tp.perm(i)) * rs + ucol] = -acc;
     }
   }
   SYNC();
@@ -1021,11 +1026,14 @@ __device__ void ph_vjp_sweep(const Ctx<S, Tp>& c) {
 
 // One warp processes knot points k0 .. k0 + 32/T - 1 (those < N). M is the
 // shared-memory copy of the model, gM the same model in device memory.
-// CHAIN_N: 0 run-time topology, N > 0 a chain of N bodies, -(100 K + L) a forest of K chains of L
+// CHAIN_N: 0 run-time topology, 0 < N < 100 a chain of N bodies, 100 + N a chain of
+// N bodies that is a part placed in a robot's arrays, -(100 K + L) a forest of K
+// chains of L
 template <class S, int MODE, int CHAIN_N>
 using topo_for = typename grid_cond<
     CHAIN_N == 0, RtTopo<S, MODE>,
-    typename grid_cond<(CHAIN_N > 0), ChainTopo<S, MODE, (CHAIN_N > 0 ? CHAIN_N : 1)>,
+    typename grid_cond<(CHAIN_N > 0),
+                       ChainTopo<S, MODE, (CHAIN_N > 0 ? CHAIN_N % 100 : 1), (CHAIN_N > 100)>,
                        ForestTopo<S, MODE, (CHAIN_N < 0 ? -CHAIN_N / 100 : 1),
                                   (CHAIN_N < 0 ? -CHAIN_N % 100 : 1)>>::type>::type;
 
@@ -1046,18 +1054,30 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
   const int nvalid = min(G, N - k0);
   // A part placed in a robot's arrays (MODE_GRAD only) reads and writes the
   // robot's joints of its own: knot point k's slot s is at k ld + gslot[s].
-  const bool placed = MODE == MODE_GRAD && M.ld != n;
-  // stage inputs (coalesced across the warp)
-  for (int e = lane32; e < G * n; e += 32) {
-    const int kk = e / n, i = e % n;
-    S* Wk = Wwarp + kk * L.stride;
-    const bool ok = kk < nvalid;
-    const size_t gi = placed ? (size_t)(k0 + kk) * M.ld + M.gslot[i] : (size_t)k0 * n + e;
-    Wk[L.Q + i] = ok ? q[gi] : S(0);
-    if (MODE != MODE_MINV) Wk[L.QD + i] = ok ? qd[gi] : S(0);
-    if (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) Wk[L.TAU + i] = (ok && x3) ? x3[gi] : S(0);
-    if (MODE == MODE_FD || MODE == MODE_GRAD || MODE == MODE_VJP) Wk[L.TAU + i] = ok ? x3[gi] : S(0);
-    if (MODE == MODE_VJP) Wk[L.UNION + L.GB + i] = ok ? x4[gi] : S(0);
+  const bool placed = MODE == MODE_GRAD && (Tp::kPlace == 2 ? M.ld != n : Tp::kPlace == 1);
+  if (placed) {
+    for (int e = lane32; e < G * n; e += 32) {
+      const int kk = e / n, i = e % n;
+      S* Wk = Wwarp + kk * L.stride;
+      const bool ok = kk < nvalid;
+      const size_t gi = (size_t)(k0 + kk) * M.ld + gM->gslot[i];
+      Wk[L.Q + i] = ok ? q[gi] : S(0);
+      Wk[L.QD + i] = ok ? qd[gi] : S(0);
+      Wk[L.TAU + i] = ok ? x3[gi] : S(0);
+    }
+  } else {
+    // stage inputs (coalesced across the warp)
+    for (int e = lane32; e < G * n; e += 32) {
+      const int kk = e / n, i = e % n;
+      S* Wk = Wwarp + kk * L.stride;
+      const bool ok = kk < nvalid;
+      const size_t gi = (size_t)k0 * n + e;
+      Wk[L.Q + i] = ok ? q[gi] : S(0);
+      if (MODE != MODE_MINV) Wk[L.QD + i] = ok ? qd[gi] : S(0);
+      if (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) Wk[L.TAU + i] = (ok && x3) ? x3[gi] : S(0);
+      if (MODE == MODE_FD || MODE == MODE_GRAD || MODE == MODE_VJP) Wk[L.TAU + i] = ok ? x3[gi] : S(0);
+      if (MODE == MODE_VJP) Wk[L.UNION + L.GB + i] = ok ? x4[gi] : S(0);
+    }
   }
   SYNC();
   ph_transforms<S, T>(c);
@@ -1100,7 +1120,7 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
         if (Jk) {
           for (int e = c.l; e < n * 2 * ld; e += T) {
             const int i = e / (2 * ld), cc = e % (2 * ld), jj = cc < ld ? cc : cc - ld;
-            if (!((M.gmask >> jj) & 1u)) Jk[M.gidx[i] * 2 * ld + cc] = S(0);
+            if (!((M.gmask >> jj) & 1u)) Jk[gM->gidx[i] * 2 * ld + cc] = S(0);
           }
         }
       } else {
@@ -1116,9 +1136,16 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
     if (out2) {                                     // qdd in caller order
       for (int i = c.l; i < n; i += T) W[L.CB + tp.perm(i)] = W[L.QDD + i];
       SYNC();
-      for (int e = lane32; e < nvalid * n; e += 32) {
-        const int kk = e / n, r = e % n;
-        out2[placed ? (size_t)(k0 + kk) * M.ld + M.gslot[r] : (size_t)k0 * n + e] = Wwarp[kk * L.stride + L.CB + r];
+      if (placed) {
+        for (int e = lane32; e < nvalid * n; e += 32) {
+          const int kk = e / n, r = e % n;
+          out2[(size_t)(k0 + kk) * M.ld + gM->gslot[r]] = Wwarp[kk * L.stride + L.CB + r];
+        }
+      } else {
+        for (int e = lane32; e < nvalid * n; e += 32) {
+          const int kk = e / n, r = e % n;
+          out2[(size_t)k0 * n + e] = Wwarp[kk * L.stride + L.CB + r];
+        }
       }
     }
     if (out3 && g < nvalid) {                       // M^-1 in caller order (full symmetric)
@@ -1135,11 +1162,11 @@ __device__ void process_tile_t(const ModelDev<S>& M, const ModelDev<S>* gM, cons
         S* Mo = out3 + (size_t)(k0 + g) * ld * ld;
         for (int e = c.l; e < n * n; e += T) {
           const int i = e / n, j = e % n;
-          Mo[M.gidx[i] * ld + M.gidx[j]] = W[L.MINV + i * L.MS + j];
+          Mo[gM->gidx[i] * ld + gM->gidx[j]] = W[L.MINV + i * L.MS + j];
         }
         for (int e = c.l; e < n * ld; e += T) {
           const int i = e / ld, cc = e % ld;
-          if (!((M.gmask >> cc) & 1u)) Mo[M.gidx[i] * ld + cc] = S(0);
+          if (!((M.gmask >> cc) & 1u)) Mo[gM->gidx[i] * ld + cc] = S(0);
         }
       } else {
         S* Mo = out3 + (size_t)(k0 + g) * n * n;

@@ -360,3 +360,5 @@ def test_precision_report_workload(grid, key, prec, capsys):
     with capsys.disabled():
         print("\n" + line)
     assert e4.max() <= TOL32, line
+    # with the survey's floor, every column meets the derived per-column bound
+    assert (e6 / bar).max() <= 1.0, line
