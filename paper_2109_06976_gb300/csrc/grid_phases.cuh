@@ -296,7 +296,11 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
   P* DINV = reinterpret_cast<P*>(W + U + L.DINV);
   S* BIA = W + U + L.BIA;
   S* BP = W + U + L.BP;
-  for (int e = l; e < n * MS; e += T) MI[e] = S(0);
+  if constexpr (Tp::kChainN > 0) {              // every entry is written; the padding is read as zero
+    for (int e = l; e < n * (MS - n); e += T) MI[(e / (MS - n)) * MS + n + e % (MS - n)] = S(0);
+  } else {
+    for (int e = l; e < n * MS; e += T) MI[e] = S(0);
+  }
   for (int e = l; e < 36 * tp.nbranch(); e += T) BIA[e] = S(0);
   SYNC();
   S carry[6], fb[CPL][6];
@@ -366,7 +370,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
         for (int e = 0; e < 6; ++e) fb[cc][e] = act ? fn[e] : fb[cc][e];
       }
     }
-    S* CT = W + U + L.CT + 48 * (i & 1);     // alternate buffers: no second barrier needed
+    S* CT = W + U + L.CT;                    // one buffer: a barrier before it is written again
     if (p >= 0) {
       S acol[6], cx[6];
       const P ulD = P(ul) * Dinv;
@@ -391,6 +395,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
         for (int e = 0; e < 6; ++e) slot[e] += it[e];
       }
     }
+    SYNC();                                   // every lane has read CT before the next body writes it
   }
   SYNC();
   // forward pass (with the subspace-table step of the same body, for ILP)
@@ -432,6 +437,7 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
           mk = S(P(mk) - Dinv * ut);
           MI[i * MS + l] = mk;
         }
+        if (l > i) MI[l * MS + i] = mk;        // the mirrored entry
 #pragma unroll
         for (int e = 0; e < 6; ++e) pc[0][e] = (e < 3 ? a[e] * mk : S(0)) + (i > 0 ? t[e] : S(0));
       }
@@ -500,9 +506,11 @@ __device__ void ph_minv(const Ctx<S, Tp>& c) {
     if (WITH_SK) subspace_step<S, T>(c, i, E, skc);
   }
   }
-  // mirror the columns this lane owns into the lower triangle
+  // mirror the columns this lane owns into the lower triangle (the chain's
+  // forward pass has written them already)
+  constexpr bool kMirrored = Tp::kChainN > 0 && Tp::kChainN < T && CPL == 1 && WITH_SK;
 #pragma unroll
-  for (int cc = 0; cc < CPL; ++cc) {
+  for (int cc = 0; cc < (kMirrored ? 0 : CPL); ++cc) {
     const int k = l + cc * T;
     if (k < n)
       for (int i = tp.comp_lo(k); i < k; ++i) MI[k * MS + i] = MI[i * MS + k];
@@ -566,6 +574,28 @@ __device__ void ph_joint_forces(const Ctx<S, Tp>& c, int f_off, int out_off) {
   const Tp& tp = c.tp;
   S* W = c.W;
   const KnotLayout L = c.tp.layout();   // by value: offsets stay in registers
+  if constexpr (Tp::kChainN > 0) {
+    // Chain: the backward sweep F_k = f_k + X_{k+1}^T F_{k+1}, c_k = S_k^T F_k, in
+    // every lane (broadcast reads of f and X; lane k stores c_k).
+    S F[6] = {S(0), S(0), S(0), S(0), S(0), S(0)};
+#pragma unroll
+    for (int k = Tp::kChainN - 1; k >= 0; --k) {
+      S f[6];
+      ld6(W + f_off + 8 * k, f);
+      if (k + 1 < Tp::kChainN) {
+        S E[12], x[6];
+        ld12(W + L.X + 12 * (k + 1), E);
+        xt_mul(E, E + 9, F, x);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) f[e] += x[e];
+      }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) F[e] = f[e];
+      if (c.l == k) W[out_off + k] = dot_s(M.axis[k], false, F);
+    }
+    SYNC();
+    return;
+  }
   for (int i = c.l; i < tp.n(); i += T) {
     const int di = tp.depth(i);
     S acc = S(0);
@@ -808,10 +838,11 @@ __device__ void ph_columns(const Ctx<S, Tp>& c, const uint32_t* __restrict__ sch
       static_assert(Tp::kChainN <= MAXD, "accumulators");
 #pragma unroll
       for (int d = 0; d < Tp::kChainN; ++d) {
-        S sr[6];
-        ld6(rows + 8 * d, sr);
-        const S t = dot6(sr, df);
-        acc[d] += d <= dk ? t : S(0);
+        if (d <= dk) {                         // lanes past their depth load nothing
+          S sr[6];
+          ld6(rows + 8 * d, sr);
+          acc[d] += dot6(sr, df);
+        }
       }
       if (st & STEP_FLUSH) {                  // the path ends at body n - 1: all depths
 #pragma unroll
