@@ -44,14 +44,19 @@ FLOPS_PER_KNOT = {"chain7": 26845, "tree12": 21516, "tree30": 132124}
 # roofline divides by the rate the FMA loop measures in the same run.
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # DRAM bytes per knot point of the 7-DoF gradient kernel from one ncu capture of the
-# same kernel sources (key: bench.py's hash of csrc/), dram__bytes_read.sum +
+# same kernel sources (key: kernel_source_hash), dram__bytes_read.sum +
 # dram__bytes_write.sum of a 524,288-knot-point launch divided by its knot points,
 # and lts__t_sectors_srcunit_tex_op_write.sum x 32 B (the writes the SMs send to L2,
-# including those still in L2 when the kernel ends). Absent when the kernel changed.
-NCU_BYTES_PER_KNOT = {}
+# partial sectors included, whether or not they reach DRAM before the kernel ends).
+# Absent when the kernel changed since the capture.
+NCU_BYTES_PER_KNOT = {"6444a67c2e1a0b3b": (44.114176e6 + 145.084672e6) / 524288}
+NCU_L2_WRITE_BYTES_PER_KNOT = {"6444a67c2e1a0b3b": 11927552 * 32 / 524288}
 # FP32 (FMA) pipe utilisation from the same captures (sm__pipe_fma_cycles_active, % of
-# peak sustained while active), reported beside the counted-flop fraction.
-NCU_FMA_PIPE = {}
+# peak sustained while active), reported beside the counted-flop fraction, and the
+# busy share of the shared-memory data pipe (l1tex__data_pipe_lsu_wavefronts,
+# % of peak sustained elapsed), the unit that bounds the kernel.
+NCU_FMA_PIPE = {"6444a67c2e1a0b3b": 0.447}
+NCU_SMEM_PIPE = {"6444a67c2e1a0b3b": 0.879}
 
 
 # The device code of the 7-DoF chain kernel (the key of the ncu tables above).
@@ -532,7 +537,9 @@ def run_ours(args):
     achieved_tflops = flops_knot * Nk / (ms / 1e3) / 1e12
     src = kernel_source_hash()
     traffic = NCU_BYTES_PER_KNOT.get(src)
+    l2w = NCU_L2_WRITE_BYTES_PER_KNOT.get(src)
     fma_pipe = NCU_FMA_PIPE.get(src)
+    smem_pipe = NCU_SMEM_PIPE.get(src)
     if args.only_main:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms,
@@ -659,9 +666,12 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peaks["fp32"],
                          "unit": "TFLOP/s", "frac": achieved_tflops / peaks["fp32"],
                          "traffic": None if traffic is None else traffic * Nk,
-                         "traffic_note": "ncu capture of the same kernel sources (DRAM read + write and "
-                                         "SM-to-L2 writes), scaled by knot points" if traffic else
-                                         "no capture of the current kernel sources",
+                         "traffic_note": "ncu capture of the same kernel sources on 524,288 knot points "
+                                         "(DRAM read + write), scaled by knot points; below the algorithmic "
+                                         f"{in_bytes + out_bytes:.0f} B because part of J is still in L2 at "
+                                         "kernel end" if traffic else "no capture of the current kernel sources",
+                         "l2_write_bytes": None if l2w is None else l2w * Nk,
+                         "smem_pipe_util_ncu": smem_pipe,
                          "flops_per_knot": flops_knot,
                          "flops_source": "operation count of the method in compact form (oracle/opcount.py)",
                          "fp32_pipe_util_ncu": fma_pipe,
