@@ -246,7 +246,7 @@ def time_steps(fn, steps, warmup, stream, dist=None, window=None):
     return max_over_ranks(e0.elapsed_time(e1) / 1e3, dist)
 
 
-def batched_leg(grid, name, precision, knots, steps, peaks, stream, dist, seed=31):
+def batched_leg(grid, name, precision, knots, steps, peaks, stream, dist, seed=31, specialize=1):
     """The gradient of FD over `knots` knot points of one workload robot in one
     launch per step (trajectories of 128 knot points), in FP32, mixed (FP32 with
     FP64 pivots) or FP64-plain; throughput and the fraction of the measured FP32
@@ -254,6 +254,7 @@ def batched_leg(grid, name, precision, knots, steps, peaks, stream, dist, seed=3
     import torch
     r = gi.robot(name)
     m = grid.Model.from_robot(r, precision="mixed" if precision == "mixed" else "fp32")
+    m.set_option("specialize", specialize)
     dt = torch.float64 if precision == "fp64" else torch.float32
     q, qd, tau = (torch.from_numpy(x).to("cuda", dt) for x in gi.states(r.n, knots, seed))
     J = torch.empty((knots, r.n, 2 * r.n), device="cuda", dtype=dt)
@@ -609,6 +610,10 @@ def run_ours(args):
             "tree12": {"fp32": batched_leg(grid, "tree12", "fp32", 4 * K, 10, peaks, stream, dist),
                        "fp64": batched_leg(grid, "tree12", "fp64", K // 2, 5, peaks, stream, dist)},
             "tree30": {"fp32": batched_leg(grid, "tree30", "fp32", K, 5, peaks, stream, dist),
+                       "fp32_run_time_compiled": batched_leg(grid, "tree30", "fp32", K, 5, peaks, stream, dist,
+                                                             specialize=2),
+                       "fp32_whole_robot": batched_leg(grid, "tree30", "fp32", K, 5, peaks, stream, dist,
+                                                       specialize=0),
                        "mixed": batched_leg(grid, "tree30", "mixed", K, 5, peaks, stream, dist),
                        "fp64": batched_leg(grid, "tree30", "fp64", K // 4, 3, peaks, stream, dist)},
         }
@@ -638,8 +643,8 @@ def run_ours(args):
     serve = None
     if rank == 0 and world == 1 and args.serve_seconds > 0:
         serve = serve_leg(grid, args.serve_seconds,
-                          rates=(20000.0,) + ((50000.0, 100000.0, 200000.0, 400000.0, 800000.0)
-                                              if args.serve_sweep else ()))
+                          rates=(20000.0,) + ((50000.0, 100000.0, 125000.0, 150000.0, 175000.0, 200000.0,
+                                               400000.0) if args.serve_sweep else ()))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -696,7 +701,10 @@ def run_ours(args):
             "robots": robots,
             "robots_note": "gradient of FD of each workload robot, one launch of 128-knot trajectories per "
                            "step: FP32, mixed (FP64 pivots in M^-1) and FP64-plain; frac = counted flops / "
-                           "the measured FP32 (FP64 for FP64-plain) multiply-add rate",
+                           "the measured FP32 (FP64 for FP64-plain) multiply-add rate. The 30-DoF tree runs "
+                           "its base components as parts (default), also with the parts compiled at run "
+                           "time for their topology (specialize 2; the first call compiles) and, for "
+                           "comparison, as one robot in the run-time-topology kernel (specialize 0)",
             "latency_n128_us": lat128,
             "latency_n128_with_io_us": lat128_io,
             "latency_n_sweep_us": sweep,

@@ -122,7 +122,64 @@ void build_branches(grid_model* m, const int* parent, const double* axis, const 
 // its legs) gets one model per component, placed in the robot's arrays
 // (ModelDev::ld, gslot, gidx, gmask): the components share nothing through the
 // fixed base, so each is a problem of its own. Any failure leaves nparts = 0.
+}  // namespace
+
+// Streams and events on which small batches run the parts of a robot at the same
+// time: the caller's stream forks into one stream per part and joins them again.
+// A lock serialises the fork-join sequences of calls on the same model.
+struct grid_part_exec {
+  std::mutex mu;
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+};
+
+grid_status grid_parts_fork(const grid_model* m, cudaStream_t caller, cudaStream_t* streams) {
+  grid_part_exec* x = m->pexec;
+  x->mu.lock();
+  cudaError_t e = cudaEventRecord(x->fork, caller);
+  for (int p = 0; e == cudaSuccess && p < m->nparts; ++p) {
+    e = cudaStreamWaitEvent(x->st[p], x->fork, 0);
+    streams[p] = x->st[p];
+  }
+  if (e != cudaSuccess) {
+    x->mu.unlock();
+    grid_set_error("parts: fork: %s", cudaGetErrorString(e));
+    return GRID_E_CUDA;
+  }
+  return GRID_OK;
+}
+
+grid_status grid_parts_join(const grid_model* m, cudaStream_t caller) {
+  grid_part_exec* x = m->pexec;
+  cudaError_t e = cudaSuccess;
+  for (int p = 0; p < m->nparts; ++p) {
+    cudaError_t e1 = cudaEventRecord(x->join[p], x->st[p]);
+    cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(caller, x->join[p], 0) : e1;
+    if (e == cudaSuccess) e = e2;
+  }
+  x->mu.unlock();
+  if (e != cudaSuccess) {
+    grid_set_error("parts: join: %s", cudaGetErrorString(e));
+    return GRID_E_CUDA;
+  }
+  return GRID_OK;
+}
+
+namespace {
+
+void free_part_exec(grid_model* m) {
+  grid_part_exec* x = m->pexec;
+  if (!x) return;
+  for (cudaStream_t s : x->st) if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  for (cudaEvent_t e : x->join) if (e) cudaEventDestroy(e);
+  if (x->fork) cudaEventDestroy(x->fork);
+  delete x;
+  m->pexec = nullptr;
+}
+
 void free_parts(grid_model* m) {
+  free_part_exec(m);
   for (int p = 0; p < m->nparts; ++p) {
     cudaFree(m->parts[p].dev_f);
     cudaFree(m->parts[p].dev_d);
@@ -199,6 +256,18 @@ void build_parts(grid_model* m, const int* parent, const int* jtype, const doubl
       free_parts(m);
       return;
     }
+  }
+  grid_part_exec* x = new grid_part_exec();
+  m->pexec = x;
+  x->st.assign(m->nparts, nullptr);
+  x->join.assign(m->nparts, nullptr);
+  bool ok = cudaEventCreateWithFlags(&x->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int p = 0; ok && p < m->nparts; ++p)
+    ok = cudaStreamCreateWithFlags(&x->st[p], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&x->join[p], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_parts(m);
   }
 }
 
@@ -427,6 +496,7 @@ grid_status grid_create_ex(int n, const int* parent, const int* jtype, const dou
   // Base components that the forest kernels do not cover run as parts.
   m->nparts = 0;
   m->parts = nullptr;
+  m->pexec = nullptr;
   if (m->host_d->ncomp >= 2 && !(m->forest_k > 1 && forest_compiled(m->forest_k, m->forest_l)) &&
       all_moving(n, jtype) && m->n == n)
     build_parts(m, parent, jtype, axis, X_tree, inertia, gravity);

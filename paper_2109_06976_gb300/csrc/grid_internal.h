@@ -200,8 +200,9 @@ struct grid_model {
   ModelDev<double>* br_dev_d;
   ModelDev<float>* br_host_f;
   ModelDev<double>* br_host_d;
-  int nparts;                    // > 0: the gradient of FD of large batches runs per base component
+  int nparts;                    // > 0: the gradient of FD runs per base component
   struct grid_part* parts;       // [nparts] (grid_capi.cu), else nullptr
+  struct grid_part_exec* pexec;  // streams and events that run the parts at once (grid_capi.cu)
   struct grid_gen_cache* gen;    // kernels compiled at run time for this model (grid_nvrtc.cpp)
   struct grid_host_pipe* pipe;   // staging and streams of grid_grad_fd_host (grid_capi.cu)
   int host_chunk_opt;            // knot points per chunk of grid_grad_fd_host (0 = automatic)

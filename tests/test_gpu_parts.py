@@ -1,8 +1,8 @@
 """Robots whose base components differ (the 30-DoF tree: torso with two arms,
-and two legs) run the gradient of FD per component for batches above two knot
-points per SM. Checked against the FP64 oracle, against the kernel that runs
-the whole robot, for every output entry (outputs pre-filled with NaN), and
-bit for bit against the same components built as robots of their own."""
+and two legs) run the gradient of FD per component, the parts at the same time
+on streams of their own. Checked against the FP64 oracle, against the kernel that runs the
+whole robot, for every output entry (outputs pre-filled with NaN), and bit for
+bit against the same components built as robots of their own."""
 import numpy as np
 import pytest
 
@@ -13,7 +13,8 @@ from tests.metrics import FLOOR32, FLOOR64, col_rel_err, col_rel_err_knots, fp32
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-N_PARTS = 401            # above two knot points per SM: the per-component launches
+N_PARTS = 401            # batch sizes above and below two knot points per SM
+N_SMALL = 37
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +60,8 @@ def _inputs(n, N, seed, dt):
 
 @pytest.mark.parametrize("name", list(ROBOTS))
 @pytest.mark.parametrize("prec", ["fp32", "mixed", "fp64"])
-def test_parts_match_oracle_and_whole_robot(grid, name, prec):
+@pytest.mark.parametrize("N", [N_PARTS, N_SMALL])
+def test_parts_match_oracle_and_whole_robot(grid, name, prec, N):
     r = ROBOTS[name]()
     roots = int(np.sum(r.parent < 0))
     assert roots >= 2, "the robot has several base components"
@@ -68,11 +70,11 @@ def test_parts_match_oracle_and_whole_robot(grid, name, prec):
     m = grid.Model.from_robot(r, precision="mixed" if prec == "mixed" else "fp32")
     whole = grid.Model.from_robot(r, precision="mixed" if prec == "mixed" else "fp32")
     whole.set_option("specialize", 0)
-    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N_PARTS, 4100 + n, dt)
-    J = torch.full((N_PARTS, n, 2 * n), float("nan"), device="cuda", dtype=dt)
-    Mi = torch.full((N_PARTS, n, n), float("nan"), device="cuda", dtype=dt)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 4100 + n, dt)
+    J = torch.full((N, n, 2 * n), float("nan"), device="cuda", dtype=dt)
+    Mi = torch.full((N, n, n), float("nan"), device="cuda", dtype=dt)
     m.grad_fd_minv(q, qd, tau, out=J, minv_out=Mi)
-    qdd = torch.full((N_PARTS, n), float("nan"), device="cuda", dtype=dt)
+    qdd = torch.full((N, n), float("nan"), device="cuda", dtype=dt)
     J2 = m.grad_fd(q, qd, tau, qdd_out=qdd)
     Jw, qddw = whole.grad_fd(q, qd, tau, return_qdd=True)
     torch.cuda.synchronize()
@@ -103,13 +105,14 @@ def test_parts_match_oracle_and_whole_robot(grid, name, prec):
 
 
 @pytest.mark.parametrize("dt", [torch.float32, torch.float64], ids=["f32", "f64"])
-def test_parts_are_the_components_run_alone(grid, dt):
+@pytest.mark.parametrize("N", [N_PARTS, 1])
+def test_parts_are_the_components_run_alone(grid, dt, N):
     """The 30-DoF tree's rows are, bit for bit, those of its torso-and-arms
     component and of each leg built as robots of their own (the same kernels on
     the same models), with exact zeros between components."""
     r = gi.tree30()
     m = grid.Model.from_robot(r)
-    (q, qd, tau), _ = _inputs(30, N_PARTS, 77, dt)
+    (q, qd, tau), _ = _inputs(30, N, 77, dt)
     J, qdd = m.grad_fd(q, qd, tau, return_qdd=True)
     J, qdd = J.cpu().numpy(), qdd.cpu().numpy()
     for idx in (range(0, 20), range(20, 25), range(25, 30)):
