@@ -72,3 +72,13 @@ def test_host_buffer_call_checks_arguments_without_gpu(lib):
     lib.grid_set_option.restype = ctypes.c_int
     lib.grid_set_option.argtypes = [P, ctypes.c_char_p, ctypes.c_int]
     assert lib.grid_set_option(None, b"host_chunk", 1024) == 1
+
+
+def test_peak_loop_rejects_bad_arguments_without_gpu(lib):
+    """grid_peak_loop checks its arguments on the host before any launch."""
+    lib.grid_peak_loop.restype = ctypes.c_int
+    lib.grid_peak_loop.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    fl = ctypes.c_double()
+    for kind, blocks, threads, iters in ((3, 1, 32, 1), (0, 0, 32, 1), (0, 1, 33, 1), (0, 1, 2048, 1), (0, 1, 32, 0)):
+        assert lib.grid_peak_loop(kind, blocks, threads, iters, ctypes.c_void_p(16), ctypes.byref(fl), None) == 1
