@@ -49,14 +49,14 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # and lts__t_sectors_srcunit_tex_op_write.sum x 32 B (the writes the SMs send to L2,
 # partial sectors included, whether or not they reach DRAM before the kernel ends).
 # Absent when the kernel changed since the capture.
-NCU_BYTES_PER_KNOT = {"6444a67c2e1a0b3b": (44.114176e6 + 145.084672e6) / 524288}
-NCU_L2_WRITE_BYTES_PER_KNOT = {"6444a67c2e1a0b3b": 11927552 * 32 / 524288}
+NCU_BYTES_PER_KNOT = {"5b7863982b2d765b": (44.114944e6 + 145.304832e6) / 524288}
+NCU_L2_WRITE_BYTES_PER_KNOT = {"5b7863982b2d765b": 11927552 * 32 / 524288}
 # FP32 (FMA) pipe utilisation from the same captures (sm__pipe_fma_cycles_active, % of
 # peak sustained while active), reported beside the counted-flop fraction, and the
 # busy share of the shared-memory data pipe (l1tex__data_pipe_lsu_wavefronts,
 # % of peak sustained elapsed), the unit that bounds the kernel.
-NCU_FMA_PIPE = {"6444a67c2e1a0b3b": 0.447}
-NCU_SMEM_PIPE = {"6444a67c2e1a0b3b": 0.879}
+NCU_FMA_PIPE = {"5b7863982b2d765b": 0.448}
+NCU_SMEM_PIPE = {"5b7863982b2d765b": 0.875}
 
 
 # The device code of the 7-DoF chain kernel (the key of the ncu tables above).
