@@ -525,8 +525,8 @@ grid_status grid_set_option(grid_model* m, const char* key, int value) {
   if (!m || !key) { grid_set_error("grid_set_option: null argument"); return GRID_E_ARG; }
   std::string k(key);
   if (k == "lanes") {
-    if (value != 0 && value != 8 && value != 16 && value != 32) {
-      grid_set_error("lanes must be 0, 8, 16 or 32"); return GRID_E_ARG;
+    if (value != 0 && value != 1 && value != 8 && value != 16 && value != 32) {
+      grid_set_error("lanes must be 0, 1, 8, 16 or 32"); return GRID_E_ARG;
     }
     m->lanes_opt = value;
   } else if (k == "precision") {

@@ -160,6 +160,14 @@ constexpr int kChainMaxN = 8;
 template <class S, int MODE>
 grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                          const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
+// Gradient of FD of a serial chain of 2 .. 8 revolute bodies with one lane per
+// knot point (grid_lane_chain.cu): the throughput form for large batches.
+grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int N, const float* q,
+                              const float* qd, const float* tau, float* J, float* qdd, float* Minv,
+                              cudaStream_t st);
+// Batches from this many knot points up take the one-lane-per-knot-point chain
+// kernel by default (below, the 8-lane kernel has the shorter latency).
+constexpr int kLaneChainMinN = 32768;
 // The same for a chain that is a part placed in a robot's arrays (grid_chain_part.cu).
 template <class S, int MODE>
 grid_status launch_chain_part(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N,
@@ -229,8 +237,15 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   const ModelDev<S>* dm;
   if constexpr (std::is_same<S, float>::value) { hm = m->host_f; dm = m->dev_f; }
   else { hm = m->host_d; dm = m->dev_d; }
-  const int T = m->lanes_opt;
+  // lanes 1: one lane per knot point where that kernel exists (the gradient of
+  // FD of FP32 serial chains), automatic elsewhere
+  const int T = m->lanes_opt == 1 ? 0 : m->lanes_opt;
   const int n = hm->n;
+  if constexpr (MODE == MODE_GRAD && !MIXED && std::is_same<S, float>::value) {
+    if (m->chain && m->specialize_opt && n >= 2 && n <= kChainMaxN &&
+        (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN)))
+      return launch_lane_chain(m, hm, N, q, qd, x3, out, out2, out3, st);
+  }
   if constexpr (MODE == MODE_GRAD && !MIXED) {
     if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
       return launch_chain<S, MODE>(m, hm, dm, N, q, qd, x3, x4, out, out2, out3, st);

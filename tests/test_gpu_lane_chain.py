@@ -1,0 +1,140 @@
+"""GPU parity of the one-lane-per-knot-point kernel for serial chains (the
+throughput form that large batches of chains of 2 .. 8 revolute bodies take by
+default): against the FP64 oracle and against the 8-lane chain kernel, on
+ragged batches that span several warps, with M^-1 and qdd written beside J."""
+import numpy as np
+import pytest
+
+import grid_inputs as gi
+import oracle
+from tests.metrics import FLOOR32, col_rel_err, col_rel_err_knots, fp32_bar, vec_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def grid():
+    import paper_2109_06976_gb300 as g
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return g
+
+
+def _inputs(n, N, seed):
+    q, qd, tau = (x.astype(np.float32) for x in gi.states(n, N, seed))
+    return [torch.from_numpy(x).cuda() for x in (q, qd, tau)], [x.astype(np.float64) for x in (q, qd, tau)]
+
+
+CHAINS = [(n, s, g) for n in range(2, 9) for s, g in ((1, True), (2, False))]
+
+
+@pytest.mark.parametrize("n,seed,general", CHAINS, ids=lambda x: str(x))
+@pytest.mark.parametrize("N", [1, 77, 1000])
+def test_lane_chain_matches_oracle(grid, n, seed, general, N):
+    """lanes = 1 forced on random chains (general axes and rotated fixed
+    transforms when `general`): J, qdd and M^-1 against the oracle, per knot
+    point within the FP32 bar (the larger of 1e-4 and n kappa(M) u)."""
+    r = gi.random_tree(n, seed, general=general, max_children=1)
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 31 + N)
+    J, qdd = m.grad_fd(q, qd, tau, return_qdd=True)
+    J2, Mi = m.grad_fd_minv(q, qd, tau)
+    J, qdd, J2, Mi = (x.cpu().numpy() for x in (J, qdd, J2, Mi))
+    ref = oracle.grad_fd(r, q64, qd64, tau64)
+    mref = oracle.minv(r, q64)
+    bar = fp32_bar(mref)
+    assert np.all(col_rel_err_knots(J, ref, floor=FLOOR32) <= bar)
+    assert vec_rel_err(qdd, oracle.fd(r, q64, qd64, tau64)) <= TOL32
+    np.testing.assert_array_equal(J, J2)                        # same kernel, same arithmetic
+    assert col_rel_err(Mi, mref, FLOOR32) <= TOL32
+    np.testing.assert_array_equal(Mi, np.swapaxes(Mi, 1, 2))    # exactly symmetric
+    m.close()
+
+
+@pytest.mark.parametrize("n", [2, 5, 7, 8])
+def test_lane_chain_agrees_with_8_lane_kernel(grid, n):
+    """The default dispatch (lanes 0) of a batch above the switch-over size takes
+    the one-lane kernel; it agrees with the 8-lane chain kernel on the same
+    knot points within the FP32 bar of both against the oracle, checked on
+    sampled knot points."""
+    r = gi.random_tree(n, 4, general=True, max_children=1)
+    one = grid.Model.from_robot(r)
+    eight = grid.Model.from_robot(r)
+    eight.set_option("lanes", 8)
+    N = 32768 + 4093                                   # above the switch-over, ragged last warp
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 5)
+    J1 = one.grad_fd(q, qd, tau).cpu().numpy()
+    J8 = eight.grad_fd(q, qd, tau).cpu().numpy()
+    idx = np.sort(gi.Stream(9).u64(200) % np.uint64(N)).astype(np.int64)
+    idx = np.unique(np.concatenate([idx, [0, N - 1]]))
+    ref = oracle.grad_fd(r, q64[idx], qd64[idx], tau64[idx])
+    bar = fp32_bar(oracle.minv(r, q64[idx]))
+    assert np.all(col_rel_err_knots(J1[idx], ref, floor=FLOOR32) <= bar)
+    assert np.all(col_rel_err_knots(J8[idx], ref, floor=FLOOR32) <= bar)
+    assert np.all(col_rel_err_knots(J1, J8, floor=FLOOR32) <= 2 * fp32_bar(oracle.minv(r, q64[:4096])).max())
+    one.close()
+    eight.close()
+
+
+def test_lane_chain_writes_every_entry(grid):
+    """Outputs pre-filled with NaN: J, M^-1 and qdd of every knot point of a
+    ragged batch are written, and nothing past the batch is touched."""
+    r = gi.chain7()
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)
+    N = 32 * 5 + 13
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(7, N, 3)
+    J = torch.full((N + 1, 7, 14), float("nan"), device="cuda")
+    Mi = torch.full((N + 1, 7, 7), float("nan"), device="cuda")
+    m.grad_fd_minv(q, qd, tau, out=J[:N], minv_out=Mi[:N])
+    qdd = torch.full((N + 1, 7), float("nan"), device="cuda")
+    m.grad_fd(q, qd, tau, qdd_out=qdd[:N])
+    Jh, Mh, qh = J.cpu().numpy(), Mi.cpu().numpy(), qdd.cpu().numpy()
+    assert np.isfinite(Jh[:N]).all() and np.isfinite(Mh[:N]).all() and np.isfinite(qh[:N]).all()
+    assert np.isnan(Jh[N]).all() and np.isnan(Mh[N]).all() and np.isnan(qh[N]).all()
+    assert col_rel_err(Jh[:N], oracle.grad_fd(r, q64, qd64, tau64), FLOOR32) <= TOL32
+    assert col_rel_err(Mh[:N], oracle.minv(r, q64), FLOOR32) <= TOL32
+    m.close()
+
+
+def test_lane_chain_workload_chain7_and_repeatable(grid):
+    """The 7-DoF workload chain through the default dispatch at the benchmark's
+    trajectory length (2048 trajectories x 128 knot points): sampled knot points
+    against the oracle, and two calls bit-identical."""
+    r = gi.chain7()
+    m = grid.Model.from_robot(r)
+    N = 2048 * 128
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(7, N, gi.workload_seed(2, 128))
+    J = m.grad_fd(q, qd, tau)
+    J2 = m.grad_fd(q, qd, tau)
+    torch.cuda.synchronize()
+    assert torch.equal(J, J2)
+    idx = np.sort(gi.Stream(11).u64(256) % np.uint64(N)).astype(np.int64)
+    ref = oracle.grad_fd(r, q64[idx], qd64[idx], tau64[idx], nthreads=8)
+    assert col_rel_err(J[torch.from_numpy(idx).cuda()].cpu().numpy(), ref, FLOOR32) <= TOL32
+    m.close()
+
+
+def test_lane_option_checks(grid):
+    """lanes = 1 applies to chains in FP32 only: FP64 and other robots keep
+    their kernels, and an unknown lane count is refused."""
+    r = gi.tree12()
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)                          # not a chain: the tree's own kernel
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(12, 40, 2)
+    J = m.grad_fd(q, qd, tau).cpu().numpy()
+    assert col_rel_err(J, oracle.grad_fd(r, q64, qd64, tau64), FLOOR32) <= TOL32
+    with pytest.raises(grid.GridError):
+        m.set_option("lanes", 2)
+    m.close()
+    c = grid.Model.from_robot(gi.chain7())
+    c.set_option("lanes", 1)
+    q, qd, tau = (torch.from_numpy(x).cuda() for x in gi.states(7, 50, 4))   # FP64: 8-lane FP64 kernel
+    J = c.grad_fd(q, qd, tau).cpu().numpy()
+    q64, qd64, tau64 = gi.states(7, 50, 4)
+    assert col_rel_err(J, oracle.grad_fd(gi.chain7(), q64, qd64, tau64)) <= 1e-10
+    c.close()
