@@ -39,6 +39,12 @@ struct LcParams {
   float inert[kLcMaxB][10];   // m, h = m c (3), Ibar about the body origin: xx yy zz xy xz yz
   float a0[6];                // base acceleration -g
   unsigned et_ident;          // bit i: the fixed rotation of body i is the identity
+  // Placement in the caller's arrays (a chain that is one component of a larger
+  // robot): joints per knot point, the caller joint of body i, and a bit for
+  // each caller joint of the chain. A whole robot has ld = n, slot[i] = i.
+  int ld;
+  int slot[kLcMaxB];
+  unsigned mask;
 };
 
 
@@ -123,18 +129,42 @@ __device__ __forceinline__ constexpr int lc_tri(int r, int c) {
 // body indices, shared-memory offsets and the robot's constants are immediate
 // operands; one code path serves both kinds of column, which differ only in
 // the case terms at the column's own joint.
-template <int NB>
+// A body's record as the column passes read it.
+struct LcBody {
+  float E[9], v[6], qd;
+};
+
+__device__ __forceinline__ void lc_load_body(const LcWs& w, int i, LcBody& b) {
+  const float4 x0 = w.f4(7 * i), x1 = w.f4(7 * i + 1), a = w.f4(7 * i + 2), c = w.f4(7 * i + 3);
+  b.E[0] = x0.x; b.E[1] = x0.y; b.E[2] = x0.z; b.E[3] = x0.w;
+  b.E[4] = x1.x; b.E[5] = x1.y; b.E[6] = x1.z; b.E[7] = x1.w; b.E[8] = c.z;
+  b.v[0] = a.x; b.v[1] = a.y; b.v[2] = a.z; b.v[3] = a.w; b.v[4] = c.x; b.v[5] = c.y;
+  b.qd = c.w;
+}
+
+// One derivative column (u, j), u = q when uq: the forward pass over bodies
+// j .. n-1, the backward pass down to the base (dc_i for every body), then
+// J[:, col] = -M^-1 dc. The loops run over the bodies at compile time (the
+// bodies before j are skipped by a branch that is uniform across the warp), so
+// body indices, shared-memory offsets and the robot's constants are immediate
+// operands; one code path serves both kinds of column, which differ only in
+// the case terms at the column's own joint. The next body's record is loaded
+// before the current body's arithmetic, so that the shared-memory latency
+// overlaps it.
+template <int NB, bool PL>
 __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int j, bool uq, const float* Mi,
                                           float* __restrict__ Jk) {
   float df[NB][6];
   float dv[6], da[6];
+  LcBody cur, nxt;
+  lc_load_body(w, j, cur);
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     if (i >= j) {
-      float v[6], qdi, e8;
-      lc_load_v(w, i, v, qdi, e8);
+      if (i + 1 < NB) lc_load_body(w, i + 1, nxt);
       const float* a = P.axis[i];
       const float* in = P.inert[i];
+      const float* v = cur.v;
       float g[6], ndv[6], nda[6], vxs[6];
       i_mul(in, v, g);                                 // gamma_i = I_i v_i
       cross_s(v, a, false, vxs);                       // v x S
@@ -149,14 +179,10 @@ __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int 
           nda[e] = uq ? beta[e] : vxs[e];
         }
       } else {
-        float E[9];
-        const float4 x0 = w.f4(7 * i), x1 = w.f4(7 * i + 1);
-        E[0] = x0.x; E[1] = x0.y; E[2] = x0.z; E[3] = x0.w; E[4] = x1.x; E[5] = x1.y; E[6] = x1.z; E[7] = x1.w;
-        E[8] = e8;
-        x_mul(E, P.rT[i], dv, ndv);
-        x_mul(E, P.rT[i], da, nda);
+        x_mul(cur.E, P.rT[i], dv, ndv);
+        x_mul(cur.E, P.rT[i], da, nda);
       }
-      const float sq[3] = {a[0] * qdi, a[1] * qdi, a[2] * qdi};
+      const float sq[3] = {a[0] * cur.qd, a[1] * cur.qd, a[2] * cur.qd};
       cross_s_acc(ndv, sq, false, nda);                // + dv x S qd
       float f[6], idv[6];
       i_mul(in, nda, f);
@@ -170,37 +196,43 @@ __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int 
       }
 #pragma unroll
       for (int e = 0; e < 6; ++e) { df[i][e] = f[e]; dv[e] = ndv[e]; da[e] = nda[e]; }
+      cur = nxt;
     }
   }
   // backward: dF_i = df_i + X_{i+1}^T dF_{i+1} (df_i = 0 above j's subtree),
   // dc_i = S_i^T dF_i
   float dF[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, dc[NB];
+  float Ec[9], En[9];
+  lc_load_E(w, NB - 1, Ec);
 #pragma unroll
   for (int i = NB - 1; i >= 0; --i) {
+    if (i > 1) lc_load_E(w, i - 1, En);
     if (i >= j) {
 #pragma unroll
       for (int e = 0; e < 6; ++e) dF[e] += df[i][e];
     }
     dc[i] = dot_s(P.axis[i], false, dF);
     if (i > 0) {
-      float E[9], t[6];
-      lc_load_E(w, i, E);
-      xt_mul(E, P.rT[i], dF, t);
+      float t[6];
+      xt_mul(Ec, P.rT[i], dF, t);
 #pragma unroll
       for (int e = 0; e < 6; ++e) dF[e] = t[e];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) Ec[e] = En[e];
     }
   }
-  const int col = uq ? j : NB + j;
+  const int ld = PL ? P.ld : NB;
+  const int col = (uq ? 0 : ld) + (PL ? P.slot[j] : j);
 #pragma unroll
   for (int rr = 0; rr < NB; ++rr) {
     float acc = 0.0f;
 #pragma unroll
     for (int m = 0; m < NB; ++m) acc += Mi[lc_tri<NB>(rr, m)] * dc[m];
-    if (Jk) Jk[rr * 2 * NB + col] = -acc;
+    if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = -acc;
   }
 }
 
-template <int NB>
+template <int NB, bool PL>
 __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k, const float* __restrict__ q,
                                         const float* __restrict__ qd, const float* __restrict__ tau,
                                         float* __restrict__ J, float* __restrict__ qdd_out,
@@ -210,7 +242,9 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
   //   U_i = I^A_i S_i, D_i = S_i^T U_i, Minv[i][i] = D_i^-1,
   //   Minv[i][k] = -D_i^-1 S_i^T F_k (k > i),  F_k <- X_i^T (F_k + U_i Minv[i][k]) (k >= i)
   // The sweeps are loops over bodies with the F and P columns indexed at
-  // compile time, which keeps the code small.
+  // compile time, which keeps the code small. A placed chain (PL) reads and
+  // writes the caller joints slot[i] of knot points of ld joints.
+  const int ld = PL ? P.ld : NB;
   {
     float Fc[NB][6], carry[6][6];
 #pragma unroll
@@ -224,8 +258,9 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
 #pragma unroll 1
     for (int i = NB - 1; i >= 0; --i) {
       float E[9];
-      lc_transform(P, i, __ldg(q + k * NB + i), E);
-      const float qdi = __ldg(qd + k * NB + i);
+      const long gi = k * ld + (PL ? P.slot[i] : i);
+      lc_transform(P, i, __ldg(q + gi), E);
+      const float qdi = __ldg(qd + gi);
       w.f4(7 * i) = make_float4(E[0], E[1], E[2], E[3]);
       w.f4(7 * i + 1) = make_float4(E[4], E[5], E[6], E[7]);
       const float* a = P.axis[i];
@@ -352,9 +387,15 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
   }
   if (minv_out) {
 #pragma unroll
-    for (int i = 0; i < NB; ++i)
+    for (int i = 0; i < NB; ++i) {
+      float* row = minv_out + (k * ld + (PL ? P.slot[i] : i)) * ld;
 #pragma unroll
-      for (int kk = 0; kk < NB; ++kk) minv_out[(k * NB + i) * NB + kk] = Mi[lc_tri<NB>(i, kk)];
+      for (int kk = 0; kk < NB; ++kk) row[PL ? P.slot[kk] : kk] = Mi[lc_tri<NB>(i, kk)];
+      if (PL) {                                        // zeros beside the chain's block
+        for (int cc = 0; cc < ld; ++cc)
+          if (!((P.mask >> cc) & 1u)) row[cc] = 0.0f;
+      }
+    }
   }
   // ---- a3: RNEA(q, qd, 0); X_i a_parent in B0 / B2.xy and f_i in B1 / B2.zw
   {
@@ -413,7 +454,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
   {
     float rhs[NB], qdd[NB];
 #pragma unroll
-    for (int i = 0; i < NB; ++i) rhs[i] = __ldg(tau + k * NB + i) - w.f1(i);
+    for (int i = 0; i < NB; ++i) rhs[i] = __ldg(tau + k * ld + (PL ? P.slot[i] : i)) - w.f1(i);
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       float acc = 0.0f;
@@ -425,7 +466,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
     for (int i = 0; i < NB; ++i) w.f1(i) = qdd[i];
     if (qdd_out) {
 #pragma unroll
-      for (int i = 0; i < NB; ++i) qdd_out[k * NB + i] = qdd[i];
+      for (int i = 0; i < NB; ++i) qdd_out[k * ld + (PL ? P.slot[i] : i)] = qdd[i];
     }
   }
   // ---- a6: RNEA at qdd: da_i = X_i da_{i-1} + S_i qdd_i, f_i += I_i da_i;
@@ -476,12 +517,20 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
     }
   }
   // ---- a7 - a9: derivative columns and J = -M^-1 dc
-  float* Jk = J + k * 2 * NB * NB;
+  float* Jk = J + k * 2 * ld * ld;
 #pragma unroll 1
-  for (int c = 0; c < 2 * NB; ++c) lc_column<NB>(P, w, c >> 1, (c & 1) == 0, Mi, Jk);
+  for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL>(P, w, c >> 1, (c & 1) == 0, Mi, Jk);
+  if (PL) {                                            // the chain's rows of J: zeros beside its blocks
+#pragma unroll 1
+    for (int rr = 0; rr < NB; ++rr) {
+      float* row = Jk + P.slot[rr] * 2 * ld;
+      for (int cc = 0; cc < 2 * ld; ++cc)
+        if (!((P.mask >> (cc < ld ? cc : cc - ld)) & 1u)) row[cc] = 0.0f;
+    }
+  }
 }
 
-template <int NB>
+template <int NB, bool PL>
 __global__ void __launch_bounds__(256, 1) grid_lane_chain_kernel(const __grid_constant__ LcParams P, int N,
                                                                  const float* __restrict__ q,
                                                                  const float* __restrict__ qd,
@@ -497,7 +546,7 @@ __global__ void __launch_bounds__(256, 1) grid_lane_chain_kernel(const __grid_co
   w.s1 = reinterpret_cast<float*>(base + 32 * 16 * Lay::kS4) + lane;
   const long stride = (long)gridDim.x * blockDim.x;
   for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride)
-    lc_knot<NB>(P, w, k, q, qd, tau, J, qdd_out, minv_out);
+    lc_knot<NB, PL>(P, w, k, q, qd, tau, J, qdd_out, minv_out);
 }
 
 
@@ -519,10 +568,10 @@ LcDev lc_dev(int dev) {
   return cache[dev];
 }
 
-template <int NB>
+template <int NB, bool PL>
 grid_status lc_launch(const grid_model* m, const LcParams& P, int N, const float* q, const float* qd,
                       const float* tau, float* J, float* qdd, float* Minv, cudaStream_t st) {
-  auto kern = grid_lane_chain_kernel<NB>;
+  auto kern = grid_lane_chain_kernel<NB, PL>;
   const int wb = LcLayout<NB>::kWarpBytes;
   const LcDev di = lc_dev(m->device);
   static std::atomic<int> opted{0};
@@ -565,19 +614,38 @@ grid_status lc_launch(const grid_model* m, const LcParams& P, int N, const float
   return GRID_OK;
 }
 
+template <bool PL>
+grid_status lc_dispatch(const grid_model* m, int n, const LcParams& P, int N, const float* q, const float* qd,
+                        const float* tau, float* J, float* qdd, float* Minv, cudaStream_t st) {
+  switch (n) {
+    case 2: return lc_launch<2, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
+    case 3: return lc_launch<3, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
+    case 4: return lc_launch<4, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
+    case 5: return lc_launch<5, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
+    case 6: return lc_launch<6, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
+    case 7: return lc_launch<7, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
+    default: return lc_launch<8, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
+  }
+}
+
 }  // namespace
 
 // Gradient of FD (and optionally qdd and M^-1) of a serial chain of 2 .. 8
-// revolute bodies in caller order, one lane per knot point.
-grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int N, const float* q,
-                              const float* qd, const float* tau, float* J, float* qdd, float* Minv,
-                              cudaStream_t st) {
+// revolute bodies in its own caller order, one lane per knot point. With slot
+// non-NULL the chain is one component of a robot of ld joints per knot point
+// (ld <= 32): body i is caller joint slot[i], and the call writes the chain's
+// rows of J and M^-1 (its blocks, zeros in the other joints' columns) and its
+// entries of qdd; the other components' calls write the rest.
+grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
+                              const float* q, const float* qd, const float* tau, float* J, float* qdd,
+                              float* Minv, cudaStream_t st) {
   const int n = hm->n;
-  if (n < 2 || n > kLcMaxB || hm->any_prism) {
-    grid_set_error("lane chain kernel: %d bodies", n);
+  if (n < 2 || n > kLcMaxB || hm->any_prism || (slot && (ld < n || ld > 32)) || (!slot && ld != n)) {
+    grid_set_error("lane chain kernel: %d bodies in knot points of %d joints", n, ld);
     return GRID_E_TOPOLOGY;
   }
   LcParams P{};
+  P.ld = ld;
   for (int i = 0; i < n; ++i) {
     if (hm->parent[i] != i - 1 || hm->perm[i] != i) {
       grid_set_error("lane chain kernel: not a serial chain in caller order");
@@ -587,15 +655,14 @@ grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, in
     for (int e = 0; e < 9; ++e) P.ET[i][e] = hm->ET[i][e];
     for (int e = 0; e < 10; ++e) P.inert[i][e] = hm->inert[i][e];
     if (hm->et_ident[i]) P.et_ident |= 1u << i;
+    P.slot[i] = slot ? slot[i] : i;
+    if (P.slot[i] < 0 || P.slot[i] >= ld || ((P.mask >> P.slot[i]) & 1u)) {
+      grid_set_error("lane chain kernel: bad joint placement");
+      return GRID_E_TOPOLOGY;
+    }
+    P.mask |= 1u << P.slot[i];
   }
   for (int e = 0; e < 6; ++e) P.a0[e] = hm->a0[e];
-  switch (n) {
-    case 2: return lc_launch<2>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 3: return lc_launch<3>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 4: return lc_launch<4>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 5: return lc_launch<5>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 6: return lc_launch<6>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 7: return lc_launch<7>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    default: return lc_launch<8>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-  }
+  return slot ? lc_dispatch<true>(m, n, P, N, q, qd, tau, J, qdd, Minv, st)
+              : lc_dispatch<false>(m, n, P, N, q, qd, tau, J, qdd, Minv, st);
 }

@@ -161,10 +161,12 @@ template <class S, int MODE>
 grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int N, const S* q,
                          const S* qd, const S* x3, const S* x4, S* out, S* out2, S* out3, cudaStream_t st);
 // Gradient of FD of a serial chain of 2 .. 8 revolute bodies with one lane per
-// knot point (grid_lane_chain.cu): the throughput form for large batches.
-grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int N, const float* q,
-                              const float* qd, const float* tau, float* J, float* qdd, float* Minv,
-                              cudaStream_t st);
+// knot point (grid_lane_chain.cu): the throughput form for large batches. With
+// slot non-NULL the chain is a component of a robot of ld joints per knot point
+// whose body i is caller joint slot[i] (a leg of a forest, a part).
+grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
+                              const float* q, const float* qd, const float* tau, float* J, float* qdd,
+                              float* Minv, cudaStream_t st);
 // Batches from this many knot points up take the one-lane-per-knot-point chain
 // kernel by default (below, the 8-lane kernel has the shorter latency).
 constexpr int kLaneChainMinN = 32768;
@@ -242,9 +244,21 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   const int T = m->lanes_opt == 1 ? 0 : m->lanes_opt;
   const int n = hm->n;
   if constexpr (MODE == MODE_GRAD && !MIXED && std::is_same<S, float>::value) {
-    if (m->chain && m->specialize_opt && n >= 2 && n <= kChainMaxN &&
-        (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN)))
-      return launch_lane_chain(m, hm, N, q, qd, x3, out, out2, out3, st);
+    const bool lane1 = m->specialize_opt && (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN));
+    if (lane1 && m->chain && n >= 2 && n <= kChainMaxN)
+      return launch_lane_chain(m, hm, n, nullptr, N, q, qd, x3, out, out2, out3, st);
+    // a forest with one model per chain: each chain (a leg) in turn, one lane per
+    // (knot point, leg); every call writes its leg's rows of the outputs
+    if (lane1 && m->forest_k > 1 && m->branches == m->forest_k && m->forest_l >= 2 && m->forest_l <= kChainMaxN &&
+        n <= 32) {
+      int slot[kChainMaxN];
+      for (int c = 0; c < m->forest_k; ++c) {
+        for (int i = 0; i < m->forest_l; ++i) slot[i] = c * m->forest_l + i;
+        const grid_status r = launch_lane_chain(m, &m->br_host_f[c], n, slot, N, q, qd, x3, out, out2, out3, st);
+        if (r != GRID_OK) return r;
+      }
+      return GRID_OK;
+    }
   }
   if constexpr (MODE == MODE_GRAD && !MIXED) {
     if (m->chain && m->specialize_opt && (T == 0 || T == 8) && n >= 2 && n <= kChainMaxN)
@@ -273,10 +287,16 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
         if constexpr (std::is_same<S, float>::value) { ph = P.host_f; pd = P.dev_f; }
         else { ph = P.host_d; pd = P.dev_d; }
         const cudaStream_t s = ps[p];
-        if (!MIXED && P.chain && P.n >= 2 && P.n <= kChainMaxN)
+        const bool lane1 = m->lanes_opt == 1 || N >= kLaneChainMinN;
+        if (!MIXED && P.chain && P.n >= 2 && P.n <= kChainMaxN && std::is_same<S, float>::value && lane1 &&
+            ph->ld <= 32) {
+          if constexpr (std::is_same<S, float>::value)
+            r = launch_lane_chain(m, ph, ph->ld, ph->gslot, N, q, qd, x3, out, out2, out3, s);
+        } else if (!MIXED && P.chain && P.n >= 2 && P.n <= kChainMaxN) {
           r = launch_chain_part<S, MODE>(m, ph, pd, N, q, qd, x3, x4, out, out2, out3, s);
-        else
+        } else {
           r = dispatch_model<S, MODE, MIXED>(m, ph, pd, 0, N, q, qd, x3, x4, out, out2, out3, s);
+        }
       }
       const grid_status j = grid_parts_join(m, st);
       return r == GRID_OK ? j : r;

@@ -138,3 +138,83 @@ def test_lane_option_checks(grid):
     q64, qd64, tau64 = gi.states(7, 50, 4)
     assert col_rel_err(J, oracle.grad_fd(gi.chain7(), q64, qd64, tau64)) <= 1e-10
     c.close()
+
+
+def _interleaved_tree30():
+    """The 30-DoF tree with its components interleaved in the caller's numbering
+    (parents still before children): its leg parts sit at scattered joints."""
+    r = gi.tree30()
+    arms_torso, leg1, leg2 = list(range(20)), list(range(20, 25)), list(range(25, 30))
+    perm = []
+    while arms_torso or leg1 or leg2:
+        for lst in (arms_torso, leg1, arms_torso, leg2):
+            if lst:
+                perm.append(lst.pop(0))
+    return r.permuted(perm)
+
+
+PLACED = {"tree12": gi.tree12, "tree30": gi.tree30, "tree30-interleaved": _interleaved_tree30,
+          "rand13": lambda: gi.random_tree(13, 21), "rand9": lambda: gi.random_tree(9, 8)}
+
+
+@pytest.mark.parametrize("key", list(PLACED))
+@pytest.mark.parametrize("N", [1, 77])
+def test_lane_chain_placed_components(grid, key, N):
+    """Chains that are components of a larger robot (the quadruped's legs, the
+    humanoid's legs, chain components of random trees) with lanes = 1: each leg
+    writes its rows of J and M^-1 (its blocks and exact zeros beside them) and
+    its entries of qdd, at its caller joints. Outputs pre-filled with NaN; J, M^-1
+    and qdd against the oracle."""
+    r = PLACED[key]()
+    n = r.n
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 41 + N)
+    J = torch.full((N, n, 2 * n), float("nan"), device="cuda")
+    Mi = torch.full((N, n, n), float("nan"), device="cuda")
+    qdd = torch.full((N, n), float("nan"), device="cuda")
+    m.grad_fd_minv(q, qd, tau, out=J, minv_out=Mi)
+    J2, _ = m.grad_fd(q, qd, tau, qdd_out=qdd, return_qdd=True)
+    Jh, Mh, qh, J2h = (x.cpu().numpy() for x in (J, Mi, qdd, J2))
+    assert np.isfinite(Jh).all() and np.isfinite(Mh).all() and np.isfinite(qh).all()
+    np.testing.assert_array_equal(Jh, J2h)
+    ref, mref = oracle.grad_fd(r, q64, qd64, tau64), oracle.minv(r, q64)
+    if key.startswith("rand"):
+        bar = fp32_bar(mref)
+        assert np.all(col_rel_err_knots(Jh, ref, floor=FLOOR32) <= bar)
+    else:
+        assert col_rel_err(Jh, ref, FLOOR32) <= TOL32
+    assert col_rel_err(Mh, mref, FLOOR32) <= TOL32
+    assert vec_rel_err(qh, oracle.fd(r, q64, qd64, tau64)) <= TOL32
+    if key == "tree12":                                   # exact zeros between the legs
+        for c in range(4):
+            jmask = np.ones(24, bool)
+            jmask[3 * c:3 * c + 3] = jmask[12 + 3 * c:12 + 3 * c + 3] = False
+            mmask = np.ones(12, bool)
+            mmask[3 * c:3 * c + 3] = False
+            rows = slice(3 * c, 3 * c + 3)
+            assert np.all(Jh[:, rows][:, :, jmask] == 0) and np.all(Mh[:, rows][:, :, mmask] == 0)
+    m.close()
+
+
+@pytest.mark.parametrize("key", ["tree12", "tree30"])
+def test_lane_chain_placed_default_dispatch(grid, key):
+    """Above the switch-over size the quadruped's legs and the humanoid's leg
+    parts take the one-lane kernel by default; sampled knot points of a ragged
+    batch against the oracle, and the result equal to the forced lanes = 1 run."""
+    r = gi.robot(key)
+    n = r.n
+    m = grid.Model.from_robot(r)
+    one = grid.Model.from_robot(r)
+    one.set_option("lanes", 1)
+    N = 32768 + 7
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 12)
+    J = m.grad_fd(q, qd, tau)
+    J1 = one.grad_fd(q, qd, tau)
+    torch.cuda.synchronize()
+    assert torch.equal(J, J1)
+    idx = np.unique(np.concatenate([np.sort(gi.Stream(13).u64(128) % np.uint64(N)).astype(np.int64), [0, N - 1]]))
+    ref = oracle.grad_fd(r, q64[idx], qd64[idx], tau64[idx], nthreads=8)
+    assert col_rel_err(J[torch.from_numpy(idx).cuda()].cpu().numpy(), ref, FLOOR32) <= TOL32
+    m.close()
+    one.close()
