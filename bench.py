@@ -43,25 +43,25 @@ FLOPS_PER_KNOT = {"chain7": 26845, "tree12": 21516, "tree30": 132124}
 # Nominal FP32 rate for context only (152 SMs x 128 lanes x 2 flops x 2.07 GHz); the
 # roofline divides by the rate the FMA loop measures in the same run.
 FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
-# DRAM bytes per knot point of the 7-DoF gradient kernel from one ncu capture of the
-# same kernel sources (key: kernel_source_hash), dram__bytes_read.sum +
-# dram__bytes_write.sum of a 524,288-knot-point launch divided by its knot points,
+# DRAM bytes per knot point of the 7-DoF gradient kernel (one lane per knot point)
+# from one ncu capture of the same kernel sources (key: kernel_source_hash),
+# dram__bytes_read.sum + dram__bytes_write.sum of a 524,288-knot-point launch divided
+# by its knot points,
 # and lts__t_sectors_srcunit_tex_op_write.sum x 32 B (the writes the SMs send to L2,
 # partial sectors included, whether or not they reach DRAM before the kernel ends).
 # Absent when the kernel changed since the capture.
-NCU_BYTES_PER_KNOT = {"5b7863982b2d765b": (44.114944e6 + 145.304832e6) / 524288}
-NCU_L2_WRITE_BYTES_PER_KNOT = {"5b7863982b2d765b": 11927552 * 32 / 524288}
+NCU_BYTES_PER_KNOT = {}
+NCU_L2_WRITE_BYTES_PER_KNOT = {}
 # FP32 (FMA) pipe utilisation from the same captures (sm__pipe_fma_cycles_active, % of
 # peak sustained while active), reported beside the counted-flop fraction, and the
 # busy share of the shared-memory data pipe (l1tex__data_pipe_lsu_wavefronts,
 # % of peak sustained elapsed), the unit that bounds the kernel.
-NCU_FMA_PIPE = {"5b7863982b2d765b": 0.448}
-NCU_SMEM_PIPE = {"5b7863982b2d765b": 0.875}
+NCU_FMA_PIPE = {}
+NCU_SMEM_PIPE = {}
 
 
-# The device code of the 7-DoF chain kernel (the key of the ncu tables above).
-KERNEL_FILES = ("grid_internal.h", "grid_phases.cuh", "spatial.cuh", "grid_kernel.cuh", "grid_launch.cuh",
-                "grid_chain.cu")
+# The device code of the 7-DoF step's kernel (the key of the ncu tables above).
+KERNEL_FILES = ("grid_internal.h", "spatial.cuh", "grid_lane_chain.cu")
 
 
 def kernel_source_hash() -> str:
@@ -595,6 +595,12 @@ def run_ours(args):
     sec_gen = time_steps(lambda: mgen.grad_fd(q, qd, tau, out=J), gen_steps, 2, stream, dist)
     other_value = aggregate_value(world, Nk, gen_steps, sec_gen)
     mgen.close()
+    # and in the 8-lane chain kernel (the form that batches below 32768 knot points take)
+    m8 = grid.Model.from_robot(robot)
+    m8.set_option("lanes", 8)
+    sec_8 = time_steps(lambda: m8.grad_fd(q, qd, tau, out=J), gen_steps, 2, stream, dist)
+    lanes8_value = aggregate_value(world, Nk, gen_steps, sec_8)
+    m8.close()
 
     # every workload robot, batched, in FP32, mixed and FP64-plain (the metric's
     # "FP32/mixed vs FP64 plain"); N = 128-knot trajectories, one launch per step
@@ -671,10 +677,12 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peaks["fp32"],
                          "unit": "TFLOP/s", "frac": achieved_tflops / peaks["fp32"],
                          "traffic": None if traffic is None else traffic * Nk,
-                         "traffic_note": "ncu capture of the same kernel sources on 524,288 knot points "
-                                         "(DRAM read + write), scaled by knot points; below the algorithmic "
-                                         f"{in_bytes + out_bytes:.0f} B because part of J is still in L2 at "
-                                         "kernel end" if traffic else "no capture of the current kernel sources",
+                         "traffic_note": ("ncu capture of the same kernel sources on 524,288 knot points "
+                                          "(DRAM read + write), scaled by knot points, against the algorithmic "
+                                          f"{in_bytes + out_bytes:.0f} B of a step"
+                                          + ("; below it because part of J is still in L2 at kernel end"
+                                             if traffic * Nk < in_bytes + out_bytes else ""))
+                                         if traffic else "no capture of the current kernel sources",
                          "l2_write_bytes": None if l2w is None else l2w * Nk,
                          "smem_pipe_util_ncu": smem_pipe,
                          "flops_per_knot": flops_knot,
@@ -694,10 +702,10 @@ def run_ours(args):
                             "(the kernel reads/writes host memory) and grid_grad_fd_host (H2D, "
                             "kernel and D2H in chunks, overlapped on three streams); "
                             "serial_copies = H2D, kernel, D2H one after another, for comparison"},
-            "topology": {"kernel": "chain-specialised" if args.specialize else "run-time topology",
-                         "other_kernel_value": other_value, "unit": UNIT,
-                         "note": "the same step in the other kernel (run-time topology vs the chain "
-                                 "compiled for its length)"},
+            "topology": {"kernel": "one lane per knot point (chain)" if args.specialize else "run-time topology",
+                         "other_kernel_value": other_value, "chain_8_lanes_value": lanes8_value, "unit": UNIT,
+                         "note": "the same step in the other kernels: the run-time-topology kernel "
+                                 "(specialize 0 against 1) and the chain kernel with 8 lanes per knot point"},
             "robots": robots,
             "robots_note": "gradient of FD of each workload robot, one launch of 128-knot trajectories per "
                            "step: FP32, mixed (FP64 pivots in M^-1) and FP64-plain; frac = counted flops / "
@@ -719,7 +727,8 @@ def run_ours(args):
             "clocks": clocks,
             "timed_s": sec,
             "gpu_launches": args.steps,
-            "gpu_launches_note": "timed region of `value`: one grid_grad_fd kernel per step",
+            "gpu_launches_note": "timed region of `value`: one grid_lane_chain_kernel launch per step "
+                                 "(grid_grad_fd)",
             "kernel_source": kernel_source_hash(),
         }
         print(json.dumps(line), flush=True)

@@ -45,6 +45,7 @@ struct LcParams {
   int ld;
   int slot[kLcMaxB];
   unsigned mask;
+  int zero_fill;              // write the zeros beside the chain's blocks (else the caller has)
 };
 
 
@@ -391,7 +392,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
       float* row = minv_out + (k * ld + (PL ? P.slot[i] : i)) * ld;
 #pragma unroll
       for (int kk = 0; kk < NB; ++kk) row[PL ? P.slot[kk] : kk] = Mi[lc_tri<NB>(i, kk)];
-      if (PL) {                                        // zeros beside the chain's block
+      if (PL && P.zero_fill) {                         // zeros beside the chain's block
         for (int cc = 0; cc < ld; ++cc)
           if (!((P.mask >> cc) & 1u)) row[cc] = 0.0f;
       }
@@ -520,7 +521,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
   float* Jk = J + k * 2 * ld * ld;
 #pragma unroll 1
   for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL>(P, w, c >> 1, (c & 1) == 0, Mi, Jk);
-  if (PL) {                                            // the chain's rows of J: zeros beside its blocks
+  if (PL && P.zero_fill) {                             // the chain's rows of J: zeros beside its blocks
 #pragma unroll 1
     for (int rr = 0; rr < NB; ++rr) {
       float* row = Jk + P.slot[rr] * 2 * ld;
@@ -635,10 +636,11 @@ grid_status lc_dispatch(const grid_model* m, int n, const LcParams& P, int N, co
 // non-NULL the chain is one component of a robot of ld joints per knot point
 // (ld <= 32): body i is caller joint slot[i], and the call writes the chain's
 // rows of J and M^-1 (its blocks, zeros in the other joints' columns) and its
-// entries of qdd; the other components' calls write the rest.
+// entries of qdd; the other components' calls write the rest. Without zero_fill
+// the zeros beside the blocks are left to the caller (who cleared the outputs).
 grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                               const float* q, const float* qd, const float* tau, float* J, float* qdd,
-                              float* Minv, cudaStream_t st) {
+                              float* Minv, cudaStream_t st, bool zero_fill) {
   const int n = hm->n;
   if (n < 2 || n > kLcMaxB || hm->any_prism || (slot && (ld < n || ld > 32)) || (!slot && ld != n)) {
     grid_set_error("lane chain kernel: %d bodies in knot points of %d joints", n, ld);
@@ -646,6 +648,7 @@ grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, in
   }
   LcParams P{};
   P.ld = ld;
+  P.zero_fill = zero_fill ? 1 : 0;
   for (int i = 0; i < n; ++i) {
     if (hm->parent[i] != i - 1 || hm->perm[i] != i) {
       grid_set_error("lane chain kernel: not a serial chain in caller order");

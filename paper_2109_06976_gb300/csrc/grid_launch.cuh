@@ -166,7 +166,7 @@ grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const Model
 // whose body i is caller joint slot[i] (a leg of a forest, a part).
 grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                               const float* q, const float* qd, const float* tau, float* J, float* qdd,
-                              float* Minv, cudaStream_t st);
+                              float* Minv, cudaStream_t st, bool zero_fill = true);
 // Batches from this many knot points up take the one-lane-per-knot-point chain
 // kernel by default (below, the 8-lane kernel has the shorter latency).
 constexpr int kLaneChainMinN = 32768;
@@ -247,14 +247,23 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
     const bool lane1 = m->specialize_opt && (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN));
     if (lane1 && m->chain && n >= 2 && n <= kChainMaxN)
       return launch_lane_chain(m, hm, n, nullptr, N, q, qd, x3, out, out2, out3, st);
-    // a forest with one model per chain: each chain (a leg) in turn, one lane per
-    // (knot point, leg); every call writes its leg's rows of the outputs
+    // a forest with one model per chain: the outputs cleared, then each chain (a
+    // leg) in turn, one lane per (knot point, leg), writing its blocks of J and
+    // M^-1 and its entries of qdd (scattered zero stores from every lane measured
+    // slower than one clearing pass over the outputs)
     if (lane1 && m->forest_k > 1 && m->branches == m->forest_k && m->forest_l >= 2 && m->forest_l <= kChainMaxN &&
         n <= 32) {
+      cudaError_t e = cudaMemsetAsync(out, 0, (size_t)N * 2 * n * n * sizeof(float), st);
+      if (e == cudaSuccess && out3) e = cudaMemsetAsync(out3, 0, (size_t)N * n * n * sizeof(float), st);
+      if (e != cudaSuccess) {
+        grid_set_error("clearing the outputs: %s", cudaGetErrorString(e));
+        return GRID_E_CUDA;
+      }
       int slot[kChainMaxN];
       for (int c = 0; c < m->forest_k; ++c) {
         for (int i = 0; i < m->forest_l; ++i) slot[i] = c * m->forest_l + i;
-        const grid_status r = launch_lane_chain(m, &m->br_host_f[c], n, slot, N, q, qd, x3, out, out2, out3, st);
+        const grid_status r =
+            launch_lane_chain(m, &m->br_host_f[c], n, slot, N, q, qd, x3, out, out2, out3, st, false);
         if (r != GRID_OK) return r;
       }
       return GRID_OK;
