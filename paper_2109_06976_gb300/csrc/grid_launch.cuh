@@ -244,7 +244,19 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   const int T = m->lanes_opt == 1 ? 0 : m->lanes_opt;
   const int n = hm->n;
   if constexpr (MODE == MODE_GRAD && !MIXED && std::is_same<S, float>::value) {
-    const bool lane1 = m->specialize_opt && (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN));
+    // (by default not for outputs in host memory: its scattered per-lane stores
+    // over the host link measured 2.6e7 against 2.2e8 knot-points/s for the
+    // 8-lane kernel's row-wise stores, 7-DoF chain, 2,097,152 knot points)
+    bool lane1 = m->specialize_opt && (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN));
+    if (lane1 && m->lanes_opt == 0) {
+      cudaPointerAttributes pa{};
+      if (cudaPointerGetAttributes(&pa, out) != cudaSuccess) {
+        cudaGetLastError();
+        lane1 = false;
+      } else if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) {
+        lane1 = false;
+      }
+    }
     if (lane1 && m->chain && n >= 2 && n <= kChainMaxN)
       return launch_lane_chain(m, hm, n, nullptr, N, q, qd, x3, out, out2, out3, st);
     // a forest with one model per chain: the outputs cleared, then each chain (a

@@ -218,3 +218,33 @@ def test_lane_chain_placed_default_dispatch(grid, key):
     assert col_rel_err(J[torch.from_numpy(idx).cuda()].cpu().numpy(), ref, FLOOR32) <= TOL32
     m.close()
     one.close()
+
+
+@pytest.mark.parametrize("key", ["chain7", "tree12"])
+def test_lane_chain_precision_report(grid, key, capsys):
+    """The one-lane kernel (lanes = 1) on the 7-DoF chain and the 12-DoF tree's
+    legs at N = 1024 against the FP64 oracle: the per-column metric with the
+    survey's floor (1e-6) and with the FP32 floor (1e-4), and the ratio of the
+    1e-6-floor error to the derived per-column bound (tests/metrics.py:
+    derived_col_bar). Printed for the record."""
+    from tests.metrics import col_rel_err_cols, derived_col_bar
+    r = gi.robot(key)
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)
+    N = 1024
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(r.n, N, gi.workload_seed(3, N))
+    ref_J, ref_qdd = oracle.grad_fd(r, q64, qd64, tau64, nthreads=8, with_qdd=True)
+    ref_mi = oracle.minv(r, q64, nthreads=8)
+    dq, dqd = oracle.grad_rnea(r, q64, qd64, ref_qdd, nthreads=8)
+    J = m.grad_fd(q, qd, tau).cpu().numpy()
+    e6 = col_rel_err_cols(J, ref_J, 1e-6)
+    e4 = col_rel_err_cols(J, ref_J, FLOOR32)
+    bar = derived_col_bar(ref_mi, np.concatenate([dq, dqd], axis=2), ref_J)
+    line = (f"{key} one lane per knot point N={N}: max err floor 1e-6 {e6.max():.2e} "
+            f"(p50 {np.median(e6.max(axis=1)):.2e}), floor 1e-4 {e4.max():.2e}; "
+            f"err / derived bar max {(e6 / bar).max():.2f}")
+    with capsys.disabled():
+        print("\n" + line)
+    assert e4.max() <= TOL32, line
+    assert (e6 / bar).max() <= 1.0, line
+    m.close()
