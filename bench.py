@@ -61,7 +61,7 @@ NCU_SMEM_PIPE = {"cd3378d1dcefb8f9": 0.470}
 
 
 # The device code of the 7-DoF step's kernel (the key of the ncu tables above).
-KERNEL_FILES = ("grid_internal.h", "spatial.cuh", "grid_lane_chain.cu")
+KERNEL_FILES = ("grid_internal.h", "spatial.cuh", "grid_lane_chain.cuh", "grid_lane_chain.cu")
 
 
 def kernel_source_hash() -> str:

@@ -1,671 +1,9 @@
-// Gradient of FD for serial chains of revolute joints with ONE LANE PER KNOT
-// POINT (throughput form for large batches).
-//
-// Each lane evaluates the whole method for its own knot point, in the order of
-// Sec. IV-B: joint transforms, the direct M^-1 (articulated-inertia recursion,
-// backward then forward sweep), RNEA(q, qd, 0), qdd = M^-1 (tau - c), RNEA at
-// qdd, then per derivative column (u, j) the forward pass of Alg. 1 over the
-// bodies j .. n-1 and its backward pass down to the base (with the readings of
-// the paper used by every kernel here: the case terms act only at the column's
-// own joint, the velocity-product term uses dv_k, and the accumulated force F_j
-// enters X_j^T (S_j x* F_j) for u = q), and J = -M^-1 dc column by column.
-//
-// The lanes never exchange data: no shuffles and no warp barriers. What a lane
-// keeps between phases (its transforms, velocities, I v, the case-term vectors
-// beta and phi, the M^-1 temporaries) sits in shared memory in a lane-major
-// layout: slot s of lane t of a warp is element s * 32 + t of the warp's area,
-// so a warp's 128-bit access moves 32 lanes' records in 4 wavefronts without
-// bank conflicts, against one wavefront per knot point for the kernels whose
-// lanes cooperate on one knot point. The robot's constants (axes, fixed
-// transforms, inertias, gravity) are kernel parameters, uniform across the
-// warp. M^-1 and the per-column force derivatives live in registers.
-#include <cuda_runtime.h>
+// Gradient of FD with one lane per knot point (grid_lane_chain.cuh), for serial
+// chains of 2 .. 8 revolute bodies and chains placed in a larger robot.
+#include "grid_lane_chain.cuh"
 
-#include <algorithm>
-#include <atomic>
-
-#include "grid_internal.h"
-#include "spatial.cuh"
-
-namespace {
-
-constexpr int kLcMaxB = 8;
-
-// The robot's constants, passed by value.
-struct LcParams {
-  float axis[kLcMaxB][3];
-  float rT[kLcMaxB][3];
-  float ET[kLcMaxB][9];
-  float inert[kLcMaxB][10];   // m, h = m c (3), Ibar about the body origin: xx yy zz xy xz yz
-  float a0[6];                // base acceleration -g
-  unsigned et_ident;          // bit i: the fixed rotation of body i is the identity
-  // Placement in the caller's arrays (a chain that is one component of a larger
-  // robot): joints per knot point, the caller joint of body i, and a bit for
-  // each caller joint of the chain. A whole robot has ld = n, slot[i] = i.
-  int ld;
-  int slot[kLcMaxB];
-  unsigned mask;
-  int zero_fill;              // write the zeros beside the chain's blocks (else the caller has)
-};
-
-
-// Lane-major workspace of one warp. Per body i, float4 slots 7 i + 0..6:
-//   E0 = E[0..3], E1 = E[4..7], V0 = v[0..3], V1 = {v4, v5, E[8], qd_i},
-//   B0 = beta[0..3], B1 = phi[0..3], B2 = {beta4, beta5, phi4, phi5}
-// (while M^-1 is formed: V0, V1.xy hold U_i, B0 and B1 row i of M^-1 by column
-// index, B2.x D_i^-1; between the RNEA passes B0, B2.xy hold X_i a_parent and
-// B1, B2.zw the force f_i), then scalar slots 0 .. 7 (the bias forces c, then
-// qdd). I v is recomputed where the columns need it, and M^-1 and dc sit in
-// registers: 816 B per knot point of the 7-DoF chain, so that eight warps (two
-// per scheduler) fit on an SM.
-template <int NB>
-struct LcLayout {
-  static constexpr int kMi = NB * (NB + 1) / 2;      // packed upper triangle of M^-1
-  static constexpr int kS4 = 7 * NB;
-  static constexpr int kS1 = 8;
-  static constexpr int kWarpBytes = 32 * (16 * kS4 + 4 * kS1);
-};
-
-struct LcWs {
-  float4* s4;   // this lane's element of float4 slot 0
-  float* s1;
-  __device__ float4& f4(int s) const { return s4[s * 32]; }
-  __device__ float& f1(int s) const { return s1[s * 32]; }
-};
-
-// E_i, and from the same slots v_i and qd_i
-__device__ __forceinline__ void lc_load_E(const LcWs& w, int i, float* E) {
-  const float4 a = w.f4(7 * i), b = w.f4(7 * i + 1);
-  E[0] = a.x; E[1] = a.y; E[2] = a.z; E[3] = a.w;
-  E[4] = b.x; E[5] = b.y; E[6] = b.z; E[7] = b.w;
-  E[8] = w.f4(7 * i + 3).z;
-}
-
-__device__ __forceinline__ void lc_load_v(const LcWs& w, int i, float* v, float& qdi, float& e8) {
-  const float4 a = w.f4(7 * i + 2), b = w.f4(7 * i + 3);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
-  e8 = b.z;
-  qdi = b.w;
-}
-
-// X_i = X_J(q_i) X_T,i with E_J = R(a, q)^T = cos q 1 + (1 - cos q) a a^T - sin q a~.
-__device__ __forceinline__ void lc_transform(const LcParams& P, int i, float q, float* E) {
-  const float* a = P.axis[i];
-  float s, co;
-  sincosf(q, &s, &co);
-  const float omc = 1.0f - co;
-  float EJ[9];
-  EJ[0] = co + omc * a[0] * a[0];      EJ[1] = omc * a[0] * a[1] + s * a[2]; EJ[2] = omc * a[0] * a[2] - s * a[1];
-  EJ[3] = omc * a[1] * a[0] - s * a[2]; EJ[4] = co + omc * a[1] * a[1];     EJ[5] = omc * a[1] * a[2] + s * a[0];
-  EJ[6] = omc * a[2] * a[0] + s * a[1]; EJ[7] = omc * a[2] * a[1] - s * a[0]; EJ[8] = co + omc * a[2] * a[2];
-  if ((P.et_ident >> i) & 1u) {
-#pragma unroll
-    for (int e = 0; e < 9; ++e) E[e] = EJ[e];
-  } else {
-    const float* ET = P.ET[i];
-#pragma unroll
-    for (int u = 0; u < 3; ++u)
-#pragma unroll
-      for (int v = 0; v < 3; ++v)
-        E[3 * u + v] = EJ[3 * u] * ET[v] + EJ[3 * u + 1] * ET[3 + v] + EJ[3 * u + 2] * ET[6 + v];
-  }
-}
-
-// Structural zeros of the 6x6 spatial inertia [Ibar h~; h~^T m 1]: the diagonal
-// of h~ and the off-diagonal entries of m 1.
-__device__ __forceinline__ constexpr bool lc_izero(int u, int s) {
-  return ((u < 3) != (s < 3) && u % 3 == s % 3) || (u >= 3 && s >= 3 && u != s);
-}
-
-// Packed upper triangle of the symmetric n x n M^-1: entry (r, c).
-template <int NB>
-__device__ __forceinline__ constexpr int lc_tri(int r, int c) {
-  return r <= c ? r * NB - r * (r - 1) / 2 + (c - r) : c * NB - c * (c - 1) / 2 + (r - c);
-}
-
-// One derivative column (u, j), u = q when uq: the forward pass over bodies
-// j .. n-1, the backward pass down to the base (dc_i for every body), then
-// J[:, col] = -M^-1 dc. The loops run over the bodies at compile time (the
-// bodies before j are skipped by a branch that is uniform across the warp), so
-// body indices, shared-memory offsets and the robot's constants are immediate
-// operands; one code path serves both kinds of column, which differ only in
-// the case terms at the column's own joint.
-// A body's record as the column passes read it.
-struct LcBody {
-  float E[9], v[6], qd;
-};
-
-__device__ __forceinline__ void lc_load_body(const LcWs& w, int i, LcBody& b) {
-  const float4 x0 = w.f4(7 * i), x1 = w.f4(7 * i + 1), a = w.f4(7 * i + 2), c = w.f4(7 * i + 3);
-  b.E[0] = x0.x; b.E[1] = x0.y; b.E[2] = x0.z; b.E[3] = x0.w;
-  b.E[4] = x1.x; b.E[5] = x1.y; b.E[6] = x1.z; b.E[7] = x1.w; b.E[8] = c.z;
-  b.v[0] = a.x; b.v[1] = a.y; b.v[2] = a.z; b.v[3] = a.w; b.v[4] = c.x; b.v[5] = c.y;
-  b.qd = c.w;
-}
-
-// One derivative column (u, j), u = q when uq: the forward pass over bodies
-// j .. n-1, the backward pass down to the base (dc_i for every body), then
-// J[:, col] = -M^-1 dc. The loops run over the bodies at compile time (the
-// bodies before j are skipped by a branch that is uniform across the warp), so
-// body indices, shared-memory offsets and the robot's constants are immediate
-// operands; one code path serves both kinds of column, which differ only in
-// the case terms at the column's own joint. The next body's record is loaded
-// before the current body's arithmetic, so that the shared-memory latency
-// overlaps it.
-template <int NB, bool PL>
-__device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int j, bool uq, const float* Mi,
-                                          float* __restrict__ Jk) {
-  float df[NB][6];
-  float dv[6], da[6];
-  LcBody cur, nxt;
-  lc_load_body(w, j, cur);
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    if (i >= j) {
-      if (i + 1 < NB) lc_load_body(w, i + 1, nxt);
-      const float* a = P.axis[i];
-      const float* in = P.inert[i];
-      const float* v = cur.v;
-      float g[6], ndv[6], nda[6], vxs[6];
-      i_mul(in, v, g);                                 // gamma_i = I_i v_i
-      cross_s(v, a, false, vxs);                       // v x S
-      if (i == j) {
-        // u = q: dv_j = v_j x S_j, da_j = beta_j;  u = qd: dv_j = S_j, da_j = v_j x S_j
-        const float4 b0 = w.f4(7 * i + 4), b2 = w.f4(7 * i + 6);
-        const float beta[6] = {b0.x, b0.y, b0.z, b0.w, b2.x, b2.y};
-        const float s6[6] = {a[0], a[1], a[2], 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int e = 0; e < 6; ++e) {
-          ndv[e] = uq ? vxs[e] : s6[e];
-          nda[e] = uq ? beta[e] : vxs[e];
-        }
-      } else {
-        x_mul(cur.E, P.rT[i], dv, ndv);
-        x_mul(cur.E, P.rT[i], da, nda);
-      }
-      const float sq[3] = {a[0] * cur.qd, a[1] * cur.qd, a[2] * cur.qd};
-      cross_s_acc(ndv, sq, false, nda);                // + dv x S qd
-      float f[6], idv[6];
-      i_mul(in, nda, f);
-      crf_mul_acc(ndv, g, f);
-      i_mul(in, ndv, idv);
-      crf_mul_acc(v, idv, f);
-      if (i == j && uq && j > 0) {                     // + S_j x* F_j (backward-pass term; it
-                                                       // reaches the ancestors of j only)
-        const float4 b1 = w.f4(7 * i + 5), b2 = w.f4(7 * i + 6);
-        f[0] += b1.x; f[1] += b1.y; f[2] += b1.z; f[3] += b1.w; f[4] += b2.z; f[5] += b2.w;
-      }
-#pragma unroll
-      for (int e = 0; e < 6; ++e) { df[i][e] = f[e]; dv[e] = ndv[e]; da[e] = nda[e]; }
-      cur = nxt;
-    }
-  }
-  // backward: dF_i = df_i + X_{i+1}^T dF_{i+1} (df_i = 0 above j's subtree),
-  // dc_i = S_i^T dF_i
-  float dF[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, dc[NB];
-  float Ec[9], En[9];
-  lc_load_E(w, NB - 1, Ec);
-#pragma unroll
-  for (int i = NB - 1; i >= 0; --i) {
-    if (i > 1) lc_load_E(w, i - 1, En);
-    if (i >= j) {
-#pragma unroll
-      for (int e = 0; e < 6; ++e) dF[e] += df[i][e];
-    }
-    dc[i] = dot_s(P.axis[i], false, dF);
-    if (i > 0) {
-      float t[6];
-      xt_mul(Ec, P.rT[i], dF, t);
-#pragma unroll
-      for (int e = 0; e < 6; ++e) dF[e] = t[e];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) Ec[e] = En[e];
-    }
-  }
-  const int ld = PL ? P.ld : NB;
-  const int col = (uq ? 0 : ld) + (PL ? P.slot[j] : j);
-#pragma unroll
-  for (int rr = 0; rr < NB; ++rr) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int m = 0; m < NB; ++m) acc += Mi[lc_tri<NB>(rr, m)] * dc[m];
-    if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = -acc;
-  }
-}
-
-template <int NB, bool PL>
-__device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k, const float* __restrict__ q,
-                                        const float* __restrict__ qd, const float* __restrict__ tau,
-                                        float* __restrict__ J, float* __restrict__ qdd_out,
-                                        float* __restrict__ minv_out) {
-  // ---- a2 + a4: transforms and the backward sweep of the direct M^-1
-  //   I^A_i = I_i + X_{i+1}^T (I^A_{i+1} - U_{i+1} D_{i+1}^-1 U_{i+1}^T) X_{i+1}
-  //   U_i = I^A_i S_i, D_i = S_i^T U_i, Minv[i][i] = D_i^-1,
-  //   Minv[i][k] = -D_i^-1 S_i^T F_k (k > i),  F_k <- X_i^T (F_k + U_i Minv[i][k]) (k >= i)
-  // The sweeps are loops over bodies with the F and P columns indexed at
-  // compile time, which keeps the code small. A placed chain (PL) reads and
-  // writes the caller joints slot[i] of knot points of ld joints.
-  const int ld = PL ? P.ld : NB;
-  {
-    float Fc[NB][6], carry[6][6];
-#pragma unroll
-    for (int kk = 0; kk < NB; ++kk)
-#pragma unroll
-      for (int e = 0; e < 6; ++e) Fc[kk][e] = 0.0f;
-#pragma unroll
-    for (int u = 0; u < 6; ++u)
-#pragma unroll
-      for (int s = 0; s < 6; ++s) carry[u][s] = 0.0f;
-#pragma unroll 1
-    for (int i = NB - 1; i >= 0; --i) {
-      float E[9];
-      const long gi = k * ld + (PL ? P.slot[i] : i);
-      lc_transform(P, i, __ldg(q + gi), E);
-      const float qdi = __ldg(qd + gi);
-      w.f4(7 * i) = make_float4(E[0], E[1], E[2], E[3]);
-      w.f4(7 * i + 1) = make_float4(E[4], E[5], E[6], E[7]);
-      const float* a = P.axis[i];
-      const float* r = P.rT[i];
-      const float* in = P.inert[i];
-      // I^A_i = I_i + the child's X^T A X (column s of it in carry[s]; zero for the
-      // leaf); the structural zeros of I_i add nothing
-      float IA[6][6];
-#pragma unroll
-      for (int u = 0; u < 6; ++u)
-#pragma unroll
-        for (int s = 0; s < 6; ++s) IA[u][s] = lc_izero(u, s) ? carry[s][u] : i_entry(in, u, s) + carry[s][u];
-      float U[6];
-#pragma unroll
-      for (int u = 0; u < 6; ++u) U[u] = IA[u][0] * a[0] + IA[u][1] * a[1] + IA[u][2] * a[2];
-      const float D = a[0] * U[0] + a[1] * U[1] + a[2] * U[2];
-      const float Dinv = rcp_pivot(D);
-      w.f4(7 * i + 2) = make_float4(U[0], U[1], U[2], U[3]);
-      w.f4(7 * i + 3) = make_float4(U[4], U[5], E[8], qdi);
-      float row[8];
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        if (kk < NB) {
-          const float st = a[0] * Fc[kk][0] + a[1] * Fc[kk][1] + a[2] * Fc[kk][2];
-          row[kk] = kk == i ? Dinv : (kk > i ? -Dinv * st : 0.0f);
-        } else {
-          row[kk] = 0.0f;
-        }
-      }
-      w.f4(7 * i + 4) = make_float4(row[0], row[1], row[2], row[3]);
-      w.f4(7 * i + 5) = make_float4(row[4], row[5], row[6], row[7]);
-      w.f4(7 * i + 6) = make_float4(Dinv, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-      for (int kk = 0; kk < NB; ++kk) {
-        if (kk == i) {
-#pragma unroll
-          for (int e = 0; e < 6; ++e) Fc[kk][e] = U[e] * Dinv;
-        } else if (kk > i) {
-#pragma unroll
-          for (int e = 0; e < 6; ++e) Fc[kk][e] += U[e] * row[kk];
-        }
-      }
-      if (i > 0) {
-#pragma unroll
-        for (int kk = 0; kk < NB; ++kk) {
-          if (kk >= i) {
-            float t[6];
-            xt_mul(E, r, Fc[kk], t);
-#pragma unroll
-            for (int e = 0; e < 6; ++e) Fc[kk][e] = t[e];
-          }
-        }
-        // X^T A X for A = I^A - U D^-1 U^T: B = X^T A column by column, then
-        // column s of X^T A X = X^T (row s of B)   (A symmetric)
-        float wv[6];
-#pragma unroll
-        for (int u = 0; u < 6; ++u) wv[u] = U[u] * Dinv;
-        float A[6][6];                                  // upper triangle, mirrored
-#pragma unroll
-        for (int u = 0; u < 6; ++u)
-#pragma unroll
-          for (int s = u; s < 6; ++s) { A[u][s] = IA[u][s] - wv[u] * U[s]; A[s][u] = A[u][s]; }
-        float B[6][6];                                  // B[s] = column s of X^T A
-#pragma unroll
-        for (int s = 0; s < 6; ++s) xt_mul(E, r, A[s], B[s]);   // (column s of A = row s)
-#pragma unroll
-        for (int s = 0; s < 6; ++s) {
-          float rw[6];
-#pragma unroll
-          for (int u = 0; u < 6; ++u) rw[u] = B[u][s];
-          xt_mul(E, r, rw, carry[s]);                   // column s of X^T A X (symmetric)
-        }
-      }
-    }
-  }
-  // forward sweep: for k >= i, t = X_i P_{i-1}[k], Minv[i][k] -= D_i^-1 U_i^T t,
-  // P_i[k] = S_i Minv[i][k] + t   (P_0[k] = S_0 Minv[0][k])
-  {
-    float Pc[NB][6];
-    {
-      const float* a = P.axis[0];
-      const float4 m0 = w.f4(4), m1 = w.f4(5);
-      const float row[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-      for (int kk = 0; kk < NB; ++kk) {
-        Pc[kk][0] = a[0] * row[kk]; Pc[kk][1] = a[1] * row[kk]; Pc[kk][2] = a[2] * row[kk];
-        Pc[kk][3] = Pc[kk][4] = Pc[kk][5] = 0.0f;
-      }
-    }
-#pragma unroll 1
-    for (int i = 1; i < NB; ++i) {
-      const float* a = P.axis[i];
-      float E[9];
-      lc_load_E(w, i, E);
-      const float4 u0 = w.f4(7 * i + 2), u1 = w.f4(7 * i + 3);
-      const float U[6] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y};
-      const float Dinv = w.f4(7 * i + 6).x;
-      const float4 m0 = w.f4(7 * i + 4), m1 = w.f4(7 * i + 5);
-      float row[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-      for (int kk = 0; kk < NB; ++kk) {
-        if (kk >= i) {
-          float t[6];
-          x_mul(E, P.rT[i], Pc[kk], t);
-          const float mk = row[kk] - Dinv * dot6(U, t);
-          row[kk] = mk;
-          Pc[kk][0] = a[0] * mk + t[0]; Pc[kk][1] = a[1] * mk + t[1]; Pc[kk][2] = a[2] * mk + t[2];
-          Pc[kk][3] = t[3]; Pc[kk][4] = t[4]; Pc[kk][5] = t[5];
-        }
-      }
-      w.f4(7 * i + 4) = make_float4(row[0], row[1], row[2], row[3]);
-      w.f4(7 * i + 5) = make_float4(row[4], row[5], row[6], row[7]);
-    }
-  }
-  // M^-1 (packed upper triangle) into registers, where it stays for FD and the
-  // column products
-  float Mi[LcLayout<NB>::kMi];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    const float4 m0 = w.f4(7 * i + 4), m1 = w.f4(7 * i + 5);
-    const float row[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-    for (int kk = i; kk < NB; ++kk) Mi[lc_tri<NB>(i, kk)] = row[kk];
-  }
-  if (minv_out) {
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      float* row = minv_out + (k * ld + (PL ? P.slot[i] : i)) * ld;
-#pragma unroll
-      for (int kk = 0; kk < NB; ++kk) row[PL ? P.slot[kk] : kk] = Mi[lc_tri<NB>(i, kk)];
-      if (PL && P.zero_fill) {                         // zeros beside the chain's block
-        for (int cc = 0; cc < ld; ++cc)
-          if (!((P.mask >> cc) & 1u)) row[cc] = 0.0f;
-      }
-    }
-  }
-  // ---- a3: RNEA(q, qd, 0); X_i a_parent in B0 / B2.xy and f_i in B1 / B2.zw
-  {
-    float vp[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, ap[6];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) ap[e] = P.a0[e];
-#pragma unroll 1
-    for (int i = 0; i < NB; ++i) {
-      float E[9];
-      lc_load_E(w, i, E);
-      const float* a = P.axis[i];
-      const float* r = P.rT[i];
-      const float* in = P.inert[i];
-      const float qdi = w.f4(7 * i + 3).w;
-      const float sq[3] = {a[0] * qdi, a[1] * qdi, a[2] * qdi};   // S qd
-      float v[6], Xa[6], acc[6], g[6], f[6];
-      x_mul(E, r, vp, v);                              // v_parent = 0 at the base
-      v[0] += sq[0]; v[1] += sq[1]; v[2] += sq[2];
-      x_mul(E, r, ap, Xa);                             // a_parent = a_0 at the base
-#pragma unroll
-      for (int e = 0; e < 6; ++e) acc[e] = Xa[e];
-      {
-        const float vj[6] = {sq[0], sq[1], sq[2], 0.0f, 0.0f, 0.0f};
-        crm_mul_acc(v, vj, acc);                       // a = X a_parent + v x S qd
-      }
-      i_mul(in, v, g);
-      i_mul(in, acc, f);
-      crf_mul_acc(v, g, f);
-      w.f4(7 * i + 2) = make_float4(v[0], v[1], v[2], v[3]);
-      w.f4(7 * i + 3) = make_float4(v[4], v[5], E[8], qdi);
-      w.f4(7 * i + 4) = make_float4(Xa[0], Xa[1], Xa[2], Xa[3]);
-      w.f4(7 * i + 5) = make_float4(f[0], f[1], f[2], f[3]);
-      w.f4(7 * i + 6) = make_float4(Xa[4], Xa[5], f[4], f[5]);
-#pragma unroll
-      for (int e = 0; e < 6; ++e) { vp[e] = v[e]; ap[e] = acc[e]; }
-    }
-    // backward: F_i = f_i + X_{i+1}^T F_{i+1}, c_i = S_i^T F_i (scalar slot i)
-    float F[6];
-    {
-      const float4 f0 = w.f4(7 * (NB - 1) + 5), f2 = w.f4(7 * (NB - 1) + 6);
-      F[0] = f0.x; F[1] = f0.y; F[2] = f0.z; F[3] = f0.w; F[4] = f2.z; F[5] = f2.w;
-      w.f1(NB - 1) = dot_s(P.axis[NB - 1], false, F);
-    }
-#pragma unroll 1
-    for (int i = NB - 2; i >= 0; --i) {
-      float E[9], t[6];
-      lc_load_E(w, i + 1, E);
-      xt_mul(E, P.rT[i + 1], F, t);
-      const float4 f0 = w.f4(7 * i + 5), f2 = w.f4(7 * i + 6);
-      F[0] = f0.x + t[0]; F[1] = f0.y + t[1]; F[2] = f0.z + t[2]; F[3] = f0.w + t[3];
-      F[4] = f2.z + t[4]; F[5] = f2.w + t[5];
-      w.f1(i) = dot_s(P.axis[i], false, F);
-    }
-  }
-  // ---- a5: qdd = M^-1 (tau - c) (scalar slot i then holds qdd_i)
-  {
-    float rhs[NB], qdd[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) rhs[i] = __ldg(tau + k * ld + (PL ? P.slot[i] : i)) - w.f1(i);
-#pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int kk = 0; kk < NB; ++kk) acc += Mi[lc_tri<NB>(i, kk)] * rhs[kk];
-      qdd[i] = acc;
-    }
-#pragma unroll
-    for (int i = 0; i < NB; ++i) w.f1(i) = qdd[i];
-    if (qdd_out) {
-#pragma unroll
-      for (int i = 0; i < NB; ++i) qdd_out[k * ld + (PL ? P.slot[i] : i)] = qdd[i];
-    }
-  }
-  // ---- a6: RNEA at qdd: da_i = X_i da_{i-1} + S_i qdd_i, f_i += I_i da_i;
-  // beta_i = (X_i a_parent) x S_i at qdd; accumulated forces F_i, phi_i = S_i x* F_i
-  {
-    float dap[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 1
-    for (int i = 0; i < NB; ++i) {
-      const float* a = P.axis[i];
-      float E[9], da[6], Xa[6], f[6];
-      lc_load_E(w, i, E);
-      const float4 x0 = w.f4(7 * i + 4), f0 = w.f4(7 * i + 5), x2 = w.f4(7 * i + 6);
-      Xa[0] = x0.x; Xa[1] = x0.y; Xa[2] = x0.z; Xa[3] = x0.w; Xa[4] = x2.x; Xa[5] = x2.y;
-      f[0] = f0.x; f[1] = f0.y; f[2] = f0.z; f[3] = f0.w; f[4] = x2.z; f[5] = x2.w;
-      x_mul(E, P.rT[i], dap, da);                      // zero at the base
-#pragma unroll
-      for (int e = 0; e < 6; ++e) Xa[e] += da[e];
-      const float qddi = w.f1(i);
-      da[0] += a[0] * qddi; da[1] += a[1] * qddi; da[2] += a[2] * qddi;
-      i_mul_acc(P.inert[i], da, f);
-      float beta[6];
-      cross_s(Xa, a, false, beta);
-      w.f4(7 * i + 4) = make_float4(beta[0], beta[1], beta[2], beta[3]);
-      w.f4(7 * i + 5) = make_float4(f[0], f[1], f[2], f[3]);
-      w.f4(7 * i + 6) = make_float4(beta[4], beta[5], f[4], f[5]);
-#pragma unroll
-      for (int e = 0; e < 6; ++e) dap[e] = da[e];
-    }
-    float F[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 1
-    for (int i = NB - 1; i >= 0; --i) {
-      const float4 f0 = w.f4(7 * i + 5), b2 = w.f4(7 * i + 6);
-      float t[6];
-      if (i + 1 < NB) {
-        float E[9];
-        lc_load_E(w, i + 1, E);
-        xt_mul(E, P.rT[i + 1], F, t);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 6; ++e) t[e] = 0.0f;
-      }
-      F[0] = f0.x + t[0]; F[1] = f0.y + t[1]; F[2] = f0.z + t[2]; F[3] = f0.w + t[3];
-      F[4] = b2.z + t[4]; F[5] = b2.w + t[5];
-      float ph[6];
-      crf_s(P.axis[i], false, F, ph);
-      w.f4(7 * i + 5) = make_float4(ph[0], ph[1], ph[2], ph[3]);
-      w.f4(7 * i + 6) = make_float4(b2.x, b2.y, ph[4], ph[5]);
-    }
-  }
-  // ---- a7 - a9: derivative columns and J = -M^-1 dc
-  float* Jk = J + k * 2 * ld * ld;
-#pragma unroll 1
-  for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL>(P, w, c >> 1, (c & 1) == 0, Mi, Jk);
-  if (PL && P.zero_fill) {                             // the chain's rows of J: zeros beside its blocks
-#pragma unroll 1
-    for (int rr = 0; rr < NB; ++rr) {
-      float* row = Jk + P.slot[rr] * 2 * ld;
-      for (int cc = 0; cc < 2 * ld; ++cc)
-        if (!((P.mask >> (cc < ld ? cc : cc - ld)) & 1u)) row[cc] = 0.0f;
-    }
-  }
-}
-
-template <int NB, bool PL>
-__global__ void __launch_bounds__(256, 1) grid_lane_chain_kernel(const __grid_constant__ LcParams P, int N,
-                                                                 const float* __restrict__ q,
-                                                                 const float* __restrict__ qd,
-                                                                 const float* __restrict__ tau,
-                                                                 float* __restrict__ J, float* __restrict__ qdd_out,
-                                                                 float* __restrict__ minv_out) {
-  extern __shared__ __align__(16) unsigned char lc_smem[];
-  using Lay = LcLayout<NB>;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* base = lc_smem + (size_t)warp * Lay::kWarpBytes;
-  LcWs w;
-  w.s4 = reinterpret_cast<float4*>(base) + lane;
-  w.s1 = reinterpret_cast<float*>(base + 32 * 16 * Lay::kS4) + lane;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride)
-    lc_knot<NB, PL>(P, w, k, q, qd, tau, J, qdd_out, minv_out);
-}
-
-
-struct LcDev {
-  int nsm = 0, smem_optin = 0;
-};
-
-LcDev lc_dev(int dev) {
-  static LcDev cache[64];
-  static std::atomic<int> ready[64];
-  if (dev < 0 || dev >= 64) return LcDev{};
-  if (!ready[dev].load()) {
-    LcDev d;
-    cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cache[dev] = d;
-    ready[dev].store(1);
-  }
-  return cache[dev];
-}
-
-template <int NB, bool PL>
-grid_status lc_launch(const grid_model* m, const LcParams& P, int N, const float* q, const float* qd,
-                      const float* tau, float* J, float* qdd, float* Minv, cudaStream_t st) {
-  auto kern = grid_lane_chain_kernel<NB, PL>;
-  const int wb = LcLayout<NB>::kWarpBytes;
-  const LcDev di = lc_dev(m->device);
-  static std::atomic<int> opted{0};
-  if (!opted.load()) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, di.smem_optin);
-    if (e != cudaSuccess) {
-      grid_set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-      return GRID_E_CUDA;
-    }
-    opted.store(1);
-  }
-  // warps per CTA: the count that keeps the most warps resident per SM
-  static std::atomic<int> cached{0};
-  int c0 = cached.load();
-  int warps = c0 >> 8, per_sm = c0 & 0xff;
-  if (!c0) {
-    int best = 0;
-    for (int wc = 8; wc >= 1; --wc) {
-      if (wc * wb > di.smem_optin) continue;
-      int b = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 32 * wc, (size_t)wc * wb);
-      if (b * wc > best) { best = b * wc; warps = wc; per_sm = b; }
-    }
-    if (!warps) {
-      grid_set_error("lane chain kernel: %d B of shared memory per warp do not fit", wb);
-      return GRID_E_ARG;
-    }
-    cached.store((warps << 8) | per_sm);
-  }
-  if (m->ctas_opt > 0 && m->ctas_opt < per_sm) per_sm = m->ctas_opt;
-  const int threads = 32 * warps;
-  const long ctas = ((long)N + threads - 1) / threads;
-  const int grid = (int)std::min<long>(ctas, (long)di.nsm * per_sm);
-  kern<<<grid, threads, (size_t)warps * wb, st>>>(P, N, q, qd, tau, J, qdd, Minv);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    grid_set_error("kernel launch: %s", cudaGetErrorString(e));
-    return GRID_E_CUDA;
-  }
-  return GRID_OK;
-}
-
-template <bool PL>
-grid_status lc_dispatch(const grid_model* m, int n, const LcParams& P, int N, const float* q, const float* qd,
-                        const float* tau, float* J, float* qdd, float* Minv, cudaStream_t st) {
-  switch (n) {
-    case 2: return lc_launch<2, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 3: return lc_launch<3, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 4: return lc_launch<4, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 5: return lc_launch<5, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 6: return lc_launch<6, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    case 7: return lc_launch<7, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-    default: return lc_launch<8, PL>(m, P, N, q, qd, tau, J, qdd, Minv, st);
-  }
-}
-
-}  // namespace
-
-// Gradient of FD (and optionally qdd and M^-1) of a serial chain of 2 .. 8
-// revolute bodies in its own caller order, one lane per knot point. With slot
-// non-NULL the chain is one component of a robot of ld joints per knot point
-// (ld <= 32): body i is caller joint slot[i], and the call writes the chain's
-// rows of J and M^-1 (its blocks, zeros in the other joints' columns) and its
-// entries of qdd; the other components' calls write the rest. Without zero_fill
-// the zeros beside the blocks are left to the caller (who cleared the outputs).
 grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                               const float* q, const float* qd, const float* tau, float* J, float* qdd,
                               float* Minv, cudaStream_t st, bool zero_fill) {
-  const int n = hm->n;
-  if (n < 2 || n > kLcMaxB || hm->any_prism || (slot && (ld < n || ld > 32)) || (!slot && ld != n)) {
-    grid_set_error("lane chain kernel: %d bodies in knot points of %d joints", n, ld);
-    return GRID_E_TOPOLOGY;
-  }
-  LcParams P{};
-  P.ld = ld;
-  P.zero_fill = zero_fill ? 1 : 0;
-  for (int i = 0; i < n; ++i) {
-    if (hm->parent[i] != i - 1 || hm->perm[i] != i) {
-      grid_set_error("lane chain kernel: not a serial chain in caller order");
-      return GRID_E_TOPOLOGY;
-    }
-    for (int e = 0; e < 3; ++e) { P.axis[i][e] = hm->axis[i][e]; P.rT[i][e] = hm->rT[i][e]; }
-    for (int e = 0; e < 9; ++e) P.ET[i][e] = hm->ET[i][e];
-    for (int e = 0; e < 10; ++e) P.inert[i][e] = hm->inert[i][e];
-    if (hm->et_ident[i]) P.et_ident |= 1u << i;
-    P.slot[i] = slot ? slot[i] : i;
-    if (P.slot[i] < 0 || P.slot[i] >= ld || ((P.mask >> P.slot[i]) & 1u)) {
-      grid_set_error("lane chain kernel: bad joint placement");
-      return GRID_E_TOPOLOGY;
-    }
-    P.mask |= 1u << P.slot[i];
-  }
-  for (int e = 0; e < 6; ++e) P.a0[e] = hm->a0[e];
-  return slot ? lc_dispatch<true>(m, n, P, N, q, qd, tau, J, qdd, Minv, st)
-              : lc_dispatch<false>(m, n, P, N, q, qd, tau, J, qdd, Minv, st);
+  return lc_run<MODE_GRAD>(m, hm, ld, slot, N, q, qd, tau, nullptr, J, qdd, Minv, st, zero_fill);
 }

@@ -167,6 +167,13 @@ grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const Model
 grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                               const float* q, const float* qd, const float* tau, float* J, float* qdd,
                               float* Minv, cudaStream_t st, bool zero_fill = true);
+// FD and the vector-Jacobian product through FD in the same form
+// (grid_lane_chain_fdv.cu): qdd; dL/dq, dL/dqd, dL/dtau for gbar = dL/dqdd.
+grid_status launch_lane_chain_fd(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
+                                 const float* q, const float* qd, const float* tau, float* qdd, cudaStream_t st);
+grid_status launch_lane_chain_vjp(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
+                                  const float* q, const float* qd, const float* tau, const float* gbar, float* dq,
+                                  float* dqd, float* dtau, cudaStream_t st);
 // Batches from this many knot points up take the one-lane-per-knot-point chain
 // kernel by default (below, the 8-lane kernel has the shorter latency).
 constexpr int kLaneChainMinN = 32768;
@@ -243,6 +250,35 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   // FD of FP32 serial chains), automatic elsewhere
   const int T = m->lanes_opt == 1 ? 0 : m->lanes_opt;
   const int n = hm->n;
+  if constexpr ((MODE == MODE_FD || MODE == MODE_VJP) && !MIXED && std::is_same<S, float>::value) {
+    // FD and the vector-Jacobian product of chains and of a forest's legs, one lane
+    // per knot point (each leg writes its joints' entries of the vector outputs)
+    bool lane1 = m->specialize_opt && (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN));
+    if (lane1 && m->lanes_opt == 0) {
+      cudaPointerAttributes pa{};
+      if (cudaPointerGetAttributes(&pa, out) != cudaSuccess) {
+        cudaGetLastError();
+        lane1 = false;
+      } else if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) {
+        lane1 = false;
+      }
+    }
+    auto one = [&](const ModelDev<float>* mh, const int* slot) {
+      if constexpr (MODE == MODE_FD) return launch_lane_chain_fd(m, mh, n, slot, N, q, qd, x3, out, st);
+      else return launch_lane_chain_vjp(m, mh, n, slot, N, q, qd, x3, x4, out, out2, out3, st);
+    };
+    if (lane1 && m->chain && n >= 2 && n <= kChainMaxN) return one(hm, nullptr);
+    if (lane1 && m->forest_k > 1 && m->branches == m->forest_k && m->forest_l >= 2 && m->forest_l <= kChainMaxN &&
+        n <= 32) {
+      int slot[kChainMaxN];
+      for (int c = 0; c < m->forest_k; ++c) {
+        for (int i = 0; i < m->forest_l; ++i) slot[i] = c * m->forest_l + i;
+        const grid_status r = one(&m->br_host_f[c], slot);
+        if (r != GRID_OK) return r;
+      }
+      return GRID_OK;
+    }
+  }
   if constexpr (MODE == MODE_GRAD && !MIXED && std::is_same<S, float>::value) {
     // (by default not for outputs in host memory: its scattered per-lane stores
     // over the host link measured 2.6e7 against 2.2e8 knot-points/s for the

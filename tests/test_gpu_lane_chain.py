@@ -248,3 +248,62 @@ def test_lane_chain_precision_report(grid, key, capsys):
     assert e4.max() <= TOL32, line
     assert (e6 / bar).max() <= 1.0, line
     m.close()
+
+
+FDV = [("chain7", None), ("tree12", None), ("rand-chain5", (5, 3)), ("rand-chain8", (8, 6))]
+
+
+def _fdv_robot(key, spec):
+    return gi.robot(key) if spec is None else gi.random_tree(spec[0], spec[1], general=True, max_children=1)
+
+
+@pytest.mark.parametrize("key,spec", FDV, ids=[k for k, _ in FDV])
+@pytest.mark.parametrize("N", [1, 77])
+def test_lane_fd_and_vjp_match_oracle(grid, key, spec, N):
+    """FD and the vector-Jacobian product through FD with one lane per knot point
+    (lanes = 1) on chains and on the 12-DoF tree's legs: qdd against the oracle's
+    FD, and (dL/dq, dL/dqd, dL/dtau) for upstream gradients N(0, 1) against the
+    oracle's transpose products with the FD Jacobian and M^-1."""
+    r = _fdv_robot(key, spec)
+    n = r.n
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 51 + N)
+    gb = gi.upstream(n, N, 51 + N).astype(np.float32)
+    qdd = m.fd(q, qd, tau).cpu().numpy()
+    assert vec_rel_err(qdd, oracle.fd(r, q64, qd64, tau64)) <= TOL32
+    dq, dqd, dtau = (x.cpu().numpy() for x in m.fd_vjp(q, qd, tau, torch.from_numpy(gb).cuda()))
+    rq, rqd, rtau = oracle.fd_vjp(r, q64, qd64, tau64, gb.astype(np.float64))
+    tol = TOL32 if spec is None else float(fp32_bar(oracle.minv(r, q64)).max())
+    for x, y, name in ((dq, rq, "dq"), (dqd, rqd, "dqd"), (dtau, rtau, "dtau")):
+        assert vec_rel_err(x, y) <= tol, name
+    m.close()
+
+
+@pytest.mark.parametrize("key", ["chain7", "tree12"])
+def test_lane_fd_and_vjp_default_dispatch(grid, key):
+    """Above the switch-over size FD and the VJP of chains and of the 12-DoF tree's
+    legs take the one-lane kernel by default: equal to the forced lanes = 1 run, and
+    sampled knot points against the oracle."""
+    r = gi.robot(key)
+    n = r.n
+    m = grid.Model.from_robot(r)
+    one = grid.Model.from_robot(r)
+    one.set_option("lanes", 1)
+    N = 32768 + 11
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 23)
+    gb = torch.from_numpy(gi.upstream(n, N, 23).astype(np.float32)).cuda()
+    a = m.fd(q, qd, tau)
+    b = one.fd(q, qd, tau)
+    va = m.fd_vjp(q, qd, tau, gb)
+    vb = one.fd_vjp(q, qd, tau, gb)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and all(torch.equal(x, y) for x, y in zip(va, vb))
+    idx = np.unique(np.concatenate([np.sort(gi.Stream(29).u64(128) % np.uint64(N)).astype(np.int64), [0, N - 1]]))
+    ti = torch.from_numpy(idx).cuda()
+    assert vec_rel_err(a[ti].cpu().numpy(), oracle.fd(r, q64[idx], qd64[idx], tau64[idx])) <= TOL32
+    ref = oracle.fd_vjp(r, q64[idx], qd64[idx], tau64[idx], gb[ti].cpu().numpy().astype(np.float64))
+    for x, y in zip(va, ref):
+        assert vec_rel_err(x[ti].cpu().numpy(), y) <= TOL32
+    m.close()
+    one.close()
