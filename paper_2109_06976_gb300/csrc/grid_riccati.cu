@@ -223,11 +223,252 @@ __global__ void __launch_bounds__(128) riccati_kernel(
 }
 
 
+// The same backward pass for n <= 8 with one matrix column per lane: lanes
+// 0 .. m-1 own the state columns c (A[:, c], then V_xx A, Q_xx, Q_ux, K, Q_uu K and
+// the new V_xx, all columns c), lanes m .. m+n-1 the control columns (B, V_xx B,
+// Q_uu), lane m+n the feed-forward column (Q_u, k). A lane keeps its columns in
+// registers and reads the other operand of each product by broadcast from the
+// warp's shared memory (every lane reads the same entry), so a product is m
+// independent accumulations per lane; every lane factors Q_uu = L L^T itself in
+// registers. Same arithmetic, term for term, as riccati_kernel.
+template <class S, int NN>
+__global__ void __launch_bounds__(128) riccati_col_kernel(
+    int B, int H, S dt, const S* __restrict__ Q, const S* __restrict__ QD, const S* __restrict__ U,
+    const S* __restrict__ J, const S* __restrict__ Minv, const S* __restrict__ Qr, const S* __restrict__ QDr,
+    const S* __restrict__ wq, const S* __restrict__ wr, const S* __restrict__ wf, S mu, S* __restrict__ Ko,
+    S* __restrict__ kffo, S* __restrict__ dV) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int n = NN, m = 2 * NN;
+  static_assert(m + n + 1 <= 32, "one column per lane");
+  constexpr RicLayout R = ric_layout(NN, (int)sizeof(S));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  S* Wb = reinterpret_cast<S*>(smem) + warp * R.stride;
+  S* Vxx = Wb + R.Vxx; S* Vn = Wb + R.Vn; S* A = Wb + R.A; S* Bm = Wb + R.Bm; S* Quu = Wb + R.Quu;
+  S* Qux = Wb + R.Qux; S* Kk = Wb + R.Kk; S* Vx = Wb + R.Vx; S* Qu = Wb + R.Qu; S* kk = Wb + R.kk;
+  S* Qk = Wb + R.Qk; S* lx = Wb + R.lx; S* lu = Wb + R.lu;
+  const bool st_lane = lane < m, ct_lane = lane >= m && lane < m + n, ff_lane = lane == m + n;
+  const int cb = lane - m;
+  const size_t knots = (size_t)H + 1;
+  for (int b = blockIdx.x * wpb + warp; b < B; b += gridDim.x * wpb) {
+    const size_t kH = (size_t)b * knots + H;
+    GRID_LANES(e, m * m) Vxx[e] = (e / m == e % m) ? wf[e % m] : S(0);
+    GRID_LANES(i, m) {
+      const S x = i < n ? Q[kH * n + i] : QD[kH * n + i - n];
+      const S r = i < n ? Qr[kH * n + i] : QDr[kH * n + i - n];
+      Vx[i] = wf[i] * (x - r);
+    }
+    S dv0 = S(0), dv1 = S(0);
+    bool pd = true;
+    // this lane's entries of the next step's J, M^-1, states and controls, loaded
+    // one step ahead so that their latency overlaps the current step
+    constexpr int PJ = (n * m + 31) / 32, PM = (n * n + 31) / 32;
+    S pj[PJ], pm[PM], px = S(0), pr = S(0), pu = S(0);
+    auto fetch = [&](int kf) {
+      const size_t kb = (size_t)b * knots + kf;
+#pragma unroll
+      for (int u = 0; u < PJ; ++u) {
+        const int e = lane + 32 * u;
+        pj[u] = e < n * m ? J[kb * n * m + e] : S(0);
+      }
+#pragma unroll
+      for (int u = 0; u < PM; ++u) {
+        const int e = lane + 32 * u;
+        pm[u] = e < n * n ? Minv[kb * n * n + e] : S(0);
+      }
+      if (lane < m) {
+        px = lane < n ? Q[kb * n + lane] : QD[kb * n + lane - n];
+        pr = lane < n ? Qr[kb * n + lane] : QDr[kb * n + lane - n];
+      }
+      if (lane < n) pu = U[kb * n + lane];
+    };
+    fetch(H - 1);
+    __syncwarp();
+    for (int k = H - 1; k >= 0; --k) {
+      const size_t kb = (size_t)b * knots + k;
+#pragma unroll
+      for (int u = 0; u < PJ; ++u) {
+        const int e = lane + 32 * u;
+        if (e < n * m) {
+          const int i = e / m, j = e % m;
+          A[(n + i) * m + j] = dt * pj[u] + ((j == n + i) ? S(1) : S(0));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PM; ++u) {
+        const int e = lane + 32 * u;
+        if (e < n * n) Bm[n * n + e] = dt * pm[u];
+      }
+      if (lane < m) lx[lane] = wq[lane] * (px - pr);
+      if (lane < n) lu[lane] = wr[lane] * pu;
+      if (k > 0) fetch(k - 1);
+      __syncwarp();
+      GRID_LANES(e, n * m) {
+        const int i = e / m, j = e % m;
+        A[i * m + j] = ((j == i) ? S(1) : S(0)) + dt * A[(n + i) * m + j];
+      }
+      GRID_LANES(e, n * n) Bm[e] = dt * Bm[n * n + e];
+      __syncwarp();
+      // this lane's column of A (state lanes) or B (control lanes), and of V_xx times it
+      S a[m], col[m];
+#pragma unroll
+      for (int t = 0; t < m; ++t) a[t] = st_lane ? A[t * m + lane] : (ct_lane ? Bm[t * n + cb] : S(0));
+#pragma unroll
+      for (int r = 0; r < m; ++r) {
+        S s = S(0);
+#pragma unroll
+        for (int t = 0; t < m; ++t) s += Vxx[r * m + t] * a[t];
+        col[r] = s;
+      }
+      // Q columns: state lanes Q_xx[:, c] and Q_ux[:, c] (= B^T (V_xx A)[:, c]) and
+      // Q_x[c]; control lanes Q_uu[:, cb] and Q_u[cb]
+      S qcol[m], qux[n];
+#pragma unroll
+      for (int r = 0; r < m; ++r) {
+        S s = (st_lane && r == lane) ? wq[r] : S(0);
+#pragma unroll
+        for (int t = 0; t < m; ++t) s += A[t * m + r] * col[t];
+        qcol[r] = s;
+      }
+#pragma unroll
+      for (int r = 0; r < n; ++r) {
+        S s = (ct_lane && r == cb) ? wr[r] + mu : S(0);
+#pragma unroll
+        for (int t = 0; t < m; ++t) s += Bm[t * n + r] * col[t];
+        qux[r] = s;                                     // Q_ux[r][c] (state) or Q_uu[r][cb] (control)
+      }
+      S qv = S(0);                                      // Q_x[c] (state) or Q_u[cb] (control)
+      {
+        S s = st_lane ? lx[lane] : (ct_lane ? lu[cb] : S(0));
+#pragma unroll
+        for (int t = 0; t < m; ++t) s += a[t] * Vx[t];
+        qv = s;
+      }
+      if (st_lane) {
+#pragma unroll
+        for (int r = 0; r < n; ++r) Qux[r * m + lane] = qux[r];
+      }
+      if (ct_lane) {
+#pragma unroll
+        for (int r = 0; r < n; ++r) Quu[r * n + cb] = qux[r];
+        Qu[cb] = qv;
+      }
+      __syncwarp();
+      // Q_uu = L L^T in every lane (lower triangle of Q_uu as stored)
+      S qu[n * n], L[n * n], linv[n];
+#pragma unroll
+      for (int e = 0; e < n * n; ++e) qu[e] = Quu[e];
+      // (loops of fixed trip count with the triangle as a condition, so that they
+      // unroll completely and L stays in registers)
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        S d = qu[j * n + j];
+#pragma unroll
+        for (int t = 0; t < n; ++t)
+          if (t < j) d -= L[j * n + t] * L[j * n + t];
+        if (!(d > S(0))) { pd = false; d = S(1); }
+        const S li = rsqrtf(d);                         // 1 / L_jj (FP32 reciprocal square root)
+        const S ljj = d * li;
+        L[j * n + j] = ljj;
+        linv[j] = li;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+          if (i > j) {
+            S s = qu[i * n + j];
+#pragma unroll
+            for (int t = 0; t < n; ++t)
+              if (t < j) s -= L[i * n + t] * L[j * n + t];
+            L[i * n + j] = s * linv[j];
+          }
+        }
+      }
+      // K[:, c] = -Q_uu^-1 Q_ux[:, c] (state lanes), k = -Q_uu^-1 Q_u (feed-forward lane)
+      S y[n];
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        S s = ff_lane ? Qu[i] : qux[i];
+#pragma unroll
+        for (int t = 0; t < n; ++t)
+          if (t < i) s -= L[i * n + t] * y[t];
+        y[i] = s * linv[i];
+      }
+#pragma unroll
+      for (int ii = 0; ii < n; ++ii) {
+        const int i = n - 1 - ii;
+        S s = y[i];
+#pragma unroll
+        for (int t = 0; t < n; ++t)
+          if (t > i) s -= L[t * n + i] * y[t];
+        y[i] = s * linv[i];
+      }
+      S kc[n], qk[n];
+#pragma unroll
+      for (int i = 0; i < n; ++i) kc[i] = -y[i];
+#pragma unroll
+      for (int r = 0; r < n; ++r) {                     // Q_uu K[:, c] or Q_uu k
+        S s = S(0);
+#pragma unroll
+        for (int t = 0; t < n; ++t) s += qu[r * n + t] * kc[t];
+        qk[r] = s;
+      }
+      if (st_lane) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) { Kk[i * m + lane] = kc[i]; Ko[kb * n * m + i * m + lane] = kc[i]; }
+      }
+      if (ff_lane) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) { kk[i] = kc[i]; Qk[i] = qk[i]; kffo[kb * n + i] = kc[i]; }
+      }
+      __syncwarp();
+      if (ff_lane) {
+        S a0 = S(0), q2 = S(0);
+#pragma unroll
+        for (int t = 0; t < n; ++t) { a0 += kk[t] * Qu[t]; q2 += kk[t] * Qk[t]; }
+        dv0 += a0;
+        dv1 += S(0.5) * q2;
+      }
+      // V_x = Q_x + K^T Q_uu k + K^T Q_u + Q_ux^T k; V_xx columns before symmetrising
+      S vxn = S(0);
+      if (st_lane) {
+        S s = qv;
+#pragma unroll
+        for (int t = 0; t < n; ++t) s += kc[t] * Qk[t] + kc[t] * Qu[t] + qux[t] * kk[t];
+        vxn = s;
+#pragma unroll
+        for (int r = 0; r < m; ++r) {
+          S v = qcol[r];
+#pragma unroll
+          for (int t = 0; t < n; ++t) v += Kk[t * m + r] * qk[t] + Kk[t * m + r] * qux[t] + Qux[t * m + r] * kc[t];
+          Vn[r * m + lane] = v;
+        }
+      }
+      __syncwarp();
+      if (st_lane) {
+        Vx[lane] = vxn;
+#pragma unroll
+        for (int r = 0; r < m; ++r) Vxx[r * m + lane] = S(0.5) * (Vn[r * m + lane] + Vn[lane * m + r]);
+      }
+      __syncwarp();
+    }
+    if (ff_lane) {                                      // dv0 and dv1 were summed in this lane
+      dV[2 * (size_t)b] = pd ? dv0 : S(NAN);
+      dV[2 * (size_t)b + 1] = pd ? dv1 : S(NAN);
+    }
+    GRID_LANES(e, n * m) Ko[((size_t)b * knots + H) * n * m + e] = S(0);
+    GRID_LANES(i, n) kffo[((size_t)b * knots + H) * n + i] = S(0);
+    __syncwarp();
+  }
+}
+
 template <class S, int NN>
 grid_status launch_riccati_n(const grid_model* m, int B, int H, S dt, const S* Q, const S* QD, const S* U,
                              const S* J, const S* Minv, const S* Qr, const S* QDr, const S* wq, const S* wr,
                              const S* wf, S mu, S* K, S* kff, S* dV, cudaStream_t st) {
-  auto kern = riccati_kernel<S, NN>;
+  // FP32 and n <= 8: one matrix column per lane (riccati_col_kernel); otherwise
+  // lanes over matrix entries
+  auto kern = [] {
+    if constexpr (std::is_same<S, float>::value && NN <= 8) return riccati_col_kernel<S, NN>;
+    else return riccati_kernel<S, NN>;
+  }();
   const DevInfo di = dev_info(m->device);
   static std::atomic<int> opted{0};
   if (!opted.load()) {
