@@ -30,8 +30,9 @@ namespace {
 // qdd_k = FD(q_k, qd_k, u_k), qd_{k+1} = qd_k + dt qdd_k, q_{k+1} = q_k + dt qd_{k+1};
 // with a policy u_k = U_k + alpha kff_k + K_k (x_k - xnom_k). One knot slot of
 // a warp per trajectory (T lanes), the H steps in sequence; the state stays in
-// the slot's workspace between steps.
-template <class S, int T, int CPL, bool MIXED>
+// the slot's workspace between steps. CHAIN_N > 0: a serial chain of that many
+// bodies, whose topology the phases then take at compile time.
+template <class S, int T, int CPL, bool MIXED, int CHAIN_N = 0>
 __global__ void __launch_bounds__(128) rollout_kernel(
     const ModelDev<S>* __restrict__ gm, int B, int H, S dt, const S* __restrict__ q0,
     const S* __restrict__ qd0, const S* __restrict__ U, const S* __restrict__ K, const S* __restrict__ kff,
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(128) rollout_kernel(
   }
   __syncthreads();
   using P = typename std::conditional<MIXED, double, S>::type;
-  using Tp = RtTopo<S, MODE_FD>;
+  using Tp = topo_for<S, MODE_FD, CHAIN_N>;
   const ModelDev<S>& M = *reinterpret_cast<const ModelDev<S>*>(smem);
   const Tp tp(M);
   const KnotLayout& L = tp.layout();
@@ -121,11 +122,17 @@ bool pick_launch(Kern kern, int dev_optin, size_t fixed, size_t per_warp, int& w
   return warps > 0;
 }
 
-template <class S, int T, int CPL, bool MIXED>
+template <class S, int T, int CPL, bool MIXED, int CHAIN_N = 0>
 grid_status launch_rollout(const grid_model* m, const ModelDev<S>* hm, const ModelDev<S>* dm, int B, int H, S dt,
                            const S* q0, const S* qd0, const S* U, const S* K, const S* kff, const S* Qn,
                            const S* QDn, S alpha, S* Q, S* QD, S* Uout, cudaStream_t st) {
-  auto kern = rollout_kernel<S, T, CPL, MIXED>;
+  auto kern = rollout_kernel<S, T, CPL, MIXED, CHAIN_N>;
+  if constexpr (CHAIN_N > 0) {               // the compile-time layout must be the one the host built
+    if (hm->n != CHAIN_N || ChainTopo<S, MODE_FD, CHAIN_N>::layout().stride != hm->LS.stride) {
+      grid_set_error("rollout chain kernel for %d bodies does not match the model", CHAIN_N);
+      return GRID_E_TOPOLOGY;
+    }
+  }
   const DevInfo di = dev_info(m->device);
   static std::atomic<int> opted{0};
   if (!opted.load()) {
@@ -165,8 +172,19 @@ grid_status rollout_dispatch(const grid_model* m, int B, int H, S dt, const S* q
   else { hm = m->host_d; dm = m->dev_d; }
   const int n = hm->n;
   int T = m->lanes_opt;
-  if (T == 0) T = n <= 12 ? 8 : 16;
+  if (T == 0 || T == 1) T = n <= 12 ? 8 : 16;
   const int cpl = (n + T - 1) / T;
+  // serial chains of 2 .. 8 bodies: the chain topology at compile time (8 lanes)
+  if (!MIXED && m->chain && m->specialize_opt && T == 8 && n >= 2 && n <= kChainMaxN) {
+    switch (n) {
+#define GRID_RLC(NB) \
+      case NB: return launch_rollout<S, 8, 1, MIXED, NB>(m, hm, dm, B, H, dt, q0, qd0, U, K, kff, Qn, QDn, alpha, \
+                                                          Q, QD, Uout, st);
+      GRID_RLC(2) GRID_RLC(3) GRID_RLC(4) GRID_RLC(5) GRID_RLC(6) GRID_RLC(7) GRID_RLC(8)
+#undef GRID_RLC
+      default: break;
+    }
+  }
 #define GRID_RL(TT, CC) return launch_rollout<S, TT, CC, MIXED>(m, hm, dm, B, H, dt, q0, qd0, U, K, kff, Qn, QDn, \
                                                                   alpha, Q, QD, Uout, st)
   if (T == 8) { if (cpl <= 1) GRID_RL(8, 1); if (cpl <= 2) GRID_RL(8, 2); GRID_RL(8, 4); }
