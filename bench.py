@@ -269,6 +269,30 @@ def batched_leg(grid, name, precision, knots, steps, peaks, stream, dist, seed=3
             "peak_kind": "fp64 measured" if precision == "fp64" else "fp32 measured"}
 
 
+def entry_points_leg(grid, stream, dist, steps=5):
+    """Batched throughput of every entry point (RNEA at given accelerations, M^-1,
+    FD, the gradient of ID and of FD) for the 7-DoF chain (2,097,152 knot points)
+    and the 12-DoF tree (1,048,576), FP32, one launch per step."""
+    import torch
+    out = {}
+    for name, N in (("chain7", 16384 * KNOTS), ("tree12", 8192 * KNOTS)):
+        r = gi.robot(name)
+        n = r.n
+        m = grid.Model.from_robot(r)
+        q, qd, tau = (torch.from_numpy(x.astype(np.float32)).cuda() for x in gi.states(n, N, 41))
+        T = torch.empty((N, n), device="cuda")
+        Mi = torch.empty((N, n, n), device="cuda")
+        D = torch.empty((N, n, 2 * n), device="cuda")
+        calls = {"rnea": lambda: m.rnea(q, qd, tau, out=T), "minv": lambda: m.minv(q, out=Mi),
+                 "fd": lambda: m.fd(q, qd, tau, out=T), "grad_id": lambda: m.grad_rnea(q, qd, tau, out=D),
+                 "grad_fd": lambda: m.grad_fd(q, qd, tau, out=D)}
+        out[name] = {k: N * steps / time_steps(fn, steps, 2, stream, dist) for k, fn in calls.items()}
+        out[name]["knot_points_per_launch"] = N
+        m.close()
+    out["unit"] = UNIT
+    return out
+
+
 def traj_leg(grid, model, stream, dist, B=2048, H=64, dt=0.01):
     """One iLQR iteration on the device for B trajectories of H steps of the
     7-DoF chain (rollout, gradient of FD and M^-1 at the B (H+1) knot points,
@@ -652,6 +676,7 @@ def run_ours(args):
     lat_table = latency_table(grid) if rank == 0 else None
     sweep = n_sweep(grid) if rank == 0 else None
     vjp = vjp_leg(grid, stream, dist) if rank == 0 and world == 1 else None
+    entry = entry_points_leg(grid, stream, dist) if rank == 0 and world == 1 else None
     traj = traj_leg(grid, model, stream, dist) if rank == 0 and world == 1 else None
 
     serve = None
@@ -730,6 +755,7 @@ def run_ours(args):
                                "(RNEA at qdd = tau's values; FP32, and the 30-DoF tree also in mixed precision)",
             "traj_step": traj,
             "vjp": vjp,
+            "entry_points": entry,
             "serve": serve,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgrid_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["grid_capi.cu", "grid_f32.cu", "grid_mixed.cu", "grid_f64.cu", "grid_chain.cu", "grid_lane_chain.cu", "grid_lane_chain_fdv.cu", "grid_chain_part.cu", "grid_forest.cu",
+SOURCES = ["grid_capi.cu", "grid_f32.cu", "grid_mixed.cu", "grid_f64.cu", "grid_chain.cu", "grid_lane_chain.cu", "grid_lane_chain_fdv.cu", "grid_lane_chain_id.cu", "grid_chain_part.cu", "grid_forest.cu",
            "grid_serve.cu", "grid_traj.cu", "grid_riccati.cu", "grid_peak.cu", "grid_host.cpp", "grid_nvrtc.cpp"]
 # Device headers embedded for run-time compilation (name as included -> file)
 EMBED = [("grid_kernel.cuh", "grid_kernel.cuh"), ("grid_phases.cuh", "grid_phases.cuh"),

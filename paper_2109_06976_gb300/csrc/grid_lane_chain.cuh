@@ -161,7 +161,7 @@ __device__ __forceinline__ void lc_load_body(const LcWs& w, int i, LcBody& b) {
 // the case terms at the column's own joint. The next body's record is loaded
 // before the current body's arithmetic, so that the shared-memory latency
 // overlaps it.
-template <int NB, bool PL>
+template <int NB, bool PL, bool DC = false>
 __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int j, bool uq, const float* Mi,
                                           float* __restrict__ Jk) {
   constexpr int PB = 7;
@@ -236,10 +236,14 @@ __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int 
   const int col = (uq ? 0 : ld) + (PL ? P.slot[j] : j);
 #pragma unroll
   for (int rr = 0; rr < NB; ++rr) {
-    float acc = 0.0f;
+    if constexpr (DC) {                                // the gradient of ID itself (no product)
+      if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = dc[rr];
+    } else {
+      float acc = 0.0f;
 #pragma unroll
-    for (int m = 0; m < NB; ++m) acc += Mi[lc_tri<NB>(rr, m)] * dc[m];
-    if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = -acc;
+      for (int m = 0; m < NB; ++m) acc += Mi[lc_tri<NB>(rr, m)] * dc[m];
+      if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = -acc;
+    }
   }
 }
 
@@ -338,9 +342,105 @@ __device__ __forceinline__ void lc_vjp(const LcParams& P, const LcWs& w, long k,
   }
 }
 
+// RNEA at a given qdd (NULL for zero) and, for MODE_GRAD_ID, the derivative
+// columns of Alg. 1 at that qdd without the product with M^-1 (no M^-1 is
+// formed): tau (MODE_RNEA) or D = [dID/dq | dID/dqd] (MODE_GRAD_ID) at the
+// chain's caller joints. The records are those of the gradient of FD (E, v, qd,
+// then X a_parent and f, then beta and phi).
+template <int NB, bool PL, int MODE>
+__device__ __forceinline__ void lc_id(const LcParams& P, const LcWs& w, long k, int ld, const float* __restrict__ q,
+                                      const float* __restrict__ qd, const float* __restrict__ qdd,
+                                      float* __restrict__ out) {
+  constexpr int PB = 7;
+  {
+    float vp[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, ap[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) ap[e] = P.a0[e];
+#pragma unroll 1
+    for (int i = 0; i < NB; ++i) {
+      const long gi = k * ld + (PL ? P.slot[i] : i);
+      float E[9];
+      lc_transform(P, i, __ldg(q + gi), E);
+      const float qdi = __ldg(qd + gi), qddi = qdd ? __ldg(qdd + gi) : 0.0f;
+      const float* a = P.axis[i];
+      const float* r = P.rT[i];
+      const float* in = P.inert[i];
+      const float sq[3] = {a[0] * qdi, a[1] * qdi, a[2] * qdi};   // S qd
+      float v[6], Xa[6], acc[6], g[6], f[6];
+      x_mul(E, r, vp, v);                              // v_parent = 0 at the base
+      v[0] += sq[0]; v[1] += sq[1]; v[2] += sq[2];
+      x_mul(E, r, ap, Xa);                             // a_parent = a_0 at the base
+#pragma unroll
+      for (int e = 0; e < 6; ++e) acc[e] = Xa[e];
+      {
+        const float vj[6] = {sq[0], sq[1], sq[2], 0.0f, 0.0f, 0.0f};
+        crm_mul_acc(v, vj, acc);                       // a = X a_parent + v x S qd + S qdd
+      }
+      acc[0] += a[0] * qddi; acc[1] += a[1] * qddi; acc[2] += a[2] * qddi;
+      i_mul(in, v, g);
+      i_mul(in, acc, f);
+      crf_mul_acc(v, g, f);
+      w.f4(PB * i) = make_float4(E[0], E[1], E[2], E[3]);
+      w.f4(PB * i + 1) = make_float4(E[4], E[5], E[6], E[7]);
+      w.f4(PB * i + 2) = make_float4(v[0], v[1], v[2], v[3]);
+      w.f4(PB * i + 3) = make_float4(v[4], v[5], E[8], qdi);
+      w.f4(PB * i + 4) = make_float4(Xa[0], Xa[1], Xa[2], Xa[3]);
+      w.f4(PB * i + 5) = make_float4(f[0], f[1], f[2], f[3]);
+      w.f4(PB * i + 6) = make_float4(Xa[4], Xa[5], f[4], f[5]);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) { vp[e] = v[e]; ap[e] = acc[e]; }
+    }
+  }
+  // backward: F_i = f_i + X_{i+1}^T F_{i+1}; tau_i = S_i^T F_i, or beta_i =
+  // (X_i a_parent) x S_i and phi_i = S_i x* F_i into the records
+  float F[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+  for (int i = NB - 1; i >= 0; --i) {
+    const float4 x0 = w.f4(PB * i + 4), f0 = w.f4(PB * i + 5), x2 = w.f4(PB * i + 6);
+    float t[6];
+    if (i + 1 < NB) {
+      float E[9];
+      lc_load_E<PB>(w, i + 1, E);
+      xt_mul(E, P.rT[i + 1], F, t);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) t[e] = 0.0f;
+    }
+    F[0] = f0.x + t[0]; F[1] = f0.y + t[1]; F[2] = f0.z + t[2]; F[3] = f0.w + t[3];
+    F[4] = x2.z + t[4]; F[5] = x2.w + t[5];
+    const float* a = P.axis[i];
+    if constexpr (MODE == MODE_RNEA) {
+      out[k * ld + (PL ? P.slot[i] : i)] = dot_s(a, false, F);
+    } else {
+      const float Xa[6] = {x0.x, x0.y, x0.z, x0.w, x2.x, x2.y};
+      float beta[6], ph[6];
+      cross_s(Xa, a, false, beta);
+      crf_s(a, false, F, ph);
+      w.f4(PB * i + 4) = make_float4(beta[0], beta[1], beta[2], beta[3]);
+      w.f4(PB * i + 5) = make_float4(ph[0], ph[1], ph[2], ph[3]);
+      w.f4(PB * i + 6) = make_float4(beta[4], beta[5], ph[4], ph[5]);
+    }
+  }
+  if constexpr (MODE == MODE_GRAD_ID) {
+    float* Dk = out + k * 2 * ld * ld;
+#pragma unroll 1
+    for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL, true>(P, w, c >> 1, (c & 1) == 0, nullptr, Dk);
+    if (PL && P.zero_fill) {                           // the chain's rows of D: zeros beside its blocks
+#pragma unroll 1
+      for (int rr = 0; rr < NB; ++rr) {
+        float* row = Dk + P.slot[rr] * 2 * ld;
+        for (int cc = 0; cc < 2 * ld; ++cc)
+          if (!((P.mask >> (cc < ld ? cc : cc - ld)) & 1u)) row[cc] = 0.0f;
+      }
+    }
+  }
+}
+
 // The phases for one knot point. MODE_GRAD: x3 = tau, out = J, out2 = qdd (or
 // NULL), out3 = M^-1 (or NULL). MODE_FD: x3 = tau, out = qdd. MODE_VJP: x3 = tau,
-// x4 = gbar = dL/dqdd, out = dL/dq, out2 = dL/dqd, out3 = dL/dtau.
+// x4 = gbar = dL/dqdd, out = dL/dq, out2 = dL/dqd, out3 = dL/dtau. MODE_MINV:
+// out = M^-1. MODE_RNEA: x3 = qdd (or NULL), out = tau. MODE_GRAD_ID: x3 = qdd
+// (or NULL), out = [dID/dq | dID/dqd].
 template <int NB, bool PL, int MODE>
 __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k, const float* __restrict__ q,
                                         const float* __restrict__ qd, const float* __restrict__ x3,
@@ -350,7 +450,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
   const float* tau = x3;
   float* J = MODE == MODE_GRAD ? out : nullptr;
   float* qdd_out = MODE == MODE_GRAD ? out2 : (MODE == MODE_FD ? out : nullptr);
-  float* minv_out = MODE == MODE_GRAD ? out3 : nullptr;
+  float* minv_out = MODE == MODE_GRAD ? out3 : (MODE == MODE_MINV ? out : nullptr);
   // ---- a2 + a4: transforms and the backward sweep of the direct M^-1
   //   I^A_i = I_i + X_{i+1}^T (I^A_{i+1} - U_{i+1} D_{i+1}^-1 U_{i+1}^T) X_{i+1}
   //   U_i = I^A_i S_i, D_i = S_i^T U_i, Minv[i][i] = D_i^-1,
@@ -359,6 +459,10 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
   // compile time, which keeps the code small. A placed chain (PL) reads and
   // writes the caller joints slot[i] of knot points of ld joints.
   const int ld = PL ? P.ld : NB;
+  if constexpr (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) {
+    lc_id<NB, PL, MODE>(P, w, k, ld, q, qd, x3, out);
+    return;
+  }
   {
     float Fc[NB][6], carry[6][6];
 #pragma unroll
@@ -374,7 +478,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
       float E[9];
       const long gi = k * ld + (PL ? P.slot[i] : i);
       lc_transform(P, i, __ldg(q + gi), E);
-      const float qdi = __ldg(qd + gi);
+      const float qdi = MODE == MODE_MINV ? 0.0f : __ldg(qd + gi);
       w.f4(PB * i) = make_float4(E[0], E[1], E[2], E[3]);
       w.f4(PB * i + 1) = make_float4(E[4], E[5], E[6], E[7]);
       const float* a = P.axis[i];
@@ -511,6 +615,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
       }
     }
   }
+  if constexpr (MODE == MODE_MINV) return;
   // ---- a3: RNEA(q, qd, 0); X_i a_parent in B0 / B2.xy and f_i in B1 / B2.zw
   {
     float vp[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, ap[6];

@@ -174,6 +174,16 @@ grid_status launch_lane_chain_fd(const grid_model* m, const ModelDev<float>* hm,
 grid_status launch_lane_chain_vjp(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                                   const float* q, const float* qd, const float* tau, const float* gbar, float* dq,
                                   float* dqd, float* dtau, cudaStream_t st);
+// RNEA (qdd NULL for zero), M^-1 and the gradient of ID in the same form
+// (grid_lane_chain_id.cu); without zero_fill a placed chain leaves the zeros beside
+// its blocks of M^-1 or D to the caller.
+grid_status launch_lane_chain_rnea(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
+                                   const float* q, const float* qd, const float* qdd, float* tau, cudaStream_t st);
+grid_status launch_lane_chain_minv(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
+                                   const float* q, float* Minv, cudaStream_t st, bool zero_fill);
+grid_status launch_lane_chain_grad_id(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot,
+                                      int N, const float* q, const float* qd, const float* qdd, float* D,
+                                      cudaStream_t st, bool zero_fill);
 // Batches from this many knot points up take the one-lane-per-knot-point chain
 // kernel by default (below, the 8-lane kernel has the shorter latency).
 constexpr int kLaneChainMinN = 32768;
@@ -250,9 +260,11 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   // FD of FP32 serial chains), automatic elsewhere
   const int T = m->lanes_opt == 1 ? 0 : m->lanes_opt;
   const int n = hm->n;
-  if constexpr ((MODE == MODE_FD || MODE == MODE_VJP) && !MIXED && std::is_same<S, float>::value) {
-    // FD and the vector-Jacobian product of chains and of a forest's legs, one lane
-    // per knot point (each leg writes its joints' entries of the vector outputs)
+  if constexpr (MODE != MODE_GRAD && !MIXED && std::is_same<S, float>::value) {
+    // RNEA, M^-1, FD, the gradient of ID and the vector-Jacobian product of chains
+    // and of a forest's legs, one lane per knot point (each leg writes its joints'
+    // entries of the vector outputs and its blocks of the matrix outputs, which
+    // are cleared first)
     bool lane1 = m->specialize_opt && (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN));
     if (lane1 && m->lanes_opt == 0) {
       cudaPointerAttributes pa{};
@@ -265,11 +277,23 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
     }
     auto one = [&](const ModelDev<float>* mh, const int* slot) {
       if constexpr (MODE == MODE_FD) return launch_lane_chain_fd(m, mh, n, slot, N, q, qd, x3, out, st);
-      else return launch_lane_chain_vjp(m, mh, n, slot, N, q, qd, x3, x4, out, out2, out3, st);
+      else if constexpr (MODE == MODE_VJP)
+        return launch_lane_chain_vjp(m, mh, n, slot, N, q, qd, x3, x4, out, out2, out3, st);
+      else if constexpr (MODE == MODE_RNEA) return launch_lane_chain_rnea(m, mh, n, slot, N, q, qd, x3, out, st);
+      else if constexpr (MODE == MODE_MINV) return launch_lane_chain_minv(m, mh, n, slot, N, q, out, st, false);
+      else return launch_lane_chain_grad_id(m, mh, n, slot, N, q, qd, x3, out, st, false);
     };
     if (lane1 && m->chain && n >= 2 && n <= kChainMaxN) return one(hm, nullptr);
     if (lane1 && m->forest_k > 1 && m->branches == m->forest_k && m->forest_l >= 2 && m->forest_l <= kChainMaxN &&
         n <= 32) {
+      if constexpr (MODE == MODE_MINV || MODE == MODE_GRAD_ID) {
+        const size_t per = MODE == MODE_MINV ? (size_t)n * n : (size_t)2 * n * n;
+        const cudaError_t e = cudaMemsetAsync(out, 0, (size_t)N * per * sizeof(float), st);
+        if (e != cudaSuccess) {
+          grid_set_error("clearing the outputs: %s", cudaGetErrorString(e));
+          return GRID_E_CUDA;
+        }
+      }
       int slot[kChainMaxN];
       for (int c = 0; c < m->forest_k; ++c) {
         for (int i = 0; i < m->forest_l; ++i) slot[i] = c * m->forest_l + i;

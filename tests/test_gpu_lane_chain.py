@@ -307,3 +307,67 @@ def test_lane_fd_and_vjp_default_dispatch(grid, key):
         assert vec_rel_err(x[ti].cpu().numpy(), y) <= TOL32
     m.close()
     one.close()
+
+
+@pytest.mark.parametrize("key,spec", FDV, ids=[k for k, _ in FDV])
+@pytest.mark.parametrize("N", [1, 77])
+def test_lane_rnea_minv_grad_id_match_oracle(grid, key, spec, N):
+    """RNEA (with accelerations given and with zero), M^-1 and the gradient of ID
+    with one lane per knot point (lanes = 1) on chains and on the 12-DoF tree's
+    legs, outputs pre-filled with NaN: every entry written, against the oracle,
+    M^-1 exactly symmetric."""
+    r = _fdv_robot(key, spec)
+    n = r.n
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 61 + N)
+    nan = lambda *shape: torch.full(shape, float("nan"), device="cuda")
+    t1 = m.rnea(q, qd, tau, out=nan(N, n)).cpu().numpy()              # tau's values as accelerations
+    t0 = m.rnea(q, qd, out=nan(N, n)).cpu().numpy()
+    Mi = m.minv(q, out=nan(N, n, n)).cpu().numpy()
+    D = m.grad_rnea(q, qd, tau, out=nan(N, n, 2 * n)).cpu().numpy()
+    for x in (t1, t0, Mi, D):
+        assert np.isfinite(x).all()
+    assert vec_rel_err(t1, oracle.rnea(r, q64, qd64, tau64)) <= TOL32
+    assert vec_rel_err(t0, oracle.rnea(r, q64, qd64, 0 * qd64)) <= TOL32
+    mref = oracle.minv(r, q64)
+    assert col_rel_err(Mi, mref, FLOOR32) <= (TOL32 if spec is None else float(fp32_bar(mref).max()))
+    np.testing.assert_array_equal(Mi, np.swapaxes(Mi, 1, 2))
+    rq, rqd = oracle.grad_rnea(r, q64, qd64, tau64)
+    assert col_rel_err(D, np.concatenate([rq, rqd], axis=2), FLOOR32) <= TOL32
+    if key == "tree12":                                   # exact zeros between the legs
+        for c in range(4):
+            jm = np.ones(24, bool)
+            jm[3 * c:3 * c + 3] = jm[12 + 3 * c:12 + 3 * c + 3] = False
+            mm = np.ones(12, bool)
+            mm[3 * c:3 * c + 3] = False
+            rows = slice(3 * c, 3 * c + 3)
+            assert np.all(D[:, rows][:, :, jm] == 0) and np.all(Mi[:, rows][:, :, mm] == 0)
+    m.close()
+
+
+@pytest.mark.parametrize("key", ["chain7", "tree12"])
+def test_lane_rnea_minv_grad_id_default_dispatch(grid, key):
+    """Above the switch-over size RNEA, M^-1 and the gradient of ID of chains and
+    of the 12-DoF tree's legs take the one-lane kernel by default: equal to the
+    forced lanes = 1 run, and sampled knot points against the oracle."""
+    r = gi.robot(key)
+    n = r.n
+    m = grid.Model.from_robot(r)
+    one = grid.Model.from_robot(r)
+    one.set_option("lanes", 1)
+    N = 32768 + 5
+    (q, qd, tau), (q64, qd64, tau64) = _inputs(n, N, 27)
+    outs = [(m.rnea(q, qd, tau), one.rnea(q, qd, tau)), (m.minv(q), one.minv(q)),
+            (m.grad_rnea(q, qd, tau), one.grad_rnea(q, qd, tau))]
+    torch.cuda.synchronize()
+    for a, b in outs:
+        assert torch.equal(a, b)
+    idx = np.unique(np.concatenate([np.sort(gi.Stream(31).u64(96) % np.uint64(N)).astype(np.int64), [0, N - 1]]))
+    ti = torch.from_numpy(idx).cuda()
+    assert vec_rel_err(outs[0][0][ti].cpu().numpy(), oracle.rnea(r, q64[idx], qd64[idx], tau64[idx])) <= TOL32
+    assert col_rel_err(outs[1][0][ti].cpu().numpy(), oracle.minv(r, q64[idx]), FLOOR32) <= TOL32
+    rq, rqd = oracle.grad_rnea(r, q64[idx], qd64[idx], tau64[idx])
+    assert col_rel_err(outs[2][0][ti].cpu().numpy(), np.concatenate([rq, rqd], axis=2), FLOOR32) <= TOL32
+    m.close()
+    one.close()
