@@ -121,10 +121,13 @@ int grid_model_dof(const grid_model* model);
 /*
  * grid_set_option -- tuning knobs (not needed for correctness).
  *   "lanes"       threads cooperating on one knot point: 0 = automatic, 1, 8, 16 or 32.
- *                 1: the gradient of FD of an FP32 serial chain of 2 to 8 revolute
- *                 bodies runs with one lane per knot point (the form that batches
- *                 of 32768 knot points or more take by default); elsewhere 1 acts
- *                 as 0
+ *                 1: the float entry points (RNEA, M^-1, FD, gradients of ID and FD,
+ *                 the vector-Jacobian product) of a serial chain of 2 to 8 revolute
+ *                 bodies, and of a forest of such chains on the fixed base (each
+ *                 chain in turn), run with one lane per knot point: the form that
+ *                 batches of 32768 knot points or more take by default (not for
+ *                 outputs in host memory); the gradient of FD also for chain
+ *                 components of robots that run as parts. Elsewhere 1 acts as 0
  *   "precision"   GRID_FP32 or GRID_MIXED for the float entry points
  *   "ctas_per_sm" resident CTAs per SM the launcher sizes the grid for (0 = auto)
  *   "specialize"  1 (default): serial chains (parent[i] = i - 1) of 2 to 8 bodies,
