@@ -131,6 +131,29 @@ __device__ __forceinline__ constexpr int lc_tri(int r, int c) {
   return r <= c ? r * NB - r * (r - 1) / 2 + (c - r) : c * NB - c * (c - 1) / 2 + (r - c);
 }
 
+// Zeros into the entries of row[0 .. len) whose bit in keep is clear (the entries
+// of the robot's other components), with one 16-byte store where four such entries
+// fill an aligned 16-byte word. The row is 4-byte aligned (the C-ABI checks it);
+// len <= 64.
+__device__ __forceinline__ void lc_zero_beside(float* row, int len, unsigned long long keep) {
+  const int head = min(len, (int)(((16u - ((unsigned)(uintptr_t)row & 15u)) & 15u) >> 2));
+  int e = 0;
+  for (; e < head; ++e)
+    if (!((keep >> e) & 1ull)) row[e] = 0.0f;
+  for (; e + 4 <= len; e += 4) {
+    const unsigned m4 = (unsigned)(keep >> e) & 0xFu;
+    if (m4 == 0u) {
+      *reinterpret_cast<float4*>(row + e) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (!((m4 >> t) & 1u)) row[e + t] = 0.0f;
+    }
+  }
+  for (; e < len; ++e)
+    if (!((keep >> e) & 1ull)) row[e] = 0.0f;
+}
+
 // One derivative column (u, j), u = q when uq: the forward pass over bodies
 // j .. n-1, the backward pass down to the base (dc_i for every body), then
 // J[:, col] = -M^-1 dc. The loops run over the bodies at compile time (the
@@ -426,12 +449,9 @@ __device__ __forceinline__ void lc_id(const LcParams& P, const LcWs& w, long k, 
 #pragma unroll 1
     for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL, true>(P, w, c >> 1, (c & 1) == 0, nullptr, Dk);
     if (PL && P.zero_fill) {                           // the chain's rows of D: zeros beside its blocks
+      const unsigned long long keep = (unsigned long long)P.mask | ((unsigned long long)P.mask << ld);
 #pragma unroll 1
-      for (int rr = 0; rr < NB; ++rr) {
-        float* row = Dk + P.slot[rr] * 2 * ld;
-        for (int cc = 0; cc < 2 * ld; ++cc)
-          if (!((P.mask >> (cc < ld ? cc : cc - ld)) & 1u)) row[cc] = 0.0f;
-      }
+      for (int rr = 0; rr < NB; ++rr) lc_zero_beside(Dk + P.slot[rr] * 2 * ld, 2 * ld, keep);
     }
   }
 }
@@ -609,10 +629,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
       float* row = minv_out + (k * ld + (PL ? P.slot[i] : i)) * ld;
 #pragma unroll
       for (int kk = 0; kk < NB; ++kk) row[PL ? P.slot[kk] : kk] = Mi[lc_tri<NB>(i, kk)];
-      if (PL && P.zero_fill) {                         // zeros beside the chain's block
-        for (int cc = 0; cc < ld; ++cc)
-          if (!((P.mask >> cc) & 1u)) row[cc] = 0.0f;
-      }
+      if (PL && P.zero_fill) lc_zero_beside(row, ld, P.mask);   // zeros beside the chain's block
     }
   }
   if constexpr (MODE == MODE_MINV) return;
@@ -750,12 +767,9 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
 #pragma unroll 1
   for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL>(P, w, c >> 1, (c & 1) == 0, Mi, Jk);
   if (PL && P.zero_fill) {                             // the chain's rows of J: zeros beside its blocks
+    const unsigned long long keep = (unsigned long long)P.mask | ((unsigned long long)P.mask << ld);
 #pragma unroll 1
-    for (int rr = 0; rr < NB; ++rr) {
-      float* row = Jk + P.slot[rr] * 2 * ld;
-      for (int cc = 0; cc < 2 * ld; ++cc)
-        if (!((P.mask >> (cc < ld ? cc : cc - ld)) & 1u)) row[cc] = 0.0f;
-    }
+    for (int rr = 0; rr < NB; ++rr) lc_zero_beside(Jk + P.slot[rr] * 2 * ld, 2 * ld, keep);
   }
 }
 

@@ -321,8 +321,10 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
       return launch_lane_chain(m, hm, n, nullptr, N, q, qd, x3, out, out2, out3, st);
     // a forest with one model per chain: the outputs cleared, then each chain (a
     // leg) in turn, one lane per (knot point, leg), writing its blocks of J and
-    // M^-1 and its entries of qdd (scattered zero stores from every lane measured
-    // slower than one clearing pass over the outputs)
+    // M^-1 and its entries of qdd (each leg writing its whole rows, zeros included,
+    // measured slower than one clearing pass over the outputs: 1.67 against
+    // 1.52 ms for the 12-DoF tree on 1,048,576 knot points, with the zeros in
+    // 16-byte stores)
     if (lane1 && m->forest_k > 1 && m->branches == m->forest_k && m->forest_l >= 2 && m->forest_l <= kChainMaxN &&
         n <= 32) {
       cudaError_t e = cudaMemsetAsync(out, 0, (size_t)N * 2 * n * n * sizeof(float), st);

@@ -197,6 +197,42 @@ def test_lane_chain_placed_components(grid, key, N):
     m.close()
 
 
+@pytest.mark.parametrize("key", ["tree12", "tree30", "rand13"])
+@pytest.mark.parametrize("offset", [1, 2, 3])
+def test_lane_chain_placed_outputs_off_16_bytes(grid, key, offset):
+    """Placed legs write the zeros beside their blocks with 16-byte stores where
+    the words are aligned and scalar stores at the rows' ends: outputs that start
+    1 .. 3 floats past a 16-byte boundary (NaN-filled around them) give the same
+    J, M^-1 and gradient of ID as aligned ones, and nothing outside is written."""
+    r = PLACED[key]()
+    n = r.n
+    m = grid.Model.from_robot(r)
+    m.set_option("lanes", 1)
+    N = 77
+    (q, qd, tau), _ = _inputs(n, N, 71 + offset)
+
+    def view(shape):
+        size = int(np.prod(shape))
+        buf = torch.full((size + 8,), float("nan"), device="cuda")
+        return buf, buf[offset:offset + size].view(shape)
+
+    bj, J = view((N, n, 2 * n))
+    bm, Mi = view((N, n, n))
+    bd, D = view((N, n, 2 * n))
+    bi, M2 = view((N, n, n))
+    m.grad_fd_minv(q, qd, tau, out=J, minv_out=Mi)
+    m.grad_rnea(q, qd, tau, out=D)
+    m.minv(q, out=M2)
+    J0, Mi0 = m.grad_fd_minv(q, qd, tau)
+    D0, M20 = m.grad_rnea(q, qd, tau), m.minv(q)
+    torch.cuda.synchronize()
+    for b, x, x0 in ((bj, J, J0), (bm, Mi, Mi0), (bd, D, D0), (bi, M2, M20)):
+        assert torch.equal(x, x0)
+        hb = b.cpu().numpy()
+        assert np.isnan(hb[:offset]).all() and np.isnan(hb[offset + x.numel():]).all()
+    m.close()
+
+
 @pytest.mark.parametrize("key", ["tree12", "tree30"])
 def test_lane_chain_placed_default_dispatch(grid, key):
     """Above the switch-over size the quadruped's legs and the humanoid's leg
