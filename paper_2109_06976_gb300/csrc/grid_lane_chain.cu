@@ -4,6 +4,6 @@
 
 grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                               const float* q, const float* qd, const float* tau, float* J, float* qdd,
-                              float* Minv, cudaStream_t st, bool zero_fill) {
-  return lc_run<MODE_GRAD>(m, hm, ld, slot, N, q, qd, tau, nullptr, J, qdd, Minv, st, zero_fill);
+                              float* Minv, cudaStream_t st) {
+  return lc_run<MODE_GRAD>(m, hm, ld, slot, N, q, qd, tau, nullptr, J, qdd, Minv, st);
 }

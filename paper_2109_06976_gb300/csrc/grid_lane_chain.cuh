@@ -13,7 +13,9 @@
 // stops after qdd; the vector-Jacobian product replaces the columns by one
 // adjoint sweep.
 //
-// The lanes never exchange data: no shuffles and no warp barriers. What a lane
+// The lanes exchange no data while they compute (no shuffles, no warp barriers;
+// only a chain placed in a larger robot hands its blocks of J and M^-1 to the
+// warp at the end, for whole-row stores). What a lane
 // keeps between phases (its transforms, velocities, the case-term vectors beta
 // and phi, the M^-1 temporaries) sits in shared memory in a lane-major layout:
 // slot s of lane t of a warp is element s * 32 + t of the warp's area, so a
@@ -50,7 +52,6 @@ struct LcParams {
   int ld;
   int slot[kLcMaxB];
   unsigned mask;
-  int zero_fill;              // write the zeros beside the chain's blocks (else the caller has)
 };
 
 
@@ -131,29 +132,6 @@ __device__ __forceinline__ constexpr int lc_tri(int r, int c) {
   return r <= c ? r * NB - r * (r - 1) / 2 + (c - r) : c * NB - c * (c - 1) / 2 + (r - c);
 }
 
-// Zeros into the entries of row[0 .. len) whose bit in keep is clear (the entries
-// of the robot's other components), with one 16-byte store where four such entries
-// fill an aligned 16-byte word. The row is 4-byte aligned (the C-ABI checks it);
-// len <= 64.
-__device__ __forceinline__ void lc_zero_beside(float* row, int len, unsigned long long keep) {
-  const int head = min(len, (int)(((16u - ((unsigned)(uintptr_t)row & 15u)) & 15u) >> 2));
-  int e = 0;
-  for (; e < head; ++e)
-    if (!((keep >> e) & 1ull)) row[e] = 0.0f;
-  for (; e + 4 <= len; e += 4) {
-    const unsigned m4 = (unsigned)(keep >> e) & 0xFu;
-    if (m4 == 0u) {
-      *reinterpret_cast<float4*>(row + e) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (!((m4 >> t) & 1u)) row[e + t] = 0.0f;
-    }
-  }
-  for (; e < len; ++e)
-    if (!((keep >> e) & 1ull)) row[e] = 0.0f;
-}
-
 // One derivative column (u, j), u = q when uq: the forward pass over bodies
 // j .. n-1, the backward pass down to the base (dc_i for every body), then
 // J[:, col] = -M^-1 dc. The loops run over the bodies at compile time (the
@@ -183,8 +161,10 @@ __device__ __forceinline__ void lc_load_body(const LcWs& w, int i, LcBody& b) {
 // operands; one code path serves both kinds of column, which differ only in
 // the case terms at the column's own joint. The next body's record is loaded
 // before the current body's arithmetic, so that the shared-memory latency
-// overlaps it.
-template <int NB, bool PL, bool DC = false>
+// overlaps it. With STG the column goes to the lane's staging block instead
+// (entry (r, c) of the chain's n x 2n block at r * 2n + c), from which the warp
+// writes whole rows of J together.
+template <int NB, bool PL, bool DC = false, bool STG = false>
 __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int j, bool uq, const float* Mi,
                                           float* __restrict__ Jk) {
   constexpr int PB = 7;
@@ -260,12 +240,14 @@ __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int 
 #pragma unroll
   for (int rr = 0; rr < NB; ++rr) {
     if constexpr (DC) {                                // the gradient of ID itself (no product)
-      if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = dc[rr];
+      if constexpr (STG) Jk[rr * 2 * NB + (uq ? 0 : NB) + j] = dc[rr];
+      else if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = dc[rr];
     } else {
       float acc = 0.0f;
 #pragma unroll
       for (int m = 0; m < NB; ++m) acc += Mi[lc_tri<NB>(rr, m)] * dc[m];
-      if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = -acc;
+      if constexpr (STG) Jk[rr * 2 * NB + (uq ? 0 : NB) + j] = -acc;
+      else if (Jk) Jk[(PL ? P.slot[rr] : rr) * 2 * ld + col] = -acc;
     }
   }
 }
@@ -365,6 +347,12 @@ __device__ __forceinline__ void lc_vjp(const LcParams& P, const LcWs& w, long k,
   }
 }
 
+// Whether a chain placed in a larger robot stages its matrix blocks per warp
+// (the gradient of FD, M^-1 and the gradient of ID; see lc_flush_rows).
+__host__ __device__ constexpr bool lc_stages(bool PL, int MODE) {
+  return PL && (MODE == MODE_GRAD || MODE == MODE_GRAD_ID || MODE == MODE_MINV);
+}
+
 // RNEA at a given qdd (NULL for zero) and, for MODE_GRAD_ID, the derivative
 // columns of Alg. 1 at that qdd without the product with M^-1 (no M^-1 is
 // formed): tau (MODE_RNEA) or D = [dID/dq | dID/dqd] (MODE_GRAD_ID) at the
@@ -373,7 +361,7 @@ __device__ __forceinline__ void lc_vjp(const LcParams& P, const LcWs& w, long k,
 template <int NB, bool PL, int MODE>
 __device__ __forceinline__ void lc_id(const LcParams& P, const LcWs& w, long k, int ld, const float* __restrict__ q,
                                       const float* __restrict__ qd, const float* __restrict__ qdd,
-                                      float* __restrict__ out) {
+                                      float* __restrict__ out, float* __restrict__ stg) {
   constexpr int PB = 7;
   {
     float vp[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, ap[6];
@@ -445,13 +433,61 @@ __device__ __forceinline__ void lc_id(const LcParams& P, const LcWs& w, long k, 
     }
   }
   if constexpr (MODE == MODE_GRAD_ID) {
-    float* Dk = out + k * 2 * ld * ld;
+    constexpr bool kStg = lc_stages(PL, MODE);         // a placed chain stages its block of D
+    float* Dk = kStg ? stg : out + k * 2 * ld * ld;
 #pragma unroll 1
-    for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL, true>(P, w, c >> 1, (c & 1) == 0, nullptr, Dk);
-    if (PL && P.zero_fill) {                           // the chain's rows of D: zeros beside its blocks
-      const unsigned long long keep = (unsigned long long)P.mask | ((unsigned long long)P.mask << ld);
+    for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL, true, kStg>(P, w, c >> 1, (c & 1) == 0, nullptr, Dk);
+  }
+}
+
+// The gradient of FD of a chain placed in a larger robot stages its blocks of J
+// and M^-1 in shared memory, and the warp writes whole rows of its 32 knot points
+// (the blocks and the zeros beside them) with stores of consecutive words: a
+// lane's own rows are short pieces of long rows, which as per-lane stores cost
+// one L2 sector each and, into lines already evicted, a read of the rest.
+// (M^-1 and the gradient of ID alone stage their one block the same way.)
+// Staged floats per lane: J's (or D's) n x 2n block, then M^-1's n x n block at
+// lc_stage_moff, made odd so that the lanes' blocks start in different banks.
+template <int NB, int MODE>
+__host__ __device__ constexpr int lc_stage_moff() { return MODE == MODE_MINV ? 0 : 2 * NB * NB; }
+template <int NB, int MODE>
+__host__ __device__ constexpr int lc_stage_floats() {
+  return (lc_stage_moff<NB, MODE>() + (MODE == MODE_GRAD_ID ? 0 : NB * NB)) | 1;
+}
+template <int NB, bool PL, int MODE>
+__host__ __device__ constexpr int lc_warp_bytes() {
+  return LcLayout<NB, MODE == MODE_VJP ? 9 : 7>::kWarpBytes +
+         (lc_stages(PL, MODE) ? 32 * 4 * lc_stage_floats<NB, MODE>() : 0);
+}
+
+// Whole rows of J (and of M^-1) of the warp's knot points kb .. kb + nk - 1 from
+// the staged blocks: entry c of a row is the staged value where column c belongs
+// to the chain, else zero. Lane l writes entries l and l + 32 of every row, so
+// that each store of the warp covers consecutive words of one row; src0 / src1
+// are the staged columns of entries l and l + 32 of a row of J and srcm that of
+// entry l of a row of M^-1 (-1: a zero).
+template <int NB, int MODE>
+__device__ __forceinline__ void lc_flush_rows(const LcParams& P, const float* stg_warp, int lane, long kb, int nk,
+                                              int src0, int src1, int srcm, float* __restrict__ J,
+                                              float* __restrict__ Minv) {
+  constexpr int SP = lc_stage_floats<NB, MODE>(), MO = lc_stage_moff<NB, MODE>();
+  const int ld = P.ld, L = 2 * ld;
 #pragma unroll 1
-      for (int rr = 0; rr < NB; ++rr) lc_zero_beside(Dk + P.slot[rr] * 2 * ld, 2 * ld, keep);
+  for (int t = 0; t < nk; ++t) {
+    const float* st = stg_warp + t * SP;
+    if (J) {
+      float* Jt = J + (kb + t) * (long)L * ld;
+#pragma unroll
+      for (int rr = 0; rr < NB; ++rr) {
+        float* row = Jt + P.slot[rr] * L;
+        if (lane < L) row[lane] = src0 >= 0 ? st[rr * 2 * NB + src0] : 0.0f;
+        if (lane + 32 < L) row[lane + 32] = src1 >= 0 ? st[rr * 2 * NB + src1] : 0.0f;
+      }
+    }
+    if (Minv && lane < ld) {
+      float* Mt = Minv + (kb + t) * (long)ld * ld;
+#pragma unroll
+      for (int rr = 0; rr < NB; ++rr) Mt[P.slot[rr] * ld + lane] = srcm >= 0 ? st[MO + rr * NB + srcm] : 0.0f;
     }
   }
 }
@@ -460,13 +496,17 @@ __device__ __forceinline__ void lc_id(const LcParams& P, const LcWs& w, long k, 
 // NULL), out3 = M^-1 (or NULL). MODE_FD: x3 = tau, out = qdd. MODE_VJP: x3 = tau,
 // x4 = gbar = dL/dqdd, out = dL/dq, out2 = dL/dqd, out3 = dL/dtau. MODE_MINV:
 // out = M^-1. MODE_RNEA: x3 = qdd (or NULL), out = tau. MODE_GRAD_ID: x3 = qdd
-// (or NULL), out = [dID/dq | dID/dqd].
+// (or NULL), out = [dID/dq | dID/dqd]. For the gradient of FD of a placed chain
+// (lc_stages) the chain's blocks of J and M^-1 go to the lane's staging block stg
+// (J's n x 2n block, then M^-1's n x n block, row-major), which the warp then
+// writes out as whole rows (lc_flush_rows).
 template <int NB, bool PL, int MODE>
 __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k, const float* __restrict__ q,
                                         const float* __restrict__ qd, const float* __restrict__ x3,
                                         const float* __restrict__ x4, float* __restrict__ out,
-                                        float* __restrict__ out2, float* __restrict__ out3) {
+                                        float* __restrict__ out2, float* __restrict__ out3, float* __restrict__ stg) {
   constexpr int PB = LcLayout<NB, MODE == MODE_VJP ? 9 : 7>::kPB;
+  constexpr bool kStg = lc_stages(PL, MODE);
   const float* tau = x3;
   float* J = MODE == MODE_GRAD ? out : nullptr;
   float* qdd_out = MODE == MODE_GRAD ? out2 : (MODE == MODE_FD ? out : nullptr);
@@ -480,7 +520,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
   // writes the caller joints slot[i] of knot points of ld joints.
   const int ld = PL ? P.ld : NB;
   if constexpr (MODE == MODE_RNEA || MODE == MODE_GRAD_ID) {
-    lc_id<NB, PL, MODE>(P, w, k, ld, q, qd, x3, out);
+    lc_id<NB, PL, MODE>(P, w, k, ld, q, qd, x3, out, stg);
     return;
   }
   {
@@ -493,12 +533,32 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
     for (int u = 0; u < 6; ++u)
 #pragma unroll
       for (int s = 0; s < 6; ++s) carry[u][s] = 0.0f;
+    // a placed chain loads q_i and qd_i one body ahead, so that the latency of
+    // its scattered rows overlaps a body (a whole chain's rows are contiguous, and
+    // there the extra registers measured slower: 2.10 against 2.01 ms per step)
+    float qn = 0.0f, qdn = 0.0f;
+    if constexpr (PL) {
+      qn = __ldg(q + k * ld + P.slot[NB - 1]);
+      if constexpr (MODE != MODE_MINV) qdn = __ldg(qd + k * ld + P.slot[NB - 1]);
+    }
 #pragma unroll 1
     for (int i = NB - 1; i >= 0; --i) {
       float E[9];
-      const long gi = k * ld + (PL ? P.slot[i] : i);
-      lc_transform(P, i, __ldg(q + gi), E);
-      const float qdi = MODE == MODE_MINV ? 0.0f : __ldg(qd + gi);
+      float qdi;
+      if constexpr (PL) {
+        const float qi = qn;
+        qdi = qdn;
+        if (i > 0) {
+          const long gn = k * ld + P.slot[i - 1];
+          qn = __ldg(q + gn);
+          if constexpr (MODE != MODE_MINV) qdn = __ldg(qd + gn);
+        }
+        lc_transform(P, i, qi, E);
+      } else {
+        const long gi = k * ld + i;
+        lc_transform(P, i, __ldg(q + gi), E);
+        qdi = MODE == MODE_MINV ? 0.0f : __ldg(qd + gi);
+      }
       w.f4(PB * i) = make_float4(E[0], E[1], E[2], E[3]);
       w.f4(PB * i + 1) = make_float4(E[4], E[5], E[6], E[7]);
       const float* a = P.axis[i];
@@ -623,13 +683,17 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
 #pragma unroll
     for (int kk = i; kk < NB; ++kk) Mi[lc_tri<NB>(i, kk)] = row[kk];
   }
-  if (minv_out) {
+  if (kStg && minv_out) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int kk = 0; kk < NB; ++kk) stg[lc_stage_moff<NB, MODE>() + i * NB + kk] = Mi[lc_tri<NB>(i, kk)];
+  } else if (minv_out) {
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       float* row = minv_out + (k * ld + (PL ? P.slot[i] : i)) * ld;
 #pragma unroll
       for (int kk = 0; kk < NB; ++kk) row[PL ? P.slot[kk] : kk] = Mi[lc_tri<NB>(i, kk)];
-      if (PL && P.zero_fill) lc_zero_beside(row, ld, P.mask);   // zeros beside the chain's block
     }
   }
   if constexpr (MODE == MODE_MINV) return;
@@ -763,14 +827,9 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
     return;
   }
   // ---- a7 - a9: derivative columns and J = -M^-1 dc
-  float* Jk = J + k * 2 * ld * ld;
+  float* Jk = kStg ? stg : J + k * 2 * ld * ld;
 #pragma unroll 1
-  for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL>(P, w, c >> 1, (c & 1) == 0, Mi, Jk);
-  if (PL && P.zero_fill) {                             // the chain's rows of J: zeros beside its blocks
-    const unsigned long long keep = (unsigned long long)P.mask | ((unsigned long long)P.mask << ld);
-#pragma unroll 1
-    for (int rr = 0; rr < NB; ++rr) lc_zero_beside(Jk + P.slot[rr] * 2 * ld, 2 * ld, keep);
-  }
+  for (int c = 0; c < 2 * NB; ++c) lc_column<NB, PL, false, kStg>(P, w, c >> 1, (c & 1) == 0, Mi, Jk);
 }
 
 template <int NB, bool PL, int MODE>
@@ -783,13 +842,39 @@ __global__ void __launch_bounds__(256, 1) grid_lane_chain_kernel(const __grid_co
   extern __shared__ __align__(16) unsigned char lc_smem[];
   using Lay = LcLayout<NB, MODE == MODE_VJP ? 9 : 7>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* base = lc_smem + (size_t)warp * Lay::kWarpBytes;
+  unsigned char* base = lc_smem + (size_t)warp * lc_warp_bytes<NB, PL, MODE>();
   LcWs w;
   w.s4 = reinterpret_cast<float4*>(base) + lane;
   w.s1 = reinterpret_cast<float*>(base + 32 * 16 * Lay::kS4) + lane;
   const long stride = (long)gridDim.x * blockDim.x;
-  for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride)
-    lc_knot<NB, PL, MODE>(P, w, k, q, qd, x3, x4, out, out2, out3);
+  if constexpr (lc_stages(PL, MODE)) {
+    // the warp's knot points kb .. kb + 31 together: each lane stages its blocks,
+    // then the warp writes their rows (kb is the same for every lane of a warp)
+    constexpr int SP = lc_stage_floats<NB, MODE>();
+    float* stg_warp = reinterpret_cast<float*>(base + Lay::kWarpBytes);
+    float* jrows = MODE == MODE_MINV ? nullptr : out;
+    float* mrows = MODE == MODE_MINV ? out : (MODE == MODE_GRAD ? out3 : nullptr);
+    const int ld = P.ld;
+    int src0 = -1, src1 = -1, srcm = -1;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int sl = P.slot[i];
+      if (lane == sl) { src0 = i; srcm = i; }        // q columns (and M^-1 columns) of the chain
+      if (lane == ld + sl) src0 = NB + i;            // its qd columns, among entries 0 .. 31
+      if (lane + 32 == ld + sl) src1 = NB + i;       // ... or among entries 32 .. 63
+    }
+    for (long kb = (long)blockIdx.x * blockDim.x + warp * 32; kb < N; kb += stride) {
+      const long k = kb + lane;
+      if (k < N) lc_knot<NB, PL, MODE>(P, w, k, q, qd, x3, x4, out, out2, out3, stg_warp + lane * SP);
+      __syncwarp();
+      lc_flush_rows<NB, MODE>(P, stg_warp, lane, kb, (int)(N - kb < 32 ? N - kb : 32), src0, src1, srcm, jrows,
+                              mrows);
+      __syncwarp();
+    }
+  } else {
+    for (long k = (long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride)
+      lc_knot<NB, PL, MODE>(P, w, k, q, qd, x3, x4, out, out2, out3, nullptr);
+  }
 }
 
 struct LcDev {
@@ -814,7 +899,7 @@ template <int NB, bool PL, int MODE>
 grid_status lc_launch(const grid_model* m, const LcParams& P, int N, const float* q, const float* qd,
                       const float* x3, const float* x4, float* out, float* out2, float* out3, cudaStream_t st) {
   auto kern = grid_lane_chain_kernel<NB, PL, MODE>;
-  const int wb = LcLayout<NB, MODE == MODE_VJP ? 9 : 7>::kWarpBytes;
+  const int wb = lc_warp_bytes<NB, PL, MODE>();
   const LcDev di = lc_dev(m->device);
   static std::atomic<int> opted{0};
   if (!opted.load()) {
@@ -873,12 +958,12 @@ grid_status lc_dispatch(const grid_model* m, int n, const LcParams& P, int N, co
 // The robot's constants and placement as kernel parameters, then the launch.
 // With slot non-NULL the chain is one component of a robot of ld joints per knot
 // point (ld <= 32) whose body i is caller joint slot[i]; the call writes only the
-// chain's entries of the outputs (for J and M^-1 its rows: its blocks, and with
-// zero_fill the zeros beside them).
+// chain's entries of the outputs: its joints' entries of the vectors and its whole
+// rows of the matrices (its blocks and the zeros beside them).
 template <int MODE>
 grid_status lc_run(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N, const float* q,
                    const float* qd, const float* x3, const float* x4, float* out, float* out2, float* out3,
-                   cudaStream_t st, bool zero_fill) {
+                   cudaStream_t st) {
   const int n = hm->n;
   if (n < 2 || n > kLcMaxB || hm->any_prism || (slot && (ld < n || ld > 32)) || (!slot && ld != n)) {
     grid_set_error("lane chain kernel: %d bodies in knot points of %d joints", n, ld);
@@ -886,7 +971,6 @@ grid_status lc_run(const grid_model* m, const ModelDev<float>* hm, int ld, const
   }
   LcParams P{};
   P.ld = ld;
-  P.zero_fill = zero_fill ? 1 : 0;
   for (int i = 0; i < n; ++i) {
     if (hm->parent[i] != i - 1 || hm->perm[i] != i) {
       grid_set_error("lane chain kernel: not a serial chain in caller order");

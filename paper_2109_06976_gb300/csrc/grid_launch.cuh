@@ -166,7 +166,7 @@ grid_status launch_chain(const grid_model* m, const ModelDev<S>* hm, const Model
 // whose body i is caller joint slot[i] (a leg of a forest, a part).
 grid_status launch_lane_chain(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                               const float* q, const float* qd, const float* tau, float* J, float* qdd,
-                              float* Minv, cudaStream_t st, bool zero_fill = true);
+                              float* Minv, cudaStream_t st);
 // FD and the vector-Jacobian product through FD in the same form
 // (grid_lane_chain_fdv.cu): qdd; dL/dq, dL/dqd, dL/dtau for gbar = dL/dqdd.
 grid_status launch_lane_chain_fd(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
@@ -175,15 +175,14 @@ grid_status launch_lane_chain_vjp(const grid_model* m, const ModelDev<float>* hm
                                   const float* q, const float* qd, const float* tau, const float* gbar, float* dq,
                                   float* dqd, float* dtau, cudaStream_t st);
 // RNEA (qdd NULL for zero), M^-1 and the gradient of ID in the same form
-// (grid_lane_chain_id.cu); without zero_fill a placed chain leaves the zeros beside
-// its blocks of M^-1 or D to the caller.
+// (grid_lane_chain_id.cu); a placed chain writes its whole rows of M^-1 or D.
 grid_status launch_lane_chain_rnea(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
                                    const float* q, const float* qd, const float* qdd, float* tau, cudaStream_t st);
 grid_status launch_lane_chain_minv(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot, int N,
-                                   const float* q, float* Minv, cudaStream_t st, bool zero_fill);
+                                   const float* q, float* Minv, cudaStream_t st);
 grid_status launch_lane_chain_grad_id(const grid_model* m, const ModelDev<float>* hm, int ld, const int* slot,
                                       int N, const float* q, const float* qd, const float* qdd, float* D,
-                                      cudaStream_t st, bool zero_fill);
+                                      cudaStream_t st);
 // Batches from this many knot points up take the one-lane-per-knot-point chain
 // kernel by default (below, the 8-lane kernel has the shorter latency).
 constexpr int kLaneChainMinN = 32768;
@@ -263,8 +262,8 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
   if constexpr (MODE != MODE_GRAD && !MIXED && std::is_same<S, float>::value) {
     // RNEA, M^-1, FD, the gradient of ID and the vector-Jacobian product of chains
     // and of a forest's legs, one lane per knot point (each leg writes its joints'
-    // entries of the vector outputs and its blocks of the matrix outputs, which
-    // are cleared first)
+    // entries of the vector outputs and its whole rows of the matrix outputs: its
+    // blocks and the zeros beside them)
     bool lane1 = m->specialize_opt && (m->lanes_opt == 1 || (m->lanes_opt == 0 && N >= kLaneChainMinN));
     if (lane1 && m->lanes_opt == 0) {
       cudaPointerAttributes pa{};
@@ -280,20 +279,12 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
       else if constexpr (MODE == MODE_VJP)
         return launch_lane_chain_vjp(m, mh, n, slot, N, q, qd, x3, x4, out, out2, out3, st);
       else if constexpr (MODE == MODE_RNEA) return launch_lane_chain_rnea(m, mh, n, slot, N, q, qd, x3, out, st);
-      else if constexpr (MODE == MODE_MINV) return launch_lane_chain_minv(m, mh, n, slot, N, q, out, st, false);
-      else return launch_lane_chain_grad_id(m, mh, n, slot, N, q, qd, x3, out, st, false);
+      else if constexpr (MODE == MODE_MINV) return launch_lane_chain_minv(m, mh, n, slot, N, q, out, st);
+      else return launch_lane_chain_grad_id(m, mh, n, slot, N, q, qd, x3, out, st);
     };
     if (lane1 && m->chain && n >= 2 && n <= kChainMaxN) return one(hm, nullptr);
     if (lane1 && m->forest_k > 1 && m->branches == m->forest_k && m->forest_l >= 2 && m->forest_l <= kChainMaxN &&
         n <= 32) {
-      if constexpr (MODE == MODE_MINV || MODE == MODE_GRAD_ID) {
-        const size_t per = MODE == MODE_MINV ? (size_t)n * n : (size_t)2 * n * n;
-        const cudaError_t e = cudaMemsetAsync(out, 0, (size_t)N * per * sizeof(float), st);
-        if (e != cudaSuccess) {
-          grid_set_error("clearing the outputs: %s", cudaGetErrorString(e));
-          return GRID_E_CUDA;
-        }
-      }
       int slot[kChainMaxN];
       for (int c = 0; c < m->forest_k; ++c) {
         for (int i = 0; i < m->forest_l; ++i) slot[i] = c * m->forest_l + i;
@@ -319,25 +310,16 @@ grid_status dispatch(const grid_model* m, int N, const S* q, const S* qd, const 
     }
     if (lane1 && m->chain && n >= 2 && n <= kChainMaxN)
       return launch_lane_chain(m, hm, n, nullptr, N, q, qd, x3, out, out2, out3, st);
-    // a forest with one model per chain: the outputs cleared, then each chain (a
-    // leg) in turn, one lane per (knot point, leg), writing its blocks of J and
-    // M^-1 and its entries of qdd (each leg writing its whole rows, zeros included,
-    // measured slower than one clearing pass over the outputs: 1.67 against
-    // 1.52 ms for the 12-DoF tree on 1,048,576 knot points, with the zeros in
-    // 16-byte stores)
+    // a forest with one model per chain: each chain (a leg) in turn, one lane per
+    // (knot point, leg), writing its whole rows of J and M^-1 (its blocks and the
+    // zeros beside them, from blocks staged per warp) and its entries of qdd
     if (lane1 && m->forest_k > 1 && m->branches == m->forest_k && m->forest_l >= 2 && m->forest_l <= kChainMaxN &&
         n <= 32) {
-      cudaError_t e = cudaMemsetAsync(out, 0, (size_t)N * 2 * n * n * sizeof(float), st);
-      if (e == cudaSuccess && out3) e = cudaMemsetAsync(out3, 0, (size_t)N * n * n * sizeof(float), st);
-      if (e != cudaSuccess) {
-        grid_set_error("clearing the outputs: %s", cudaGetErrorString(e));
-        return GRID_E_CUDA;
-      }
       int slot[kChainMaxN];
       for (int c = 0; c < m->forest_k; ++c) {
         for (int i = 0; i < m->forest_l; ++i) slot[i] = c * m->forest_l + i;
         const grid_status r =
-            launch_lane_chain(m, &m->br_host_f[c], n, slot, N, q, qd, x3, out, out2, out3, st, false);
+            launch_lane_chain(m, &m->br_host_f[c], n, slot, N, q, qd, x3, out, out2, out3, st);
         if (r != GRID_OK) return r;
       }
       return GRID_OK;

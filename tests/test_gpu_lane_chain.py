@@ -200,10 +200,10 @@ def test_lane_chain_placed_components(grid, key, N):
 @pytest.mark.parametrize("key", ["tree12", "tree30", "rand13"])
 @pytest.mark.parametrize("offset", [1, 2, 3])
 def test_lane_chain_placed_outputs_off_16_bytes(grid, key, offset):
-    """Placed legs write the zeros beside their blocks with 16-byte stores where
-    the words are aligned and scalar stores at the rows' ends: outputs that start
+    """Placed legs write whole rows of J, M^-1 and the gradient of ID (their blocks
+    and the zeros beside them) from blocks staged per warp: outputs that start
     1 .. 3 floats past a 16-byte boundary (NaN-filled around them) give the same
-    J, M^-1 and gradient of ID as aligned ones, and nothing outside is written."""
+    values as aligned ones, and nothing outside is written."""
     r = PLACED[key]()
     n = r.n
     m = grid.Model.from_robot(r)
