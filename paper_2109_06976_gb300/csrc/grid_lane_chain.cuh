@@ -44,6 +44,7 @@ struct LcParams {
   float rT[kLcMaxB][3];
   float ET[kLcMaxB][9];
   float inert[kLcMaxB][10];   // m, h = m c (3), Ibar about the body origin: xx yy zz xy xz yz
+  float2 ip[kLcMaxB][9];      // the same, paired for lc_i_mul (see there)
   float a0[6];                // base acceleration -g
   unsigned et_ident;          // bit i: the fixed rotation of body i is the identity
   // Placement in the caller's arrays (a chain that is one component of a larger
@@ -79,6 +80,45 @@ struct LcWs {
   __device__ float4& f4(int s) const { return s4[s * 32]; }
   __device__ float& f1(int s) const { return s1[s * 32]; }
 };
+
+// o = I_i m (o += I_i m for lc_i_mul_acc) in paired FP32: components k and 3 + k
+// share three paired multiply-adds, with the coefficient pairs of ip[i]
+//   (Ixx, m) (Ixy, h2) (Ixz, -h1) | (Iyy, m) (Ixy, -h2) (Iyz, h0) | (Izz, m) (Ixz, h1) (Iyz, -h0)
+// against (m_k, m_3+k) and two broadcast operands; the two remaining terms of the
+// angular component k (h x v) are scalar multiply-adds.
+template <bool ACC>
+__device__ __forceinline__ void lc_i_mul_t(const LcParams& P, int i, const float* m, float* o) {
+  const float2* c = P.ip[i];
+  const float h0 = P.inert[i][1], h1 = P.inert[i][2], h2 = P.inert[i][3];
+  float2 a0, a1, a2;
+  if constexpr (ACC) {
+    a0 = __ffma2_rn(c[0], make_float2(m[0], m[3]), make_float2(o[0], o[3]));
+    a1 = __ffma2_rn(c[3], make_float2(m[1], m[4]), make_float2(o[1], o[4]));
+    a2 = __ffma2_rn(c[6], make_float2(m[2], m[5]), make_float2(o[2], o[5]));
+  } else {
+    a0 = __fmul2_rn(c[0], make_float2(m[0], m[3]));
+    a1 = __fmul2_rn(c[3], make_float2(m[1], m[4]));
+    a2 = __fmul2_rn(c[6], make_float2(m[2], m[5]));
+  }
+  a0 = __ffma2_rn(c[1], make_float2(m[1], m[1]), a0);
+  a0 = __ffma2_rn(c[2], make_float2(m[2], m[2]), a0);
+  a1 = __ffma2_rn(c[4], make_float2(m[0], m[0]), a1);
+  a1 = __ffma2_rn(c[5], make_float2(m[2], m[2]), a1);
+  a2 = __ffma2_rn(c[7], make_float2(m[0], m[0]), a2);
+  a2 = __ffma2_rn(c[8], make_float2(m[1], m[1]), a2);
+  o[0] = a0.x + h1 * m[5] - h2 * m[4];
+  o[1] = a1.x + h2 * m[3] - h0 * m[5];
+  o[2] = a2.x + h0 * m[4] - h1 * m[3];
+  o[3] = a0.y;
+  o[4] = a1.y;
+  o[5] = a2.y;
+}
+__device__ __forceinline__ void lc_i_mul(const LcParams& P, int i, const float* m, float* o) {
+  lc_i_mul_t<false>(P, i, m, o);
+}
+__device__ __forceinline__ void lc_i_mul_acc(const LcParams& P, int i, const float* m, float* o) {
+  lc_i_mul_t<true>(P, i, m, o);
+}
 
 // E_i, and from the same slots v_i and qd_i
 template <int PB>
@@ -177,10 +217,9 @@ __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int 
     if (i >= j) {
       if (i + 1 < NB) lc_load_body<PB>(w, i + 1, nxt);
       const float* a = P.axis[i];
-      const float* in = P.inert[i];
       const float* v = cur.v;
       float g[6], ndv[6], nda[6], vxs[6];
-      i_mul(in, v, g);                                 // gamma_i = I_i v_i
+      lc_i_mul(P, i, v, g);                                 // gamma_i = I_i v_i
       cross_s(v, a, false, vxs);                       // v x S
       if (i == j) {
         // u = q: dv_j = v_j x S_j, da_j = beta_j;  u = qd: dv_j = S_j, da_j = v_j x S_j
@@ -199,9 +238,9 @@ __device__ __forceinline__ void lc_column(const LcParams& P, const LcWs& w, int 
       const float sq[3] = {a[0] * cur.qd, a[1] * cur.qd, a[2] * cur.qd};
       cross_s_acc(ndv, sq, false, nda);                // + dv x S qd
       float f[6], idv[6];
-      i_mul(in, nda, f);
+      lc_i_mul(P, i, nda, f);
       crf_mul_acc(ndv, g, f);
-      i_mul(in, ndv, idv);
+      lc_i_mul(P, i, ndv, idv);
       crf_mul_acc(v, idv, f);
       if (i == j && uq && j > 0) {                     // + S_j x* F_j (backward-pass term; it
                                                        // reaches the ancestors of j only)
@@ -302,7 +341,6 @@ __device__ __forceinline__ void lc_vjp(const LcParams& P, const LcWs& w, long k,
 #pragma unroll 1
   for (int i = NB - 1; i >= 0; --i) {
     const float* a = P.axis[i];
-    const float* in = P.inert[i];
     const float4 v0 = w.f4(PB * i + 2), v1 = w.f4(PB * i + 3), b0 = w.f4(PB * i + 4), f0 = w.f4(PB * i + 5),
                  b2 = w.f4(PB * i + 6), p0 = w.f4(PB * i + 7), p1 = w.f4(PB * i + 8);
     const float v[6] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y};
@@ -311,11 +349,11 @@ __device__ __forceinline__ void lc_vjp(const LcParams& P, const LcWs& w, long k,
     const float psi[6] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y};
     const float qdi = v1.w;
     float g[6], A[6], Vb[6], t1[6], vxp[6], t2[6];
-    i_mul(in, v, g);                                   // I v
-    i_mul(in, psi, A);                                 // abar = I psi
+    lc_i_mul(P, i, v, g);                                   // I v
+    lc_i_mul(P, i, psi, A);                                 // abar = I psi
     crf_mul(psi, g, t1);                               // psi x* (I v)
     crm_mul(v, psi, vxp);                              // v x psi
-    i_mul(in, vxp, t2);
+    lc_i_mul(P, i, vxp, t2);
 #pragma unroll
     for (int e = 0; e < 6; ++e) { A[e] += CA[e]; Vb[e] = -t1[e] - t2[e] + CV[e]; }
     {
@@ -375,7 +413,6 @@ __device__ __forceinline__ void lc_id(const LcParams& P, const LcWs& w, long k, 
       const float qdi = __ldg(qd + gi), qddi = qdd ? __ldg(qdd + gi) : 0.0f;
       const float* a = P.axis[i];
       const float* r = P.rT[i];
-      const float* in = P.inert[i];
       const float sq[3] = {a[0] * qdi, a[1] * qdi, a[2] * qdi};   // S qd
       float v[6], Xa[6], acc[6], g[6], f[6];
       x_mul(E, r, vp, v);                              // v_parent = 0 at the base
@@ -388,8 +425,8 @@ __device__ __forceinline__ void lc_id(const LcParams& P, const LcWs& w, long k, 
         crm_mul_acc(v, vj, acc);                       // a = X a_parent + v x S qd + S qdd
       }
       acc[0] += a[0] * qddi; acc[1] += a[1] * qddi; acc[2] += a[2] * qddi;
-      i_mul(in, v, g);
-      i_mul(in, acc, f);
+      lc_i_mul(P, i, v, g);
+      lc_i_mul(P, i, acc, f);
       crf_mul_acc(v, g, f);
       w.f4(PB * i) = make_float4(E[0], E[1], E[2], E[3]);
       w.f4(PB * i + 1) = make_float4(E[4], E[5], E[6], E[7]);
@@ -708,7 +745,6 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
       lc_load_E<PB>(w, i, E);
       const float* a = P.axis[i];
       const float* r = P.rT[i];
-      const float* in = P.inert[i];
       const float qdi = w.f4(PB * i + 3).w;
       const float sq[3] = {a[0] * qdi, a[1] * qdi, a[2] * qdi};   // S qd
       float v[6], Xa[6], acc[6], g[6], f[6];
@@ -721,8 +757,8 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
         const float vj[6] = {sq[0], sq[1], sq[2], 0.0f, 0.0f, 0.0f};
         crm_mul_acc(v, vj, acc);                       // a = X a_parent + v x S qd
       }
-      i_mul(in, v, g);
-      i_mul(in, acc, f);
+      lc_i_mul(P, i, v, g);
+      lc_i_mul(P, i, acc, f);
       crf_mul_acc(v, g, f);
       w.f4(PB * i + 2) = make_float4(v[0], v[1], v[2], v[3]);
       w.f4(PB * i + 3) = make_float4(v[4], v[5], E[8], qdi);
@@ -787,7 +823,7 @@ __device__ __forceinline__ void lc_knot(const LcParams& P, const LcWs& w, long k
       for (int e = 0; e < 6; ++e) Xa[e] += da[e];
       const float qddi = w.f1(i);
       da[0] += a[0] * qddi; da[1] += a[1] * qddi; da[2] += a[2] * qddi;
-      i_mul_acc(P.inert[i], da, f);
+      lc_i_mul_acc(P, i, da, f);
       float beta[6];
       cross_s(Xa, a, false, beta);
       w.f4(PB * i + 4) = make_float4(beta[0], beta[1], beta[2], beta[3]);
@@ -979,6 +1015,12 @@ grid_status lc_run(const grid_model* m, const ModelDev<float>* hm, int ld, const
     for (int e = 0; e < 3; ++e) { P.axis[i][e] = hm->axis[i][e]; P.rT[i][e] = hm->rT[i][e]; }
     for (int e = 0; e < 9; ++e) P.ET[i][e] = hm->ET[i][e];
     for (int e = 0; e < 10; ++e) P.inert[i][e] = hm->inert[i][e];
+    {
+      const float* in = P.inert[i];   // m, h0, h1, h2, Ixx, Iyy, Izz, Ixy, Ixz, Iyz
+      const float2 ip[9] = {{in[4], in[0]}, {in[7], in[3]}, {in[8], -in[2]}, {in[5], in[0]}, {in[7], -in[3]},
+                            {in[9], in[1]}, {in[6], in[0]}, {in[8], in[2]}, {in[9], -in[1]}};
+      for (int e = 0; e < 9; ++e) P.ip[i][e] = ip[e];
+    }
     if (hm->et_ident[i]) P.et_ident |= 1u << i;
     P.slot[i] = slot ? slot[i] : i;
     if (P.slot[i] < 0 || P.slot[i] >= ld || ((P.mask >> P.slot[i]) & 1u)) {
