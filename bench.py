@@ -50,14 +50,14 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # and lts__t_sectors_srcunit_tex_op_write.sum x 32 B (the writes the SMs send to L2,
 # partial sectors included, whether or not they reach DRAM before the kernel ends).
 # Absent when the kernel changed since the capture.
-NCU_BYTES_PER_KNOT = {"2be1ee1d97df5c41": (63.970816e6 + 165.347072e6) / 524288}
-NCU_L2_WRITE_BYTES_PER_KNOT = {"2be1ee1d97df5c41": 51380224 * 32 / 524288}
+NCU_BYTES_PER_KNOT = {"2dfbe76cf48a1204": (63.866112e6 + 165.638912e6) / 524288}
+NCU_L2_WRITE_BYTES_PER_KNOT = {"2dfbe76cf48a1204": 51380224 * 32 / 524288}
 # FP32 (FMA) pipe utilisation from the same captures (sm__pipe_fma_cycles_active, % of
 # peak sustained while active), reported beside the counted-flop fraction, and the
 # busy share of the LSU data pipe (l1tex__data_pipe_lsu_wavefronts, % of peak
 # sustained elapsed: shared-memory and global-store wavefronts).
-NCU_FMA_PIPE = {"2be1ee1d97df5c41": 0.509}
-NCU_SMEM_PIPE = {"2be1ee1d97df5c41": 0.469}
+NCU_FMA_PIPE = {"2dfbe76cf48a1204": 0.516}
+NCU_SMEM_PIPE = {"2dfbe76cf48a1204": 0.481}
 
 
 # The device code of the 7-DoF step's kernel (the key of the ncu tables above).
