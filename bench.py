@@ -7,7 +7,7 @@ resident in HBM. Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the FP64 CPU oracle (the reference arm of this build)
+--impl reference times the FP64 CPU oracle (the reference arm)
 on the host cores on a bounded sample of the same workload.
 Under torchrun every rank processes its own B trajectories (weak scaling, no
 collective on the data path); value = all knot points / max over ranks.

@@ -397,7 +397,10 @@ grid_status grid_server_bench(grid_server* server, double rate_hz, double second
  * serialise them. Every request is published before the launch, so the
  * kernel's waits and its request search always succeed; the call reports
  * argument and launch errors, and a fault inside a kernel surfaces at the
- * caller's next synchronisation, as for every compute call.
+ * caller's next synchronisation, as for every compute call. (The serving
+ * kernel's own status word, which its bounded waits set when they give up,
+ * sits in the fixed array and is not read back by this call: with every
+ * request published before the launch, those waits do not give up.)
  */
 grid_status grid_serve_batch_static(const grid_model* const* models, int nmodels, int nreq,
                                     const int* req_model, const int* req_H, const float* const* q,

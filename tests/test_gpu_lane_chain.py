@@ -260,7 +260,7 @@ def test_lane_chain_placed_default_dispatch(grid, key):
 def test_lane_chain_precision_report(grid, key, capsys):
     """The one-lane kernel (lanes = 1) on the 7-DoF chain and the 12-DoF tree's
     legs at N = 1024 against the FP64 oracle: the per-column metric with the
-    survey's floor (1e-6) and with the FP32 floor (1e-4), and the ratio of the
+    tight floor (1e-6) and with the FP32 floor (1e-4), and the ratio of the
     1e-6-floor error to the derived per-column bound (tests/metrics.py:
     derived_col_bar). Printed for the record."""
     from tests.metrics import col_rel_err_cols, derived_col_bar

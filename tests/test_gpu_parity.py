@@ -337,7 +337,7 @@ def test_zero_copy_host_buffers(grid):
                                       ("tree30", "mixed")])
 def test_precision_report_workload(grid, key, prec, capsys):
     """FP32 gradient of FD of each workload robot at N = 1024 against the FP64
-    oracle, measured three ways: the per-column metric with the survey's floor
+    oracle, measured three ways: the per-column metric with the tight floor
     (1e-6) and with the FP32 floor (1e-4), and the ratio of the 1e-6-floor error
     to the derived per-column bound max(1e-4, n kappa_2(M) u alpha_j)
     (tests/metrics.py: derived_col_bar). Printed for the record."""
@@ -360,5 +360,5 @@ def test_precision_report_workload(grid, key, prec, capsys):
     with capsys.disabled():
         print("\n" + line)
     assert e4.max() <= TOL32, line
-    # with the survey's floor, every column meets the derived per-column bound
+    # with the tight 1e-6 floor, every column meets the derived per-column bound
     assert (e6 / bar).max() <= 1.0, line
